@@ -1,0 +1,348 @@
+"""FP64 CPU oracle for the cell-wise matrix-free finite-element path (TEST INFRASTRUCTURE).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may use
+this package.  It wraps ``liboracle.so`` (plain C, ``oracle.c``), which is written from the
+paper's definitions and shares nothing with the CUDA library:
+
+* element operators, Eq. (mass_operator) / Eq. (laplace_operator), formed entry by entry with
+  general per-quadrature-point geometry (Sec. 2.3);
+* gather ``G`` / scatter ``G^T`` (Sec. 2.1), the constrained system and ``A_CG = G^T A G``
+  (Sec. 3.1, Eq. (constrained_system));
+* DSS ``S = G I_Riesz G^T`` (Sec. 3.3, Eq. (dss_operator)) and the Jacobi diagonal;
+* assembled Jacobi-PCG/FCG (Algorithm "Communication-Free (Flexible) PCG" on global vectors).
+
+Conventions: canonical cell-wise order ``((cz*my+cy)*mx+cx)*n^3 + (k*n+j)*n+i`` and lexicographic
+global order ``(gz*Ny+gy)*Nx+gx``, ``Nx = mx*p+1``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+
+LAPLACE, MASS = 0, 1
+RHS_SINE, RHS_QUADRATIC = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (FP contraction off, OpenMP on)."""
+    hdr = os.path.join(_HERE, "oracle.h")
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(hdr))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("mx", ctypes.c_int), ("my", ctypes.c_int), ("mz", ctypes.c_int),
+                ("p", ctypes.c_int), ("amp", ctypes.c_double), ("dirichlet", ctypes.c_int)]
+
+
+class _CGOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("flexible", ctypes.c_int)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        M = ctypes.POINTER(_Mesh)
+        ll, i32 = ctypes.c_longlong, ctypes.c_int
+        sig = {
+            "or_gauss": (i32, [i32, _D, _D]),
+            "or_gll": (i32, [i32, _D]),
+            "or_lagrange": (ctypes.c_double, [_D, i32, i32, ctypes.c_double]),
+            "or_lagrange_deriv": (ctypes.c_double, [_D, i32, i32, ctypes.c_double]),
+            "or_n_cells": (ll, [M]), "or_n_cellwise": (ll, [M]), "or_n_unique": (ll, [M]),
+            "or_map": (None, [ctypes.c_double, _D, _D]),
+            "or_cell_nodes": (None, [M, i32, i32, i32, _D]),
+            "or_jacobian": (None, [M, _D, _D, _D]),
+            "or_element_matrix": (i32, [M, i32, ll, _D]),
+            "or_element_row": (i32, [M, i32, ll, i32, _D]),
+            "or_gather": (None, [M, _D, _D]),
+            "or_scatter": (None, [M, _D, _D]),
+            "or_boundary_global": (None, [M, ctypes.POINTER(ctypes.c_ubyte)]),
+            "or_multiplicity": (None, [M, _D]),
+            "or_apply_local": (i32, [M, i32, _D, _D, i32]),
+            "or_apply_assembled": (i32, [M, i32, _D, _D, i32]),
+            "or_dss": (i32, [M, _D, _D]),
+            "or_diag_global": (i32, [M, i32, _D, i32]),
+            "or_element_matrices": (i32, [M, i32, ll, ll, _D, i32]),
+            "or_apply_local_mats": (i32, [M, ll, ll, _D, _D, _D, i32]),
+            "or_csr_nnz": (ll, [M]),
+            "or_assemble_csr": (i32, [M, i32, ctypes.POINTER(ll), ctypes.POINTER(i32), _D, i32]),
+            "or_csr_spmv": (None, [ll, ctypes.POINTER(ll), ctypes.POINTER(i32), _D, _D, _D]),
+            "or_rhs": (i32, [M, i32, _D]),
+            "or_exact_nodal": (None, [M, i32, _D]),
+            "or_l2_error": (i32, [M, i32, _D, _D]),
+            "or_cg": (i32, [M, i32, _D, _D, ctypes.POINTER(_CGOpts), ctypes.POINTER(i32),
+                            _D, _D, _D, i32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_D)
+
+
+class Mesh:
+    """Structured hexahedral mesh of the unit cube, deformed by
+    ``Phi(X) = X + amp sin(pi X) sin(pi Y) sin(pi Z) (1,1,1)`` and interpolated isoparametrically."""
+
+    def __init__(self, m, p: int, amp: float = 0.0, dirichlet: bool = False):
+        mx, my, mz = (m, m, m) if np.isscalar(m) else tuple(m)
+        self.mx, self.my, self.mz, self.p = int(mx), int(my), int(mz), int(p)
+        self.n = self.p + 1
+        self.amp, self.dirichlet = float(amp), bool(dirichlet)
+        self._c = _Mesh(self.mx, self.my, self.mz, self.p, self.amp, int(self.dirichlet))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+    @property
+    def n_cells(self) -> int:
+        return _L().or_n_cells(self.ref)
+
+    @property
+    def n_cellwise(self) -> int:
+        return _L().or_n_cellwise(self.ref)
+
+    @property
+    def n_unique(self) -> int:
+        return _L().or_n_unique(self.ref)
+
+    @property
+    def global_shape(self):
+        p = self.p
+        return (self.mz * p + 1, self.my * p + 1, self.mx * p + 1)
+
+
+# ---- 1D rules -------------------------------------------------------------------------------
+def gauss(n: int):
+    x, w = np.zeros(n), np.zeros(n)
+    assert _L().or_gauss(n, _dp(x), _dp(w)) == 0
+    return x, w
+
+
+def gll(p: int):
+    x = np.zeros(p + 1)
+    assert _L().or_gll(p, _dp(x)) == 0
+    return x
+
+
+def lagrange(t: np.ndarray, i: int, s: float, deriv: bool = False) -> float:
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    f = _L().or_lagrange_deriv if deriv else _L().or_lagrange
+    return f(_dp(t), len(t), i, float(s))
+
+
+# ---- geometry --------------------------------------------------------------------------------
+def map_point(amp: float, X) -> np.ndarray:
+    Xa = np.ascontiguousarray(X, dtype=np.float64)
+    x = np.zeros(3)
+    _L().or_map(float(amp), _dp(Xa), _dp(x))
+    return x
+
+
+def cell_nodes(mesh: Mesh, cx: int, cy: int, cz: int) -> np.ndarray:
+    xn = np.zeros((mesh.n ** 3, 3))
+    _L().or_cell_nodes(mesh.ref, cx, cy, cz, _dp(xn))
+    return xn
+
+
+def jacobian(mesh: Mesh, xn: np.ndarray, xi) -> np.ndarray:
+    J = np.zeros(9)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    _L().or_jacobian(mesh.ref, _dp(np.ascontiguousarray(xn)), _dp(xi), _dp(J))
+    return J.reshape(3, 3)
+
+
+# ---- element level ---------------------------------------------------------------------------
+def element_matrix(mesh: Mesh, op: int, cell: int) -> np.ndarray:
+    nn = mesh.n ** 3
+    A = np.zeros((nn, nn))
+    st = _L().or_element_matrix(mesh.ref, op, cell, _dp(A))
+    if st:
+        raise RuntimeError(f"or_element_matrix status {st}")
+    return A
+
+
+def element_row(mesh: Mesh, op: int, cell: int, row: int) -> np.ndarray:
+    out = np.zeros(mesh.n ** 3)
+    st = _L().or_element_row(mesh.ref, op, cell, row, _dp(out))
+    if st:
+        raise RuntimeError(f"or_element_row status {st}")
+    return out
+
+
+def element_matrices(mesh: Mesh, op: int, cell0: int, ncell: int, nthreads: int = 0):
+    nn = mesh.n ** 3
+    mats = np.zeros((ncell, nn, nn))
+    st = _L().or_element_matrices(mesh.ref, op, cell0, ncell, _dp(mats), nthreads)
+    if st:
+        raise RuntimeError(f"or_element_matrices status {st}")
+    return mats
+
+
+def apply_local_mats(mesh: Mesh, cell0: int, mats: np.ndarray, xc: np.ndarray,
+                     nthreads: int = 0) -> np.ndarray:
+    ncell = mats.shape[0]
+    yc = np.zeros(ncell * mesh.n ** 3)
+    _L().or_apply_local_mats(mesh.ref, cell0, ncell, _dp(mats), _dp(np.ascontiguousarray(xc)),
+                             _dp(yc), nthreads)
+    return yc
+
+
+# ---- gather / scatter ------------------------------------------------------------------------
+def gather(mesh: Mesh, xg: np.ndarray) -> np.ndarray:
+    xc = np.zeros(mesh.n_cellwise)
+    _L().or_gather(mesh.ref, _dp(np.ascontiguousarray(xg, dtype=np.float64)), _dp(xc))
+    return xc
+
+
+def scatter(mesh: Mesh, yc: np.ndarray) -> np.ndarray:
+    yg = np.zeros(mesh.n_unique)
+    _L().or_scatter(mesh.ref, _dp(np.ascontiguousarray(yc, dtype=np.float64)), _dp(yg))
+    return yg
+
+
+def boundary_global(mesh: Mesh) -> np.ndarray:
+    b = np.zeros(mesh.n_unique, dtype=np.uint8)
+    _L().or_boundary_global(mesh.ref, b.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return b.astype(bool)
+
+
+def multiplicity(mesh: Mesh) -> np.ndarray:
+    m = np.zeros(mesh.n_cellwise)
+    _L().or_multiplicity(mesh.ref, _dp(m))
+    return m
+
+
+# ---- operators -------------------------------------------------------------------------------
+def apply_local(mesh: Mesh, op: int, xc: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    yc = np.zeros(mesh.n_cellwise)
+    st = _L().or_apply_local(mesh.ref, op, _dp(np.ascontiguousarray(xc, dtype=np.float64)),
+                             _dp(yc), nthreads)
+    if st:
+        raise RuntimeError(f"or_apply_local status {st}")
+    return yc
+
+
+def apply_assembled(mesh: Mesh, op: int, xg: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    yg = np.zeros(mesh.n_unique)
+    st = _L().or_apply_assembled(mesh.ref, op, _dp(np.ascontiguousarray(xg, dtype=np.float64)),
+                                 _dp(yg), nthreads)
+    if st:
+        raise RuntimeError(f"or_apply_assembled status {st}")
+    return yg
+
+
+def dss(mesh: Mesh, yc: np.ndarray) -> np.ndarray:
+    zc = np.zeros(mesh.n_cellwise)
+    assert _L().or_dss(mesh.ref, _dp(np.ascontiguousarray(yc, dtype=np.float64)), _dp(zc)) == 0
+    return zc
+
+
+def diag_global(mesh: Mesh, op: int, nthreads: int = 0) -> np.ndarray:
+    d = np.zeros(mesh.n_unique)
+    st = _L().or_diag_global(mesh.ref, op, _dp(d), nthreads)
+    if st:
+        raise RuntimeError(f"or_diag_global status {st}")
+    return d
+
+
+def assemble_csr(mesh: Mesh, op: int, nthreads: int = 0):
+    """Return (rowptr, colidx, vals) of the unconstrained A_CG."""
+    nnz = _L().or_csr_nnz(mesh.ref)
+    nu = mesh.n_unique
+    rowptr = np.zeros(nu + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz)
+    st = _L().or_assemble_csr(mesh.ref, op,
+                              rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                              col.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(val), nthreads)
+    if st:
+        raise RuntimeError(f"or_assemble_csr status {st}")
+    return rowptr, col, val
+
+
+def csr_spmv(csr, x: np.ndarray) -> np.ndarray:
+    rowptr, col, val = csr
+    y = np.zeros(len(rowptr) - 1)
+    _L().or_csr_spmv(len(rowptr) - 1, rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                     col.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(val),
+                     _dp(np.ascontiguousarray(x, dtype=np.float64)), _dp(y))
+    return y
+
+
+def apply_dirichlet_csr(mesh: Mesh, csr, xg: np.ndarray) -> np.ndarray:
+    """A_D x = R A_CG R x with R zeroing Dirichlet nodes (identity without Dirichlet)."""
+    x = np.array(xg, dtype=np.float64)
+    if mesh.dirichlet:
+        b = boundary_global(mesh)
+        x[b] = 0.0
+        y = csr_spmv(csr, x)
+        y[b] = 0.0
+        return y
+    return csr_spmv(csr, x)
+
+
+# ---- rhs, exact solution, error --------------------------------------------------------------
+def rhs(mesh: Mesh, kind: int = RHS_SINE) -> np.ndarray:
+    b = np.zeros(mesh.n_cellwise)
+    st = _L().or_rhs(mesh.ref, kind, _dp(b))
+    if st:
+        raise RuntimeError(f"or_rhs status {st}")
+    return b
+
+
+def exact_nodal(mesh: Mesh, kind: int = RHS_SINE) -> np.ndarray:
+    u = np.zeros(mesh.n_unique)
+    _L().or_exact_nodal(mesh.ref, kind, _dp(u))
+    return u
+
+
+def l2_error(mesh: Mesh, uc: np.ndarray, kind: int = RHS_SINE) -> float:
+    e = ctypes.c_double(0.0)
+    _L().or_l2_error(mesh.ref, kind, _dp(np.ascontiguousarray(uc, dtype=np.float64)),
+                     ctypes.byref(e))
+    return e.value
+
+
+# ---- assembled CG ----------------------------------------------------------------------------
+def cg(mesh: Mesh, op: int, bg: np.ndarray, x0=None, rtol: float = 1e-10, maxit: int = 1000,
+       flexible: bool = False, nthreads: int = 0):
+    """Jacobi-PCG (or FCG) on the assembled global system.  Returns dict with x, status, iters,
+    alpha, beta, relres."""
+    nu = mesh.n_unique
+    x = np.zeros(nu) if x0 is None else np.array(x0, dtype=np.float64)
+    alpha, beta, relres = np.zeros(maxit + 1), np.zeros(maxit + 1), np.zeros(maxit + 2)
+    it = ctypes.c_int(0)
+    o = _CGOpts(rtol, maxit, int(flexible))
+    st = _L().or_cg(mesh.ref, op, _dp(np.ascontiguousarray(bg, dtype=np.float64)), _dp(x),
+                    ctypes.byref(o), ctypes.byref(it), _dp(alpha), _dp(beta), _dp(relres), nthreads)
+    k = it.value
+    return {"x": x, "status": st, "iters": k, "alpha": alpha[:k], "beta": beta[:max(k - 1, 0)],
+            "relres": relres[:k + 1]}
