@@ -1,0 +1,378 @@
+"""Throughput benchmark of the cell-wise matrix-free operator apply on GB300.
+
+Workload (one "step"): the FP64 operator sweep on deformed unit-cube meshes
+(x + 0.1 sin(pi x) sin(pi y) sin(pi z) per coordinate, stored per-quadrature-point geometry):
+Laplace and mass at Q2 on 48^3 cells, Q3 on 96^3 cells and Q7 on 32^3 cells, each applied with
+the shared-node summation (FE_ASSEMBLE), i.e. six assembled operator applications.  Inputs are
+drawn per unique node (seed 0) and gathered to cell-wise storage.  value = unique DoFs processed
+per second (GDoF/s) over the whole step.  L2 is flushed (a 512 MB write) before every timed step.
+
+`python bench.py --gpus N --steps K --warmup W [--impl reference]`; N > 1 runs under torchrun,
+one independent replica per GPU (weak scaling).  `--impl reference` times the FP64 CPU oracle on
+the host cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SWEEP = [(2, 48), (3, 96), (7, 32)]  # (degree, cells per direction)
+AMP = 0.1
+METRIC = "Operator-apply GDoF/s (unique DoFs, FP64, FE_ASSEMBLE) over the Q2/Q3/Q7 sweep"
+UNIT = "GDoF/s"
+GEO_BYTES = {0: 48, 1: 8}  # stored geometry bytes per cell-wise DoF: Laplace 6 doubles, mass 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="tiny sizes (plumbing check only)")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks sampling
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id, self.lines, self.proc = gpu_id, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+SAMPLE_CELLS = {2: 8192, 3: 2048, 7: 16}
+
+
+class OracleSampler:
+    """The oracle's element-by-element FP64 apply (element matrices precomputed, OpenMP over
+    cells) on a bounded sample of cells of every (op, degree) of the sweep."""
+
+    def __init__(self, threads: int):
+        import oracle as O
+        from paper_2607_02335_gb300 import synth as S
+
+        self.O, self.threads, self.items = O, threads, []
+        for p, m in SWEEP:
+            mesh = O.Mesh(m, p, amp=AMP)
+            nc, n3 = SAMPLE_CELLS[p], (p + 1) ** 3
+            xc = S.dual_cellwise(m, p, seed=0)[: nc * n3].copy()
+            for op in (O.LAPLACE, O.MASS):
+                mats = O.element_matrices(mesh, op, 0, nc, nthreads=threads)
+                self.items.append(dict(op=op, p=p, mesh=mesh, mats=mats, xc=xc, ncw=nc * n3,
+                                       t=0.0, reps=0))
+
+    def time_once(self):
+        for it in self.items:
+            t0 = time.perf_counter()
+            self.O.apply_local_mats(it["mesh"], 0, it["mats"], it["xc"], nthreads=self.threads)
+            it["t"] += time.perf_counter() - t0
+            it["reps"] += 1
+
+    def reset(self):
+        for it in self.items:
+            it["t"], it["reps"] = 0.0, 0
+
+    def full_step_estimate(self):
+        """(seconds, unique DoFs) of one full step extrapolated from the per-cell-DoF rates."""
+        t, nu = 0.0, 0
+        for it in self.items:
+            m = dict(SWEEP)[it["p"]]
+            rate = it["t"] / (it["reps"] * it["ncw"])
+            t += rate * m ** 3 * (it["p"] + 1) ** 3
+            nu += (m * it["p"] + 1) ** 3
+        return t, nu
+
+    def describe(self):
+        return (f"element-by-element FP64 apply with precomputed element matrices on the first "
+                f"{SAMPLE_CELLS} cells (per degree) of each sweep mesh, Laplace and mass, rates "
+                f"scaled to the full step (DSS not included)")
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    t_all = time.perf_counter()
+    smp = OracleSampler(threads)
+    for _ in range(args.warmup):
+        smp.time_once()
+    smp.reset()
+    for _ in range(args.steps):
+        smp.time_once()
+    t_step, nu = smp.full_step_estimate()
+    value = nu / t_step / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "FP64 operator sweep, deformed unit cube (amp 0.1), stored geometry, "
+                               "Laplace+mass at Q2/48^3, Q3/96^3, Q7/32^3, FE_ASSEMBLE",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": smp.describe()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(time.perf_counter() - t_all, 2),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("fe_apply_kernel.cuh", "fe_internal.h", "fe_apply_launch.cuh"):
+        with open(os.path.join(ROOT, "paper_2607_02335_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_sha") != kernel_source_sha():
+        return None
+    return d.get("bytes_per_launch")
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2607_02335_gb300 import fe
+    from paper_2607_02335_gb300 import synth as S
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    sweep = [(2, 6), (3, 6), (7, 3)] if args.small else SWEEP
+    cases = []  # (mesh, x, y, op, p, m)
+    meshes = []
+    for p, m in sweep:
+        gm = fe.Mesh(m, p, deform_amp=AMP, device=dev)
+        x = gm.gather(S.primal_unique(m, p, seed=0))
+        meshes.append((gm, x, p, m))
+        for op in (fe.FE_LAPLACE, fe.FE_MASS):
+            cases.append((gm, x, gm.empty(fe.FE_F64), op, p, m))
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        for gm, x, y, op, p, m in cases:
+            fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, fe.FE_ASSEMBLE, stream)
+
+    units_per_step = sum(gm.unique_dofs for gm, _, _, _, _, _ in cases)
+    launches_per_step = len(cases) * 4  # volumetric kernel + 3 DSS axis passes
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    gpu_id = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    sampler = ClockSampler(f"GPU-{gpu_id}" if gpu_id else str(dev))
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = units_per_step * world * args.steps / (total_ms * 1e-3) / 1e9
+
+    # per-case breakdown: assembled apply and the volumetric kernel alone (flushed, averaged)
+    peak, peak_kind = load_peaks()
+    reps = max(5, min(args.steps, 20))
+    per_case = []
+    for gm, x, y, op, p, m in cases:
+        res = {}
+        for flags, key in ((fe.FE_ASSEMBLE, "assembled_ms"), (0, "volumetric_ms")):
+            tot = 0.0
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, flags, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            res[key] = tot / reps
+        ncw = gm.cellwise_len
+        alg_bytes = ncw * (16 + GEO_BYTES[op])
+        vol_gbs = alg_bytes / (res["volumetric_ms"] * 1e-3) / 1e9
+        per_case.append({
+            "op": "laplace" if op == fe.FE_LAPLACE else "mass", "degree": p, "cells": f"{m}^3",
+            "cellwise_dofs": ncw, "unique_dofs": gm.unique_dofs,
+            "assembled_ms": round(res["assembled_ms"], 4), "volumetric_ms": round(res["volumetric_ms"], 4),
+            "gdofs_unique_assembled": round(gm.unique_dofs / (res["assembled_ms"] * 1e-3) / 1e9, 3),
+            "gdofs_cellwise_volumetric": round(ncw / (res["volumetric_ms"] * 1e-3) / 1e9, 3),
+            "volumetric_alg_bytes": alg_bytes, "volumetric_gbs": round(vol_gbs, 1),
+            "volumetric_hbm_frac": round(vol_gbs / peak, 4),
+        })
+    dom = max(per_case, key=lambda c: c["volumetric_ms"])
+    achieved = dom["volumetric_gbs"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": committed_traffic(),
+                "kernel": f"k_apply<{dom['degree'] + 1},dw,{dom['op']},stored>",
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                "alg_bytes_per_launch": dom["volumetric_alg_bytes"]}
+
+    # end to end through the C ABI with host buffers: pinned x in, y out, every step
+    hx = {}
+    for gm, x, p, m in meshes:
+        hx[id(gm)] = torch.empty(gm.cellwise_len, dtype=torch.float64, pin_memory=True)
+        hx[id(gm)].copy_(x.cpu())
+    hy = [torch.empty(gm.cellwise_len, dtype=torch.float64, pin_memory=True) for gm, *_ in cases]
+    h2d = sum(gm.cellwise_len * 8 for gm, *_ in meshes)
+    d2h = sum(gm.cellwise_len * 8 for gm, *_ in cases)
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for gm, x, p, m in meshes:
+            x.copy_(hx[id(gm)], non_blocking=True)
+        for (gm, x, y, op, p, m), hyk in zip(cases, hy):
+            fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, fe.FE_ASSEMBLE, stream)
+            hyk.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = units_per_step * world / e2e_s / 1e9
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "FP64 operator sweep, deformed unit cube (amp 0.1), stored geometry, "
+                               "Laplace+mass at " + ", ".join(f"Q{p}/{m}^3" for p, m in sweep)
+                               + ", FE_ASSEMBLE (volumetric apply + structured DSS)",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "arithmetic": "double-word (hi+lo float) on the FP32 pipe, FP64 I/O",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "per_case": per_case,
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        smp = OracleSampler(threads)
+        smp.time_once()
+        smp.reset()
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 10.0:
+            smp.time_once()
+        t_cpu, nu = smp.full_step_estimate()
+        line["cpu_baseline"] = {"value": round(nu / t_cpu / 1e9, 6), "unit": UNIT, "cores": threads,
+                                "kind": "oracle", "sample": smp.describe()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    run_ours(args, rank, world)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * fe.h -- C ABI of libfe: matrix-free high-order finite elements in persistent cell-wise storage
+ * on one GB300 GPU (hand-written CUDA for sm_103a).
+ *
+ * Method: "Coalesced Matrix-Free Finite Elements in Cell-Wise Storage".  Every field lives
+ * persistently in the redundant cell-wise representation V_cell (primal) / V_cell* (dual)
+ * (Sec. 2.2); the local operator A : V_cell -> V_cell* is applied cell by cell with sum
+ * factorization (Sec. 2.3, Eq. (mass_operator), Eq. (laplace_operator)); continuity is restored
+ * only by the direct stiffness summation S = G I_Riesz G^T (Sec. 3.3, Eq. (dss_operator)),
+ * realised as dimension-split one-to-one face exchanges without atomics (Sec. 4.1, Algorithm
+ * "Dimensionally-Split Structured Summation"); Krylov solves run on cell-wise data (Sec. 3.2,
+ * Algorithm "Communication-Free (Flexible) PCG").
+ *
+ * Conventions
+ *  - Mesh: mx*my*mz hexahedra of the unit cube, deformed by
+ *    Phi(X) = X + deform_amp * sin(pi X) sin(pi Y) sin(pi Z) * (1,1,1), sampled at the
+ *    Gauss-Lobatto-Legendre (GLL) nodes of every cell and interpolated isoparametrically with
+ *    Q_p; n = p+1 GLL nodes and n Gauss points per direction.
+ *  - Cell-wise layout (layout_id 0): cell-major, cells in lexicographic order
+ *    (cell = (cz*my + cy)*mx + cx), each cell's n^3 values contiguous with local node
+ *    (i,j,k) at (k*n + j)*n + i.  Element e of a cell-wise vector is cell e / n^3, node e % n^3.
+ *  - Vectors are caller-owned DEVICE memory of `cellwise_len` elements: double for FE_F64,
+ *    float for the other precisions.  Pointers must be 16-byte aligned.  Library-owned state
+ *    (geometry, tables, solver workspaces) lives inside the opaque fe_mesh / fe_server objects.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on it
+ *    unless stated otherwise.
+ *  - Errors: every call returns an fe_status; fe_last_error() gives a thread-local message.
+ *    No exception crosses the ABI.  A CUDA error from a launch is reported as FE_ERR_CUDA.
+ *  - Dirichlet (the paper has no boundary conditions; reading used here): when the mesh is
+ *    created with dirichlet = 1, rows and columns of boundary nodes are masked, i.e. the
+ *    operator is A_D = R^T R A_CG R^T R; every copy of a boundary node is zero in the output of
+ *    fe_apply, and the Jacobi diagonal is 1 there.
+ */
+#ifndef LIBFE_FE_H
+#define LIBFE_FE_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FE_OK = 0,
+  FE_ERR_INVALID = 1,       /* bad argument: null/misaligned pointer, degree outside [1,7], ... */
+  FE_ERR_OOM = 2,           /* device allocation failed, or request over the memory budget */
+  FE_ERR_CUDA = 3,          /* CUDA runtime or launch error */
+  FE_ERR_NOT_CONVERGED = 4, /* CG reached maxit */
+  FE_ERR_BREAKDOWN = 5,     /* CG breakdown: <q,p> <= 0 or a non-finite scalar */
+  FE_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+  FE_ERR_BUSY = 7           /* fe_serve_poll: the request is still pending */
+} fe_status;
+
+typedef enum { FE_LAPLACE = 0, FE_MASS = 1 } fe_op;
+
+/* Arithmetic of a call.  FE_F64: double storage, FP64-accurate arithmetic (see FE_NATIVE_F64).
+ * FE_F32: float storage and float arithmetic. */
+typedef enum { FE_F64 = 0, FE_F32 = 1, FE_BF16_F32ACC = 2, FE_F16_F32ACC = 3 } fe_prec;
+
+/* Geometry representation (Sec. 2.3 and Sec. 5.3: "per-quadrature-point Jacobians"):
+ *  STORED    -- w_q detJ J^{-1}J^{-T} (6 symmetric entries, Laplace) and w_q detJ (mass) per
+ *               quadrature point, precomputed by fe_mesh_create;
+ *  RECOMPUTE -- only the cell-wise nodal coordinates are stored; J is formed on the fly;
+ *  AFFINE    -- undeformed Cartesian mesh (deform_amp must be 0): one diagonal J for all cells,
+ *               the paper's "scalar h" setting. */
+enum { FE_GEOM_STORED = 0, FE_GEOM_RECOMPUTE = 1, FE_GEOM_AFFINE = 2 };
+
+/* fe_apply flags */
+#define FE_ASSEMBLE 1u   /* y = S(A x): continuous output equal to G A_D x_glob when x = G x_glob */
+#define FE_NATIVE_F64 2u /* FE_F64 only: use the FP64 pipe instead of double-float arithmetic on
+                            the FP32 pipe (reference variant; slow on GB300) */
+
+typedef struct {
+  int mx, my, mz;    /* cells per direction, each >= 1 */
+  int degree;        /* p in [1, 7] */
+  double deform_amp; /* amplitude of the sine deformation (0 = affine) */
+  int geom_mode;     /* FE_GEOM_* */
+  int dirichlet;     /* 1 = homogeneous Dirichlet on the whole boundary */
+  int device;        /* CUDA device ordinal */
+} fe_mesh_desc;
+
+typedef struct {
+  long long n_cells;        /* mx*my*mz */
+  long long nodes_per_cell; /* (p+1)^3 */
+  long long cellwise_len;   /* n_cells * nodes_per_cell (no padding in layout 0) */
+  long long unique_dofs;    /* (mx p + 1)(my p + 1)(mz p + 1), Sec. 5 closed form */
+  int layout_id;            /* 0 = cell-major lexicographic (see above) */
+} fe_layout;
+
+typedef struct fe_mesh fe_mesh;
+typedef struct fe_server fe_server;
+
+/* Build a mesh: 1D tables, geometry kernel on `stream` (Sec. 2.3 geometry, Sec. 5.3).  The call
+ * returns once the geometry is built (it synchronizes `stream`).  *out is library-owned; free it
+ * with fe_mesh_destroy.  FE_ERR_INVALID for degree outside [1,7], non-positive cell counts,
+ * geom_mode AFFINE with deform_amp != 0; FE_ERR_OOM if device memory runs out. */
+fe_status fe_mesh_create(const fe_mesh_desc* desc, void* stream, fe_mesh** out);
+fe_status fe_mesh_destroy(fe_mesh* mesh);
+fe_status fe_mesh_layout(const fe_mesh* mesh, fe_layout* out);
+
+/* Gather G (Sec. 2.1): x_cell = G x_unique.  Test and input helper: x_unique_host is a HOST
+ * array of unique_dofs doubles in lexicographic global order (gz*Ny + gy)*Nx + gx,
+ * Nx = mx p + 1; x_cell_dev is a device array of cellwise_len doubles.  Synchronous. */
+fe_status fe_gather(const fe_mesh* mesh, const double* x_unique_host, double* x_cell_dev,
+                    void* stream);
+
+/* Local operator apply (Sec. 3.1 "local operator"; Eq. (mass_operator) / (laplace_operator)
+ * with per-quadrature-point geometry): y_K = A_K x_K for every cell K (dual, unassembled).
+ * With FE_ASSEMBLE the structured DSS follows (Sec. 4.1): y = S(A x), continuous.  x and y must
+ * not overlap.  prec FE_BF16_F32ACC / FE_F16_F32ACC return FE_ERR_INVALID (not provided). */
+fe_status fe_apply(const fe_mesh* mesh, fe_op op, fe_prec prec, const void* x, void* y,
+                   unsigned flags, void* stream);
+
+/* Direct stiffness summation S = G I_Riesz G^T (Eq. (dss_operator)), structured
+ * dimension-split passes (Algorithm "Dimensionally-Split Structured Summation"):
+ * z = S r.  In place (z == r) is allowed.  prec FE_F64 (double) or FE_F32 (float). */
+fe_status fe_dss(const fe_mesh* mesh, fe_prec prec, const void* r, void* z, void* stream);
+
+/* Jacobi diagonal D_cell = diag(G d), d = diag(A_D) (Sec. 3.3): d_cell is a device array of
+ * cellwise_len doubles; every copy of a node holds the assembled diagonal; 1 on Dirichlet nodes. */
+fe_status fe_diag(const fe_mesh* mesh, fe_op op, double* d_cell, void* stream);
+
+/* Duality pairing <a, b> = sum_e a_e b_e over all cell-wise entries (Lemma "Duality Pairing
+ * Identity": pairing a dual with a continuous primal vector gives the assembled inner
+ * product).  FP64 accumulation, fixed reduction order (bitwise reproducible).  result_dev is a
+ * device pointer to one double.  prec FE_F64 (double inputs) or FE_F32 (float inputs). */
+fe_status fe_pairing(const fe_mesh* mesh, fe_prec prec, const void* a, const void* b,
+                     double* result_dev, void* stream);
+
+/* Conjugate gradients on cell-wise data (Algorithm "Communication-Free (Flexible) PCG") with the
+ * Jacobi preconditioner P = D_cell^{-1} S.  Convergence (unspecified in the paper; reading):
+ * ||G^T r||_2 / ||G^T b||_2 <= rtol over free nodes, evaluated on the device as
+ * sum_e (S r)_e^2 / mult_e.  mixed = 0: FP64 throughout.  mixed = FE_F32: FP64 iterative
+ * refinement (r = b - A x in FP64, x += d in FP64) around an FP32 inner PCG solved to
+ * inner_rtol.  flexible = 1 uses the FCG beta.  b (dual) and x (primal, in/out) are device
+ * arrays of cellwise_len doubles.  Synchronous: returns after the solve. */
+typedef struct {
+  double rtol;       /* relative residual target */
+  int maxit;         /* iteration cap (inner iterations in total for mixed) */
+  int mixed;         /* 0 = FP64, FE_F32 = FP32 inner solve under FP64 refinement */
+  int flexible;      /* 1 = FCG beta */
+  double inner_rtol; /* mixed only: relative reduction per inner solve */
+} fe_cg_opts;
+typedef struct {
+  int iters;        /* total CG iterations (inner iterations for mixed) */
+  int outer_iters;  /* refinement steps (mixed), 1 otherwise */
+  double rel_res;   /* final ||G^T r|| / ||G^T b|| in FP64 */
+  fe_status status; /* FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN */
+} fe_cg_result;
+fe_status fe_cg_solve(const fe_mesh* mesh, const double* b, double* x, const fe_cg_opts* opts,
+                      fe_cg_result* res, void* stream);
+
+/* Thread-local message describing the last error of this thread ("" if none). */
+const char* fe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

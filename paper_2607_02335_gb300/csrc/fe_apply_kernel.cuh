@@ -1,0 +1,293 @@
+// fe_apply_kernel.cuh -- sum-factorized cell-wise operator apply (one template, three
+// arithmetics).
+//
+// Per cell K the kernel computes y_K = A_K x_K, the unassembled dual output of the local
+// operator (Sec. 3.1), with the sum factorization of Sec. 2.3 extended to general
+// per-quadrature-point geometry:
+//   Laplace  y_K = (V^T x V^T x V^T) [ sum_a D_a^T ( G (D_x u_q, D_y u_q, D_z u_q) )_a ],
+//            u_q = (V x V x V) x_K,  G = w_q detJ J^{-1} J^{-T}    (Eq. (laplace_operator))
+//   mass     y_K = (V^T x V^T x V^T) (w_q detJ) (V x V x V) x_K   (Eq. (mass_operator))
+// V interpolates from the n GLL nodes to the n Gauss points of a direction, D is the
+// collocation derivative at the Gauss points.
+//
+// Thread mapping.  A CTA owns CPB consecutive cells and n^2 threads per cell.  Thread t of a cell
+// owns one 1D line of the cell's n^3 tensor per phase: the z-line (i,j) = (t % n, t / n) while
+// data sits in registers (global load/store, pointwise geometry, z sweeps), the x-line
+// (j,k) = (t % n, t / n) and the y-line (i,k) = (t % n, t / n) for the x and y sweeps, which
+// read and write the cell's tile in shared memory.  Every contraction loop is unrolled with
+// compile-time indices, so the 1D matrices (kernel parameters) are read from the constant bank
+// as instruction operands.  Rows of the shared-memory tile are padded to n+1 entries, which makes
+// the x- and y-line accesses of a warp bank-conflict free for 4-byte planes (double-word values
+// are kept as separate hi and lo float planes).
+#pragma once
+#include "fe_internal.h"
+
+template <int N>
+struct Cfg {
+  static constexpr int N2 = N * N;
+  static constexpr int N3 = N * N * N;
+  static constexpr int CPB = (256 / N2) > 0 ? (256 / N2) : 1;  // cells per CTA
+  static constexpr int THREADS = CPB * N2;
+  static constexpr int RS = N + 1;      // padded row stride in shared memory
+  static constexpr int PS = N * RS;     // plane stride
+  static constexpr int CS = N * PS;     // cell stride
+  static constexpr int TILE = CPB * CS; // elements per array per CTA
+};
+
+// shared-memory view of one array of the tile
+template <class V>
+struct Sm;
+template <>
+struct Sm<double> {
+  double* p;
+  __device__ __forceinline__ Sm(unsigned char* base, int, int arr, int tile)
+      : p(reinterpret_cast<double*>(base) + (size_t)arr * tile) {}
+  __device__ __forceinline__ double get(int e) const { return p[e]; }
+  __device__ __forceinline__ void put(int e, double v) const { p[e] = v; }
+  static constexpr int BYTES = 8;
+};
+template <>
+struct Sm<float> {
+  float* p;
+  __device__ __forceinline__ Sm(unsigned char* base, int, int arr, int tile)
+      : p(reinterpret_cast<float*>(base) + (size_t)arr * tile) {}
+  __device__ __forceinline__ float get(int e) const { return p[e]; }
+  __device__ __forceinline__ void put(int e, float v) const { p[e] = v; }
+  static constexpr int BYTES = 4;
+};
+template <>
+struct Sm<dw> {
+  float* h;
+  float* l;
+  __device__ __forceinline__ Sm(unsigned char* base, int narr, int arr, int tile) {
+    float* f = reinterpret_cast<float*>(base);
+    h = f + (size_t)arr * tile;
+    l = f + (size_t)(narr + arr) * tile;
+  }
+  __device__ __forceinline__ dw get(int e) const { return {h[e], l[e]}; }
+  __device__ __forceinline__ void put(int e, dw v) const {
+    h[e] = v.h;
+    l[e] = v.l;
+  }
+  static constexpr int BYTES = 8;
+};
+
+// out[q] = sum_r M[q][r] in[r]
+template <int N, class V>
+__device__ __forceinline__ void mv(const V (&M)[N][N], const V (&in)[N], V (&out)[N]) {
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    V acc = NT<V>::zero();
+#pragma unroll
+    for (int r = 0; r < N; ++r) acc = NT<V>::mac(acc, M[q][r], in[r]);
+    out[q] = NT<V>::fin(acc);
+  }
+}
+// out[r] = sum_q M[q][r] in[q]
+template <int N, class V>
+__device__ __forceinline__ void mtv(const V (&M)[N][N], const V (&in)[N], V (&out)[N]) {
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    V acc = NT<V>::zero();
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc = NT<V>::mac(acc, M[q][r], in[q]);
+    out[r] = NT<V>::fin(acc);
+  }
+}
+
+// line access in the padded tile: x-line (a=j, b=k), y-line (a=i, b=k), z-line (a=i, b=j)
+template <int N>
+__device__ __forceinline__ int xl(int a, int b, int r) { return b * Cfg<N>::PS + a * Cfg<N>::RS + r; }
+template <int N>
+__device__ __forceinline__ int yl(int a, int b, int r) { return b * Cfg<N>::PS + r * Cfg<N>::RS + a; }
+template <int N>
+__device__ __forceinline__ int zl(int a, int b, int r) { return r * Cfg<N>::PS + b * Cfg<N>::RS + a; }
+
+// in-place 1D sweep of every line along one axis of the tile, by the line-owning thread
+template <int N, class V, int AX, bool TR>
+__device__ __forceinline__ void tile_sweep(const Sm<V>& s, int cbase, int a, int b,
+                                           const V (&M)[N][N]) {
+  V in[N], out[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+    in[r] = s.get(cbase + (AX == 0 ? xl<N>(a, b, r) : yl<N>(a, b, r)));
+  if (TR)
+    mtv<N, V>(M, in, out);
+  else
+    mv<N, V>(M, in, out);
+#pragma unroll
+  for (int r = 0; r < N; ++r) s.put(cbase + (AX == 0 ? xl<N>(a, b, r) : yl<N>(a, b, r)), out[r]);
+}
+
+template <int N, class V>
+struct ApplyArgs {
+  const typename NT<V>::SV* x;
+  typename NT<V>::SV* y;
+  const typename NT<V>::GV* geo;  // [cell][7][N3]: w detJ J^-1 J^-T (xx,yy,zz,xy,xz,yz), w detJ
+  long long ncells;
+  int mx, my, mz;
+  int dirichlet;
+  V aff[4];  // affine mode: detJ/h_x^2, detJ/h_y^2, detJ/h_z^2, detJ
+  Tab1D<N, V> tab;
+};
+
+enum { GEOM_STORED_K = 0, GEOM_AFFINE_K = 2 };
+
+template <int N, class V, int OP, int GEOM>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+    k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
+  using T = NT<V>;
+  using C = Cfg<N>;
+  constexpr int N2 = C::N2, N3 = C::N3;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NARR = (OP == FE_LAPLACE) ? 3 : 1;
+  const Sm<V> s0(smraw, NARR, 0, C::TILE);
+  const Sm<V> s1(smraw, NARR, NARR > 1 ? 1 : 0, C::TILE);
+  const Sm<V> s2(smraw, NARR, NARR > 2 ? 2 : 0, C::TILE);
+
+  const int t = threadIdx.x;
+  const int cl = t / N2;
+  const int lt = t - cl * N2;
+  const int la = lt % N, lb = lt / N;  // line coordinates (a, b) of this thread
+  const int cb = cl * C::CS;           // this cell's offset in the tile
+  const long long cell = (long long)blockIdx.x * C::CPB + cl;
+  const bool active = cell < a.ncells;
+  const long long gbase = cell * N3;
+
+  // Dirichlet masks of this thread's z-line (i = la, j = lb)
+  bool bnd_line = false;  // the whole z-line lies on the x- or y-boundary
+  bool bnd_k0 = false, bnd_k1 = false;
+  if (a.dirichlet && active) {
+    const int cx = (int)(cell % a.mx);
+    const int cy = (int)((cell / a.mx) % a.my);
+    const int cz = (int)(cell / ((long long)a.mx * a.my));
+    bnd_line = (cx == 0 && la == 0) || (cx == a.mx - 1 && la == N - 1) || (cy == 0 && lb == 0) ||
+               (cy == a.my - 1 && lb == N - 1);
+    bnd_k0 = (cz == 0);
+    bnd_k1 = (cz == a.mz - 1);
+  }
+  auto masked = [&](int k) { return bnd_line || (k == 0 && bnd_k0) || (k == N - 1 && bnd_k1); };
+
+  // ---- load x (z-line owner, coalesced) and interpolate along z in registers
+  V u[N], w[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    V v = active ? T::load_stream(a.x + gbase + k * N2 + lt) : T::zero();
+    u[k] = masked(k) ? T::zero() : v;
+  }
+  mv<N, V>(a.tab.V_, u, w);
+#pragma unroll
+  for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
+  __syncthreads();
+  tile_sweep<N, V, 0, false>(s0, cb, la, lb, a.tab.V_);  // x
+  __syncthreads();
+  tile_sweep<N, V, 1, false>(s0, cb, la, lb, a.tab.V_);  // y
+  __syncthreads();
+  // s0 now holds u at the Gauss points
+
+  if constexpr (OP == FE_LAPLACE) {
+    // ---- reference gradient at the Gauss points (collocation derivative)
+    {
+      V in[N], out[N];
+#pragma unroll
+      for (int r = 0; r < N; ++r) in[r] = s0.get(cb + xl<N>(la, lb, r));
+      mv<N, V>(a.tab.D_, in, out);
+#pragma unroll
+      for (int r = 0; r < N; ++r) s1.put(cb + xl<N>(la, lb, r), out[r]);
+#pragma unroll
+      for (int r = 0; r < N; ++r) in[r] = s0.get(cb + yl<N>(la, lb, r));
+      mv<N, V>(a.tab.D_, in, out);
+#pragma unroll
+      for (int r = 0; r < N; ++r) s2.put(cb + yl<N>(la, lb, r), out[r]);
+#pragma unroll
+      for (int r = 0; r < N; ++r) in[r] = s0.get(cb + zl<N>(la, lb, r));
+      mv<N, V>(a.tab.D_, in, u);  // u := d/dz along the z-line
+    }
+    __syncthreads();
+    // ---- pointwise metric: g = G grad u (z-line owner)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int e = cb + zl<N>(la, lb, k);
+      const V dx = s1.get(e), dy = s2.get(e), dz = u[k];
+      V gxx, gyy, gzz, gxy, gxz, gyz;
+      if constexpr (GEOM == GEOM_AFFINE_K) {
+        const int q1 = la, q2 = lb;
+        const V wq = T::mul(T::mul(a.tab.W_[q1], a.tab.W_[q2]), a.tab.W_[k]);
+        gxx = T::mul(wq, a.aff[0]);
+        gyy = T::mul(wq, a.aff[1]);
+        gzz = T::mul(wq, a.aff[2]);
+        V gx = T::mul(gxx, dx), gy = T::mul(gyy, dy), gz = T::mul(gzz, dz);
+        s1.put(e, gx);
+        s2.put(e, gy);
+        u[k] = gz;
+      } else {
+        const typename NT<V>::GV* gp = a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + k * N2 + lt;
+        if (active) {
+          gxx = T::geo(gp + 0 * N3);
+          gyy = T::geo(gp + 1 * N3);
+          gzz = T::geo(gp + 2 * N3);
+          gxy = T::geo(gp + 3 * N3);
+          gxz = T::geo(gp + 4 * N3);
+          gyz = T::geo(gp + 5 * N3);
+        } else {
+          gxx = gyy = gzz = gxy = gxz = gyz = T::zero();
+        }
+        V gx = T::zero(), gy = T::zero(), gz = T::zero();
+        gx = T::fin(T::mac(T::mac(T::mac(gx, gxx, dx), gxy, dy), gxz, dz));
+        gy = T::fin(T::mac(T::mac(T::mac(gy, gxy, dx), gyy, dy), gyz, dz));
+        gz = T::fin(T::mac(T::mac(T::mac(gz, gxz, dx), gyz, dy), gzz, dz));
+        s1.put(e, gx);
+        s2.put(e, gy);
+        u[k] = gz;
+      }
+    }
+    __syncthreads();
+    // ---- transposed derivative: t = D^T gx (x) + D^T gy (y) + D^T gz (z)
+    tile_sweep<N, V, 0, true>(s1, cb, la, lb, a.tab.D_);
+    tile_sweep<N, V, 1, true>(s2, cb, la, lb, a.tab.D_);
+    mtv<N, V>(a.tab.D_, u, w);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int e = cb + zl<N>(la, lb, k);
+      u[k] = T::add(T::add(w[k], s1.get(e)), s2.get(e));
+    }
+  } else {
+    // ---- mass: pointwise w detJ
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const V uq = s0.get(cb + zl<N>(la, lb, k));
+      V jw;
+      if constexpr (GEOM == GEOM_AFFINE_K) {
+        jw = T::mul(T::mul(T::mul(a.tab.W_[la], a.tab.W_[lb]), a.tab.W_[k]), a.aff[3]);
+      } else {
+        jw = active ? T::geo(a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + 6 * N3 + k * N2 + lt)
+                    : T::zero();
+      }
+      u[k] = T::mul(jw, uq);
+    }
+  }
+
+  // ---- transposed interpolation: z in registers, then x and y in the tile
+  mtv<N, V>(a.tab.V_, u, w);
+#pragma unroll
+  for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
+  __syncthreads();
+  tile_sweep<N, V, 0, true>(s0, cb, la, lb, a.tab.V_);
+  __syncthreads();
+  tile_sweep<N, V, 1, true>(s0, cb, la, lb, a.tab.V_);
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      V v = s0.get(cb + zl<N>(la, lb, k));
+      if (masked(k)) v = T::zero();
+      T::store(a.y + gbase + k * N2 + lt, v);
+    }
+  }
+}
+
+template <int N, class V>
+inline size_t apply_smem_bytes(int op) {
+  return (size_t)((op == FE_LAPLACE) ? 3 : 1) * Cfg<N>::TILE * Sm<V>::BYTES;
+}

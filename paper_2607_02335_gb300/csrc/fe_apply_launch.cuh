@@ -1,0 +1,88 @@
+// fe_apply_launch.cuh -- host launchers of the apply kernels for one arithmetic V.
+#pragma once
+#include <cstring>
+
+#include "fe_apply_kernel.cuh"
+
+template <class V>
+V fe_cast(double v);
+template <>
+inline double fe_cast<double>(double v) { return v; }
+template <>
+inline float fe_cast<float>(double v) { return (float)v; }
+template <>
+inline dw fe_cast<dw>(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+template <int N, class V>
+Tab1D<N, V> make_tab(const HostTab& h) {
+  Tab1D<N, V> t;
+  for (int a = 0; a < N; ++a) {
+    t.W_[a] = fe_cast<V>(h.w[a]);
+    for (int b = 0; b < N; ++b) {
+      t.V_[a][b] = fe_cast<V>(h.V[a][b]);
+      t.D_[a][b] = fe_cast<V>(h.D[a][b]);
+    }
+  }
+  return t;
+}
+
+template <int N, class V, int OP, int GEOM>
+static fe_status launch_one(const ApplyArgs<N, V>& a, cudaStream_t st) {
+  using C = Cfg<N>;
+  const size_t smem = apply_smem_bytes<N, V>(OP);
+  auto kern = k_apply<N, V, OP, GEOM>;
+  static bool attr_done = false;  // one attribute call per instantiation (and device)
+  if (!attr_done) {
+    FE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "apply smem attribute");
+    attr_done = true;
+  }
+  const long long blocks = (a.ncells + C::CPB - 1) / C::CPB;
+  if (blocks > 0) kern<<<(unsigned)blocks, C::THREADS, smem, st>>>(a);
+  return fe_cuda_check(cudaGetLastError(), "apply kernel launch");
+}
+
+template <int N, class V>
+static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* geo) {
+  const fe_mesh* m = L.m;
+  ApplyArgs<N, V> a;
+  std::memset(&a, 0, sizeof(a));
+  a.x = static_cast<const typename NT<V>::SV*>(L.x);
+  a.y = static_cast<typename NT<V>::SV*>(L.y);
+  a.geo = geo;
+  a.ncells = m->ncells;
+  a.mx = m->d.mx;
+  a.my = m->d.my;
+  a.mz = m->d.mz;
+  a.dirichlet = m->d.dirichlet;
+  const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / m->d.mz, det = hx * hy * hz;
+  a.aff[0] = fe_cast<V>(det / (hx * hx));
+  a.aff[1] = fe_cast<V>(det / (hy * hy));
+  a.aff[2] = fe_cast<V>(det / (hz * hz));
+  a.aff[3] = fe_cast<V>(det);
+  a.tab = make_tab<N, V>(m->tab);
+  const bool affine = m->d.geom_mode == FE_GEOM_AFFINE;
+  if (L.op == FE_LAPLACE)
+    return affine ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K>(a, L.st)
+                  : launch_one<N, V, FE_LAPLACE, GEOM_STORED_K>(a, L.st);
+  return affine ? launch_one<N, V, FE_MASS, GEOM_AFFINE_K>(a, L.st)
+                : launch_one<N, V, FE_MASS, GEOM_STORED_K>(a, L.st);
+}
+
+template <class V>
+static fe_status launch_apply_v(const ApplyLaunch& L, const typename NT<V>::GV* geo) {
+  switch (L.m->n) {
+    case 2: return launch_apply_n<2, V>(L, geo);
+    case 3: return launch_apply_n<3, V>(L, geo);
+    case 4: return launch_apply_n<4, V>(L, geo);
+    case 5: return launch_apply_n<5, V>(L, geo);
+    case 6: return launch_apply_n<6, V>(L, geo);
+    case 7: return launch_apply_n<7, V>(L, geo);
+    case 8: return launch_apply_n<8, V>(L, geo);
+  }
+  fe_set_error("apply: unsupported n = %d", L.m->n);
+  return FE_ERR_INVALID;
+}

@@ -1,0 +1,236 @@
+// fe_internal.h -- internal types of libfe (not part of the ABI).
+//
+// Number types.  The FP64 path of the library computes in double-word ("double-float")
+// arithmetic on the FP32 pipe: a value is an unevaluated sum hi + lo of two floats (Dekker 1971;
+// error-free TwoSum/TwoProd as in Joldes, Muller, Popescu, "Tight and rigorous error bounds for
+// basic building blocks of double-word arithmetic", ACM TOMS 2017).  GB300 executes FP64 FMAs at
+// about 1/70 of its FP32 rate, so this is the arithmetic that lets an FP64-accurate operator get
+// near the memory roofline.  The same sweep code is instantiated for `double` (the FP64 pipe,
+// kept as a cross-check variant) and for `float` (the FP32 path of mixed precision).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fe.h"
+
+#define FE_MAXN 8
+
+// ---------------------------------------------------------------------------------------------
+// double-word arithmetic
+// ---------------------------------------------------------------------------------------------
+struct dw {
+  float h, l;
+};
+
+// All double-word primitives use the _rn intrinsics so that the compiler never contracts a
+// product and a sum into one FMA, which would break the error-free transformations.
+__device__ __forceinline__ dw dw_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+// unnormalised accumulator acc + c*v (hi part exact through TwoSum, low parts summed in float)
+__device__ __forceinline__ dw dw_mac(dw acc, dw c, dw v) {
+  float p = __fmul_rn(c.h, v.h);
+  float e = __fmaf_rn(c.h, v.h, -p);
+  e = __fmaf_rn(c.h, v.l, e);
+  e = __fmaf_rn(c.l, v.h, e);
+  dw s = dw_two_sum(acc.h, p);
+  return {s.h, __fadd_rn(acc.l, __fadd_rn(s.l, e))};
+}
+__device__ __forceinline__ dw dw_norm(dw a) { return dw_fast_two_sum(a.h, a.l); }
+__device__ __forceinline__ dw dw_add(dw a, dw b) {
+  dw s = dw_two_sum(a.h, b.h);
+  return dw_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dw dw_mul(dw a, dw b) {
+  float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return dw_fast_two_sum(p, e);
+}
+
+// binary64 -> double-word by bit manipulation on the integer pipe (FP64<->FP32 conversions run
+// at the FP64 rate on GB300).  hi = x truncated to 24 significant bits, lo = the remaining 29
+// bits rounded to float.  Exact range 2^-74 <= |x| < 2^128; other values take the FP64 path.
+__device__ __forceinline__ dw dw_from_double(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+  if (e - 949u <= 201u) {
+    unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    float hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+    float lo = __fmul_rn(__uint2float_rn((unsigned)b & 0x1FFFFFFFu), __uint_as_float((e - 948u) << 23));
+    lo = __uint_as_float(__float_as_uint(lo) | sign);
+    return {hi, lo};
+  }
+  float hi = __double2float_rn(x);
+  float lo = __double2float_rn(x - (double)hi);
+  return {hi, lo};
+}
+// float -> binary64 exactly for normal floats by bit manipulation; zero and subnormal -> 0.
+__device__ __forceinline__ double f2d_bits(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned e = (u >> 23) & 0xFFu;
+  if (e - 1u < 254u) {
+    unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                           ((unsigned long long)(e + 896u) << 52) |
+                           ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+  }
+  if (e == 0u) return 0.0;
+  return (double)f;  // inf / nan
+}
+__device__ __forceinline__ double dw_to_double(dw a) { return f2d_bits(a.h) + f2d_bits(a.l); }
+
+// ---------------------------------------------------------------------------------------------
+// number traits: value type V, storage type of vectors (SV) and of geometry (GV)
+// ---------------------------------------------------------------------------------------------
+template <class V>
+struct NT;
+
+template <>
+struct NT<double> {
+  using SV = double;
+  using GV = double;
+  __device__ static __forceinline__ double zero() { return 0.0; }
+  __device__ static __forceinline__ double mac(double a, double c, double v) { return fma(c, v, a); }
+  __device__ static __forceinline__ double fin(double a) { return a; }
+  __device__ static __forceinline__ double mul(double a, double b) { return a * b; }
+  __device__ static __forceinline__ double add(double a, double b) { return a + b; }
+  __device__ static __forceinline__ double neg(double a) { return -a; }
+  __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
+  __device__ static __forceinline__ double load_stream(const double* p) { return __ldcs(p); }
+  __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
+  __device__ static __forceinline__ double geo(const double* p) { return __ldcs(p); }
+};
+
+template <>
+struct NT<float> {
+  using SV = float;
+  using GV = float;
+  __device__ static __forceinline__ float zero() { return 0.0f; }
+  __device__ static __forceinline__ float mac(float a, float c, float v) { return fmaf(c, v, a); }
+  __device__ static __forceinline__ float fin(float a) { return a; }
+  __device__ static __forceinline__ float mul(float a, float b) { return a * b; }
+  __device__ static __forceinline__ float add(float a, float b) { return a + b; }
+  __device__ static __forceinline__ float neg(float a) { return -a; }
+  __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
+  __device__ static __forceinline__ float load_stream(const float* p) { return __ldcs(p); }
+  __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
+  __device__ static __forceinline__ float geo(const float* p) { return __ldcs(p); }
+};
+
+template <>
+struct NT<dw> {
+  using SV = double;
+  using GV = float2;
+  __device__ static __forceinline__ dw zero() { return {0.0f, 0.0f}; }
+  __device__ static __forceinline__ dw mac(dw a, dw c, dw v) { return dw_mac(a, c, v); }
+  __device__ static __forceinline__ dw fin(dw a) { return dw_norm(a); }
+  __device__ static __forceinline__ dw mul(dw a, dw b) { return dw_mul(a, b); }
+  __device__ static __forceinline__ dw add(dw a, dw b) { return dw_add(a, b); }
+  __device__ static __forceinline__ dw neg(dw a) { return {-a.h, -a.l}; }
+  __device__ static __forceinline__ dw load(const double* p) { return dw_from_double(__ldg(p)); }
+  __device__ static __forceinline__ dw load_stream(const double* p) { return dw_from_double(__ldcs(p)); }
+  __device__ static __forceinline__ void store(double* p, dw v) { __stcs(p, dw_to_double(v)); }
+  __device__ static __forceinline__ dw geo(const float2* p) {
+    float2 g = __ldcs(p);
+    return {g.x, g.y};
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// 1D tables passed by value as kernel parameters (they land in the constant bank and are read
+// with compile-time offsets).  Index convention: A[q][i] maps node/point i to point q.
+// ---------------------------------------------------------------------------------------------
+template <int N, class V>
+struct Tab1D {
+  V V_[N][N];  // V[q][i]  = l_i(s_q): GLL-node Lagrange basis at Gauss point q      (Sec. 2.3 "V")
+  V D_[N][N];  // D[q][r]  = derivative of the Gauss-point Lagrange basis r at s_q (collocation)
+  V W_[N];     // Gauss weights on [0,1]
+};
+
+// host-side 1D rules in double precision for one degree
+struct HostTab {
+  int p, n;
+  double t[FE_MAXN];      // GLL nodes on [0,1]
+  double s[FE_MAXN];      // Gauss points on [0,1]
+  double w[FE_MAXN];      // Gauss weights on [0,1]
+  double V[FE_MAXN][FE_MAXN];   // V[q][i]  = l_i(s_q)
+  double D[FE_MAXN][FE_MAXN];   // D[q][r]  = l~_r'(s_q), Gauss-point collocation derivative
+  double Dh[FE_MAXN][FE_MAXN];  // Dh[q][i] = l_i'(s_q) = (D V)[q][i]
+};
+void fe_host_tables(int p, HostTab* out);  // fe_tables.cpp
+
+template <int N, class V>
+Tab1D<N, V> make_tab(const HostTab& h);
+
+// ---------------------------------------------------------------------------------------------
+// mesh object
+// ---------------------------------------------------------------------------------------------
+#define FE_GEO_COMPS 7  // xx, yy, zz, xy, xz, yz of w detJ J^{-1}J^{-T}, then w detJ
+
+struct fe_mesh {
+  fe_mesh_desc d;
+  int p, n, n3;
+  long long ncells, ncw, nu;
+  HostTab tab;
+  // stored geometry [cell][FE_GEO_COMPS][n3] (FP64, double-word, FP32 copies)
+  double* geo64 = nullptr;
+  float2* geodw = nullptr;
+  float* geo32 = nullptr;
+  // recompute mode: nodal coordinates [cell][3][n3]
+  double* xyz64 = nullptr;
+  float2* xyzdw = nullptr;
+  float* xyz32 = nullptr;
+  // Jacobi diagonal caches (cell-wise, continuous), per operator
+  double* diag64[2] = {nullptr, nullptr};
+  float* invdiag32[2] = {nullptr, nullptr};
+  double* invdiag64[2] = {nullptr, nullptr};
+  // inverse multiplicity (cell-wise), for the residual norm
+  double* invmult64 = nullptr;
+  // reduction scratch
+  double* red = nullptr;
+  int red_len = 0;
+};
+
+// ---------------------------------------------------------------------------------------------
+// helpers shared by the translation units of the library
+// ---------------------------------------------------------------------------------------------
+void fe_set_error(const char* fmt, ...);
+fe_status fe_cuda_check(cudaError_t e, const char* what);
+#define FE_TRY(expr)                      \
+  do {                                    \
+    fe_status _s = (expr);                \
+    if (_s != FE_OK) return _s;           \
+  } while (0)
+#define FE_CUDA(expr, what) FE_TRY(fe_cuda_check((expr), (what)))
+
+fe_status fe_ensure_geometry(const fe_mesh* m, int prec, bool native);  // fe_mesh.cu
+
+// apply (fe_apply.cu / fe_apply_*.cu)
+struct ApplyLaunch {
+  const fe_mesh* m;
+  int op;         // FE_LAPLACE / FE_MASS
+  const void* x;
+  void* y;
+  cudaStream_t st;
+};
+fe_status fe_launch_apply_f64dw(const ApplyLaunch& a);
+fe_status fe_launch_apply_f64native(const ApplyLaunch& a);
+fe_status fe_launch_apply_f32(const ApplyLaunch& a);
+
+// dss / vectors (fe_dss.cu)
+fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st);
+fe_status fe_launch_diag(const fe_mesh* m, int op, double* d, cudaStream_t st);
+fe_status fe_launch_pairing(const fe_mesh* m, int prec, const void* a, const void* b,
+                            double* out, cudaStream_t st);
+
+static inline bool fe_aligned(const void* p) { return ((uintptr_t)p & 15u) == 0; }

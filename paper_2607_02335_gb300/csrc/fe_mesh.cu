@@ -1,0 +1,387 @@
+// fe_mesh.cu -- mesh object, geometry set-up kernel, gather helper, error reporting.
+//
+// Geometry (Sec. 2.3 and Sec. 5.3 "per-quadrature-point Jacobians"): the map
+// Phi(X) = X + amp sin(pi X) sin(pi Y) sin(pi Z) (1,1,1) is sampled at the GLL nodes of every
+// cell and interpolated isoparametrically with Q_p.  For every Gauss point q the kernel forms
+// J_ab = d x_a / d xi_b (xi in [0,1]^3) by sum factorization, then stores
+// G = w_q detJ J^{-1} J^{-T} (6 symmetric entries) and w_q detJ, in FP64, laid out
+// [cell][component][q] so that the apply kernels read them with coalesced loads.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "fe_internal.h"
+
+// ---------------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+void fe_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+fe_status fe_cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FE_OK;
+  fe_set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA;
+}
+
+extern "C" const char* fe_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------------------------
+// geometry kernel: one CTA per cell, n^3 threads (one per node, then one per Gauss point)
+// ---------------------------------------------------------------------------------------------
+struct GeoTab {
+  double t[FE_MAXN];
+  double w[FE_MAXN];
+  double V[FE_MAXN][FE_MAXN];
+  double Dh[FE_MAXN][FE_MAXN];
+};
+
+struct GeoArgs {
+  double* geo;  // [cell][7][n3] or null
+  double* xyz;  // [cell][3][n3] or null
+  long long ncells;
+  int mx, my, mz;
+  double amp;
+  GeoTab tab;
+};
+
+template <int N>
+__global__ void __launch_bounds__(N* N* N) k_geometry(const __grid_constant__ GeoArgs a) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  extern __shared__ double gsm[];
+  double* sX = gsm;             // [3][N3] node coordinates
+  double* sA = gsm + 3 * N3;    // [3][N3] V along x
+  double* sB = gsm + 6 * N3;    // [3][N3] Dh along x
+  double* sAA = gsm + 9 * N3;   // [3][N3] V x, V y
+  double* sAB = gsm + 12 * N3;  // [3][N3] V x, Dh y
+  double* sBA = gsm + 15 * N3;  // [3][N3] Dh x, V y
+  const long long cell = blockIdx.x;
+  const int t = threadIdx.x;
+  const int i = t % N, j = (t / N) % N, k = t / N2;
+  const int cx = (int)(cell % a.mx), cy = (int)((cell / a.mx) % a.my),
+            cz = (int)(cell / ((long long)a.mx * a.my));
+  {
+    const double X0 = (cx + a.tab.t[i]) / a.mx, X1 = (cy + a.tab.t[j]) / a.my,
+                 X2 = (cz + a.tab.t[k]) / a.mz;
+    const double s = a.amp * sinpi(X0) * sinpi(X1) * sinpi(X2);
+    sX[0 * N3 + t] = X0 + s;
+    sX[1 * N3 + t] = X1 + s;
+    sX[2 * N3 + t] = X2 + s;
+    if (a.xyz) {
+      double* out = a.xyz + (size_t)cell * 3 * N3;
+      out[0 * N3 + t] = X0 + s;
+      out[1 * N3 + t] = X1 + s;
+      out[2 * N3 + t] = X2 + s;
+    }
+  }
+  if (!a.geo) return;
+  __syncthreads();
+  // x: thread (q1 = i, j, k) contracts over the node index along x
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double A = 0.0, B = 0.0;
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      const double v = sX[c * N3 + (k * N + j) * N + r];
+      A = fma(a.tab.V[i][r], v, A);
+      B = fma(a.tab.Dh[i][r], v, B);
+    }
+    sA[c * N3 + t] = A;
+    sB[c * N3 + t] = B;
+  }
+  __syncthreads();
+  // y: thread (q1 = i, q2 = j, k)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double AA = 0.0, AB = 0.0, BA = 0.0;
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      const int e = c * N3 + (k * N + r) * N + i;
+      AA = fma(a.tab.V[j][r], sA[e], AA);
+      AB = fma(a.tab.Dh[j][r], sA[e], AB);
+      BA = fma(a.tab.V[j][r], sB[e], BA);
+    }
+    sAA[c * N3 + t] = AA;
+    sAB[c * N3 + t] = AB;
+    sBA[c * N3 + t] = BA;
+  }
+  __syncthreads();
+  // z: thread (q1 = i, q2 = j, q3 = k) finishes J[c][b] = d x_c / d xi_b
+  double J[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      const int e = c * N3 + (r * N + j) * N + i;
+      j0 = fma(a.tab.V[k][r], sBA[e], j0);
+      j1 = fma(a.tab.V[k][r], sAB[e], j1);
+      j2 = fma(a.tab.Dh[k][r], sAA[e], j2);
+    }
+    J[c][0] = j0;
+    J[c][1] = j1;
+    J[c][2] = j2;
+  }
+  const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  const double id = 1.0 / det;
+  double Ji[3][3];  // inverse via the adjugate
+  Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) * id;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+  Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) * id;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+  Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) * id;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  const double wd = a.tab.w[i] * a.tab.w[j] * a.tab.w[k] * det;
+  // G_ab = wd * sum_c Ji[a][c] Ji[b][c]
+  auto G = [&](int p, int q) {
+    return wd * (Ji[p][0] * Ji[q][0] + Ji[p][1] * Ji[q][1] + Ji[p][2] * Ji[q][2]);
+  };
+  double* out = a.geo + (size_t)cell * FE_GEO_COMPS * N3;
+  out[0 * N3 + t] = G(0, 0);
+  out[1 * N3 + t] = G(1, 1);
+  out[2 * N3 + t] = G(2, 2);
+  out[3 * N3 + t] = G(0, 1);
+  out[4 * N3 + t] = G(0, 2);
+  out[5 * N3 + t] = G(1, 2);
+  out[6 * N3 + t] = wd;
+}
+
+template <int N>
+static fe_status launch_geometry(const GeoArgs& a, cudaStream_t st) {
+  constexpr int N3 = N * N * N;
+  size_t smem = 18 * N3 * sizeof(double);
+  FE_CUDA(cudaFuncSetAttribute(k_geometry<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+          "geometry smem attribute");
+  if (a.ncells > 0) k_geometry<N><<<(unsigned)a.ncells, N3, smem, st>>>(a);
+  return fe_cuda_check(cudaGetLastError(), "geometry kernel launch");
+}
+
+// ---------------------------------------------------------------------------------------------
+// precision copies of FP64 arrays (set-up only)
+// ---------------------------------------------------------------------------------------------
+__global__ void k_split_dw(const double* __restrict__ in, float2* __restrict__ out, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double v = in[e];
+    const float h = __double2float_rn(v);
+    out[e] = make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = __double2float_rn(in[e]);
+}
+
+static unsigned grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 64) b = 152LL * 64;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
+  fe_mesh* m = const_cast<fe_mesh*>(cm);
+  if (m->d.geom_mode != FE_GEOM_STORED) return FE_OK;
+  const long long n = m->ncells * FE_GEO_COMPS * m->n3;
+  if (prec == FE_F64 && !native) {
+    if (!m->geodw) {
+      FE_CUDA(cudaMalloc(&m->geodw, n * sizeof(float2)), "cudaMalloc geometry (double-word)");
+      k_split_dw<<<grid_for(n, 256), 256>>>(m->geo64, m->geodw, n);
+      FE_CUDA(cudaDeviceSynchronize(), "geometry double-word split");
+    }
+  } else if (prec == FE_F32) {
+    if (!m->geo32) {
+      FE_CUDA(cudaMalloc(&m->geo32, n * sizeof(float)), "cudaMalloc geometry (fp32)");
+      k_to_f32<<<grid_for(n, 256), 256>>>(m->geo64, m->geo32, n);
+      FE_CUDA(cudaDeviceSynchronize(), "geometry fp32 copy");
+    }
+  }
+  return FE_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// mesh object
+// ---------------------------------------------------------------------------------------------
+static void free_mesh(fe_mesh* m) {
+  if (!m) return;
+  cudaFree(m->geo64);
+  cudaFree(m->geodw);
+  cudaFree(m->geo32);
+  cudaFree(m->xyz64);
+  cudaFree(m->xyzdw);
+  cudaFree(m->xyz32);
+  for (int o = 0; o < 2; ++o) {
+    cudaFree(m->diag64[o]);
+    cudaFree(m->invdiag32[o]);
+    cudaFree(m->invdiag64[o]);
+  }
+  cudaFree(m->invmult64);
+  cudaFree(m->red);
+  delete m;
+}
+
+extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh** out) {
+  if (!d || !out) {
+    fe_set_error("fe_mesh_create: null argument");
+    return FE_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (d->degree < 1 || d->degree > 7) {
+    fe_set_error("fe_mesh_create: degree %d outside [1,7]", d->degree);
+    return FE_ERR_INVALID;
+  }
+  if (d->mx < 1 || d->my < 1 || d->mz < 1) {
+    fe_set_error("fe_mesh_create: cell counts must be positive (%d,%d,%d)", d->mx, d->my, d->mz);
+    return FE_ERR_INVALID;
+  }
+  if (d->geom_mode < FE_GEOM_STORED || d->geom_mode > FE_GEOM_AFFINE) {
+    fe_set_error("fe_mesh_create: unknown geom_mode %d", d->geom_mode);
+    return FE_ERR_INVALID;
+  }
+  if (d->geom_mode == FE_GEOM_AFFINE && d->deform_amp != 0.0) {
+    fe_set_error("fe_mesh_create: FE_GEOM_AFFINE needs deform_amp == 0");
+    return FE_ERR_INVALID;
+  }
+  if (!(std::fabs(d->deform_amp) <= 0.2)) {
+    fe_set_error("fe_mesh_create: |deform_amp| must be <= 0.2 (keeps the map invertible)");
+    return FE_ERR_INVALID;
+  }
+  const long long ncells = (long long)d->mx * d->my * d->mz;
+  const long long n3 = (long long)(d->degree + 1) * (d->degree + 1) * (d->degree + 1);
+  if (ncells * n3 > (1LL << 40)) {
+    fe_set_error("fe_mesh_create: mesh too large");
+    return FE_ERR_INVALID;
+  }
+  FE_CUDA(cudaSetDevice(d->device), "cudaSetDevice");
+  fe_mesh* m = new (std::nothrow) fe_mesh();
+  if (!m) {
+    fe_set_error("fe_mesh_create: host allocation failed");
+    return FE_ERR_OOM;
+  }
+  m->d = *d;
+  m->p = d->degree;
+  m->n = d->degree + 1;
+  m->n3 = (int)n3;
+  m->ncells = ncells;
+  m->ncw = ncells * n3;
+  m->nu = (long long)(d->mx * m->p + 1) * (d->my * m->p + 1) * (d->mz * m->p + 1);
+  fe_host_tables(m->p, &m->tab);
+  cudaStream_t st = (cudaStream_t)stream;
+
+  GeoArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.ncells = ncells;
+  g.mx = d->mx;
+  g.my = d->my;
+  g.mz = d->mz;
+  g.amp = d->deform_amp;
+  for (int a = 0; a < m->n; ++a) {
+    g.tab.t[a] = m->tab.t[a];
+    g.tab.w[a] = m->tab.w[a];
+    for (int b = 0; b < m->n; ++b) {
+      g.tab.V[a][b] = m->tab.V[a][b];
+      g.tab.Dh[a][b] = m->tab.Dh[a][b];
+    }
+  }
+  fe_status s = FE_OK;
+  if (d->geom_mode == FE_GEOM_STORED) {
+    s = fe_cuda_check(cudaMalloc(&m->geo64, m->ncw * FE_GEO_COMPS * sizeof(double)),
+                      "cudaMalloc geometry");
+    g.geo = m->geo64;
+  } else if (d->geom_mode == FE_GEOM_RECOMPUTE) {
+    s = fe_cuda_check(cudaMalloc(&m->xyz64, m->ncw * 3 * sizeof(double)), "cudaMalloc coordinates");
+    g.xyz = m->xyz64;
+  }
+  if (s == FE_OK && d->geom_mode != FE_GEOM_AFFINE) {
+    switch (m->n) {
+      case 2: s = launch_geometry<2>(g, st); break;
+      case 3: s = launch_geometry<3>(g, st); break;
+      case 4: s = launch_geometry<4>(g, st); break;
+      case 5: s = launch_geometry<5>(g, st); break;
+      case 6: s = launch_geometry<6>(g, st); break;
+      case 7: s = launch_geometry<7>(g, st); break;
+      case 8: s = launch_geometry<8>(g, st); break;
+    }
+  }
+  if (s == FE_OK) s = fe_cuda_check(cudaStreamSynchronize(st), "geometry synchronize");
+  if (s == FE_OK) s = fe_ensure_geometry(m, FE_F64, false);
+  if (s != FE_OK) {
+    free_mesh(m);
+    return s;
+  }
+  *out = m;
+  return FE_OK;
+}
+
+extern "C" fe_status fe_mesh_destroy(fe_mesh* m) {
+  if (!m) return FE_OK;
+  cudaSetDevice(m->d.device);
+  cudaDeviceSynchronize();
+  free_mesh(m);
+  return FE_OK;
+}
+
+extern "C" fe_status fe_mesh_layout(const fe_mesh* m, fe_layout* out) {
+  if (!m || !out) {
+    fe_set_error("fe_mesh_layout: null argument");
+    return FE_ERR_INVALID;
+  }
+  out->n_cells = m->ncells;
+  out->nodes_per_cell = m->n3;
+  out->cellwise_len = m->ncw;
+  out->unique_dofs = m->nu;
+  out->layout_id = 0;
+  return FE_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// gather G: x_cell[e] = x_unique[global(e)]
+// ---------------------------------------------------------------------------------------------
+__global__ void k_gather(const double* __restrict__ xu, double* __restrict__ xc, long long ncw,
+                         int n, int mx, int my) {
+  const int p = n - 1, n3 = n * n * n;
+  const long long Nx = (long long)mx * p + 1, Ny = (long long)my * p + 1;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ncw;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long cell = e / n3;
+    const int loc = (int)(e - cell * n3);
+    const int i = loc % n, j = (loc / n) % n, k = loc / (n * n);
+    const long long cx = cell % mx, cy = (cell / mx) % my, cz = cell / ((long long)mx * my);
+    xc[e] = xu[((cz * p + k) * Ny + (cy * p + j)) * Nx + (cx * p + i)];
+  }
+}
+
+extern "C" fe_status fe_gather(const fe_mesh* m, const double* xu_host, double* xc_dev,
+                               void* stream) {
+  if (!m || !xu_host || !xc_dev || !fe_aligned(xc_dev)) {
+    fe_set_error("fe_gather: null or misaligned argument");
+    return FE_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double* tmp = nullptr;
+  FE_CUDA(cudaMallocAsync(&tmp, m->nu * sizeof(double), st), "fe_gather: cudaMallocAsync");
+  fe_status s = fe_cuda_check(
+      cudaMemcpyAsync(tmp, xu_host, m->nu * sizeof(double), cudaMemcpyHostToDevice, st),
+      "fe_gather: copy");
+  if (s == FE_OK) {
+    k_gather<<<grid_for(m->ncw, 256), 256, 0, st>>>(tmp, xc_dev, m->ncw, m->n, m->d.mx, m->d.my);
+    s = fe_cuda_check(cudaGetLastError(), "fe_gather: launch");
+  }
+  cudaFreeAsync(tmp, st);
+  if (s == FE_OK) s = fe_cuda_check(cudaStreamSynchronize(st), "fe_gather: synchronize");
+  return s;
+}

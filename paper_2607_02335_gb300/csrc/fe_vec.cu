@@ -1,0 +1,319 @@
+// fe_vec.cu -- structured DSS, Jacobi diagonal, duality pairings and cell-wise vector kernels.
+#include <cstring>
+
+#include "fe_vec.cuh"
+
+// ---------------------------------------------------------------------------------------------
+// Structured DSS (Sec. 4.1, Algorithm "Dimensionally-Split Structured Summation").  One launch
+// per axis, in the order z, y, x.  Each thread owns one node pair of one interior interface
+// (cell K_L with local index p along the axis, cell K_R with local index 0): it sums the two
+// copies and writes the sum to both.  Pairs of one pass are disjoint, so no atomics are needed;
+// because each pass sees the partial sums of the previous one, edge and vertex copies are
+// assembled as a by-product.
+// ---------------------------------------------------------------------------------------------
+template <class S>
+__global__ void k_dss_pass(S* __restrict__ v, int axis, int n, int mx, int my, int mz,
+                           long long nwork) {
+  const int p = n - 1, n2 = n * n, n3 = n2 * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nwork;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(e % n2);
+    const long long q = e / n2;
+    const int fa = f % n, fb = f / n;
+    long long L, R;
+    int locL, locR;
+    if (axis == 0) {  // faces normal to x
+      const long long cxL = q % (mx - 1), r = q / (mx - 1);
+      L = r * mx + cxL;  // r = cz*my + cy
+      R = L + 1;
+      locL = (fb * n + fa) * n + p;
+      locR = (fb * n + fa) * n + 0;
+    } else if (axis == 1) {  // faces normal to y
+      const long long cx = q % mx, r = q / mx, cyL = r % (my - 1), cz = r / (my - 1);
+      L = (cz * my + cyL) * mx + cx;
+      R = L + mx;
+      locL = (fb * n + p) * n + fa;
+      locR = (fb * n + 0) * n + fa;
+    } else {  // faces normal to z
+      L = q;  // q = (czL*my + cy)*mx + cx
+      R = L + (long long)mx * my;
+      locL = (p * n + fb) * n + fa;
+      locR = (0 * n + fb) * n + fa;
+    }
+    S* pl = v + L * n3 + locL;
+    S* pr = v + R * n3 + locR;
+    const S s = *pl + *pr;
+    *pl = s;
+    *pr = s;
+  }
+}
+
+static unsigned grid_cap(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+template <class S>
+static fe_status dss_t(const fe_mesh* m, S* v, cudaStream_t st) {
+  const int n = m->n, n2 = n * n;
+  const int mx = m->d.mx, my = m->d.my, mz = m->d.mz;
+  const long long work[3] = {(long long)(mx - 1) * my * mz * n2, (long long)mx * (my - 1) * mz * n2,
+                             (long long)mx * my * (mz - 1) * n2};
+  for (int axis = 2; axis >= 0; --axis) {  // z, y, x
+    if (work[axis] <= 0) continue;
+    k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, mz, work[axis]);
+  }
+  return fe_cuda_check(cudaGetLastError(), "dss launch");
+}
+
+fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st) {
+  if (prec == FE_F64) return dss_t<double>(m, (double*)v, st);
+  if (prec == FE_F32) return dss_t<float>(m, (float*)v, st);
+  fe_set_error("dss: unsupported precision %d", prec);
+  return FE_ERR_INVALID;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Jacobi diagonal (Sec. 3.3: D_cell = diag(G d)).  The local diagonal of A_K,
+//   d_i = sum_q sum_ab G_ab(q) dphi_i/dxi_a(q) dphi_i/dxi_b(q)   (Laplace)
+//   d_i = sum_q w_q detJ(q) phi_i(q)^2                          (mass),
+// is a transposed sum factorization with squared 1D matrices (Dh^2, V^2, Dh*V): six terms for
+// the symmetric G.  FP64, once per mesh and operator.  Then DSS assembles the copies and
+// Dirichlet nodes get 1.
+// ---------------------------------------------------------------------------------------------
+struct DiagTab {
+  double V2[FE_MAXN][FE_MAXN];   // V[q][i]^2
+  double D2[FE_MAXN][FE_MAXN];   // Dh[q][i]^2
+  double DV[FE_MAXN][FE_MAXN];   // Dh[q][i] V[q][i]
+  double w[FE_MAXN];
+};
+struct DiagArgs {
+  const double* geo;
+  double* d;
+  long long ncells;
+  int op, affine;
+  double aff[4];
+  DiagTab tab;
+};
+
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS) k_diag(const __grid_constant__ DiagArgs a) {
+  using C = Cfg<N>;
+  constexpr int N2 = C::N2, N3 = C::N3;
+  extern __shared__ double dsm[];
+  const int t = threadIdx.x, cl = t / N2, lt = t - cl * N2, la = lt % N, lb = lt / N;
+  const int cb = cl * C::CS;
+  const long long cell = (long long)blockIdx.x * C::CPB + cl;
+  const bool active = cell < a.ncells;
+  // term t: (component, C1, C2, C3, factor)   matrices: 0 = V2, 1 = D2, 2 = DV
+  const int nterms = (a.op == FE_LAPLACE) ? 6 : 1;
+  const int comp[6] = {0, 1, 2, 3, 4, 5};
+  const int m1[6] = {1, 0, 0, 2, 2, 0}, m2[6] = {0, 1, 0, 2, 0, 2}, m3[6] = {0, 0, 1, 0, 2, 2};
+  const double fac[6] = {1, 1, 1, 2, 2, 2};
+  double dsum[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) dsum[k] = 0.0;
+  for (int term = 0; term < nterms; ++term) {
+    const int c = (a.op == FE_LAPLACE) ? comp[term] : 6;
+    const int M1 = (a.op == FE_LAPLACE) ? m1[term] : 0, M2 = (a.op == FE_LAPLACE) ? m2[term] : 0,
+              M3 = (a.op == FE_LAPLACE) ? m3[term] : 0;
+    const double (*T1)[FE_MAXN] = M1 == 0 ? a.tab.V2 : (M1 == 1 ? a.tab.D2 : a.tab.DV);
+    const double (*T2)[FE_MAXN] = M2 == 0 ? a.tab.V2 : (M2 == 1 ? a.tab.D2 : a.tab.DV);
+    const double (*T3)[FE_MAXN] = M3 == 0 ? a.tab.V2 : (M3 == 1 ? a.tab.D2 : a.tab.DV);
+    double g[N];
+#pragma unroll
+    for (int q3 = 0; q3 < N; ++q3) {
+      double v = 0.0;
+      if (active) {
+        if (a.affine) {
+          const double wq = a.tab.w[la] * a.tab.w[lb] * a.tab.w[q3];
+          v = (c == 6) ? wq * a.aff[3] : (c < 3 ? wq * a.aff[c] : 0.0);
+        } else {
+          v = a.geo[(size_t)cell * FE_GEO_COMPS * N3 + (size_t)c * N3 + q3 * N2 + lt];
+        }
+      }
+      g[q3] = v * fac[term];
+    }
+    // z: P(q1, q2, k) = sum_q3 T3[q3][k] g(q1, q2, q3)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double acc = 0.0;
+#pragma unroll
+      for (int q3 = 0; q3 < N; ++q3) acc = fma(T3[q3][k], g[q3], acc);
+      dsm[cb + zl<N>(la, lb, k)] = acc;
+    }
+    __syncthreads();
+    {  // x: line (q2 = la, k = lb), contract q1 -> i
+      double in[N];
+#pragma unroll
+      for (int r = 0; r < N; ++r) in[r] = dsm[cb + xl<N>(la, lb, r)];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int r = 0; r < N; ++r) acc = fma(T1[r][i], in[r], acc);
+        dsm[cb + xl<N>(la, lb, i)] = acc;
+      }
+    }
+    __syncthreads();
+    {  // y: line (i = la, k = lb), contract q2 -> j
+      double in[N];
+#pragma unroll
+      for (int r = 0; r < N; ++r) in[r] = dsm[cb + yl<N>(la, lb, r)];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        double acc = 0.0;
+#pragma unroll
+        for (int r = 0; r < N; ++r) acc = fma(T2[r][j], in[r], acc);
+        dsm[cb + yl<N>(la, lb, j)] = acc;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) dsum[k] += dsm[cb + zl<N>(la, lb, k)];
+    __syncthreads();
+  }
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) a.d[cell * N3 + k * N2 + lt] = dsum[k];
+  }
+}
+
+template <int N>
+static fe_status launch_diag_n(const DiagArgs& a, cudaStream_t st) {
+  using C = Cfg<N>;
+  const size_t smem = (size_t)C::TILE * sizeof(double);
+  FE_CUDA(cudaFuncSetAttribute(k_diag<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+          "diag smem attribute");
+  const long long blocks = (a.ncells + C::CPB - 1) / C::CPB;
+  if (blocks > 0) k_diag<N><<<(unsigned)blocks, C::THREADS, smem, st>>>(a);
+  return fe_cuda_check(cudaGetLastError(), "diag launch");
+}
+
+// Dirichlet nodes -> 1 (one warp per cell, lanes over the cell's nodes)
+__global__ void k_dirichlet_fill(double* __restrict__ v, double val, long long ncells, int n, int mx,
+                                 int my, int mz) {
+  const int n3 = n * n * n, p = n - 1;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long c = warp; c < ncells; c += nwarps) {
+    const int cx = (int)(c % mx), cy = (int)((c / mx) % my), cz = (int)(c / ((long long)mx * my));
+    if (cx != 0 && cx != mx - 1 && cy != 0 && cy != my - 1 && cz != 0 && cz != mz - 1) continue;
+    for (int l = lane; l < n3; l += 32) {
+      const int i = l % n, j = (l / n) % n, k = l / (n * n);
+      if ((cx == 0 && i == 0) || (cx == mx - 1 && i == p) || (cy == 0 && j == 0) ||
+          (cy == my - 1 && j == p) || (cz == 0 && k == 0) || (cz == mz - 1 && k == p))
+        v[c * n3 + l] = val;
+    }
+  }
+}
+
+fe_status fe_launch_diag(const fe_mesh* m, int op, double* d, cudaStream_t st) {
+  DiagArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.geo = m->geo64;
+  a.d = d;
+  a.ncells = m->ncells;
+  a.op = op;
+  a.affine = m->d.geom_mode == FE_GEOM_AFFINE;
+  const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / m->d.mz, det = hx * hy * hz;
+  a.aff[0] = det / (hx * hx);
+  a.aff[1] = det / (hy * hy);
+  a.aff[2] = det / (hz * hz);
+  a.aff[3] = det;
+  for (int q = 0; q < m->n; ++q) {
+    a.tab.w[q] = m->tab.w[q];
+    for (int i = 0; i < m->n; ++i) {
+      a.tab.V2[q][i] = m->tab.V[q][i] * m->tab.V[q][i];
+      a.tab.D2[q][i] = m->tab.Dh[q][i] * m->tab.Dh[q][i];
+      a.tab.DV[q][i] = m->tab.Dh[q][i] * m->tab.V[q][i];
+    }
+  }
+  if (!a.affine && !a.geo) {
+    fe_set_error("diag: needs stored or affine geometry");
+    return FE_ERR_INVALID;
+  }
+  fe_status s;
+  switch (m->n) {
+    case 2: s = launch_diag_n<2>(a, st); break;
+    case 3: s = launch_diag_n<3>(a, st); break;
+    case 4: s = launch_diag_n<4>(a, st); break;
+    case 5: s = launch_diag_n<5>(a, st); break;
+    case 6: s = launch_diag_n<6>(a, st); break;
+    case 7: s = launch_diag_n<7>(a, st); break;
+    case 8: s = launch_diag_n<8>(a, st); break;
+    default: fe_set_error("diag: bad n"); return FE_ERR_INVALID;
+  }
+  if (s != FE_OK) return s;
+  FE_TRY(fe_launch_dss(m, FE_F64, d, st));
+  if (m->d.dirichlet) {
+    k_dirichlet_fill<<<grid_cap(m->ncells * 32, 256), 256, 0, st>>>(d, 1.0, m->ncells, m->n,
+                                                                    m->d.mx, m->d.my, m->d.mz);
+    FE_TRY(fe_cuda_check(cudaGetLastError(), "dirichlet fill"));
+  }
+  return FE_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Deterministic reductions.  A fixed grid of RED_BLOCKS CTAs strides over the vector; each
+// thread accumulates in double-word arithmetic, the CTA reduces in a fixed shuffle tree and
+// writes one FP64 partial per CTA; a one-CTA kernel sums the partials in a fixed order.  The
+// result depends only on the data, never on timing.
+// ---------------------------------------------------------------------------------------------
+// partials[slot * RED_BLOCKS + block] = sum over the CTA's stride of a_e * b_e
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_pairing_partial(const S* __restrict__ a, const S* __restrict__ b, long long n,
+                      double* __restrict__ partials) {
+  __shared__ dw sh[32];
+  dw acc = {0.0f, 0.0f};
+  for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n;
+       e += (long long)RED_BLOCKS * RED_THREADS)
+    acc = dw_mac(acc, to_dw<S>(__ldg(a + e)), to_dw<S>(__ldg(b + e)));
+  acc = dw_norm(acc);
+  acc = block_reduce_dw(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = dw_to_double(acc);
+}
+
+// sum of RED_BLOCKS partials of each of `nslots` slots, in a fixed order
+__global__ void __launch_bounds__(RED_THREADS)
+    k_partials_sum(const double* __restrict__ partials, int nslots, double* __restrict__ out) {
+  __shared__ dw sh[32];
+  for (int s = 0; s < nslots; ++s) {
+    dw acc = {0.0f, 0.0f};
+    for (int b = threadIdx.x; b < RED_BLOCKS; b += RED_THREADS)
+      acc = dw_add(acc, dw_from_double(partials[s * RED_BLOCKS + b]));
+    acc = block_reduce_dw(acc, sh);
+    if (threadIdx.x == 0) out[s] = dw_to_double(acc);
+  }
+}
+
+fe_status fe_ensure_reduction(const fe_mesh* cm) {
+  fe_mesh* m = const_cast<fe_mesh*>(cm);
+  if (!m->red) {
+    FE_CUDA(cudaMalloc(&m->red, (size_t)RED_BLOCKS * RED_SLOTS * sizeof(double)),
+            "cudaMalloc reduction partials");
+    m->red_len = RED_BLOCKS * RED_SLOTS;
+  }
+  return FE_OK;
+}
+
+fe_status fe_launch_pairing(const fe_mesh* m, int prec, const void* a, const void* b, double* out,
+                            cudaStream_t st) {
+  FE_TRY(fe_ensure_reduction(m));
+  if (prec == FE_F64)
+    k_pairing_partial<double><<<RED_BLOCKS, RED_THREADS, 0, st>>>((const double*)a, (const double*)b,
+                                                                  m->ncw, m->red);
+  else if (prec == FE_F32)
+    k_pairing_partial<float><<<RED_BLOCKS, RED_THREADS, 0, st>>>((const float*)a, (const float*)b,
+                                                                 m->ncw, m->red);
+  else {
+    fe_set_error("pairing: unsupported precision %d", prec);
+    return FE_ERR_INVALID;
+  }
+  k_partials_sum<<<1, RED_THREADS, 0, st>>>(m->red, 1, out);
+  return fe_cuda_check(cudaGetLastError(), "pairing launch");
+}

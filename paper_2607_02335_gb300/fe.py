@@ -1,0 +1,218 @@
+"""Thin ctypes binding of ``libfe.so`` (C ABI in ``include/fe.h``).
+
+The functions below carry the C names and only marshal arguments: device vectors are passed as
+raw pointers (``torch.Tensor.data_ptr()``), streams as ``cudaStream_t`` handles.  Every step of
+the computation runs in the library's CUDA kernels; there is no fallback.  Importing this module
+raises ``ImportError`` when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libfe.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libfe.so not built ({_LIB_PATH}); run `python -m paper_2607_02335_gb300.build`")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+# ---- enums (mirrors of include/fe.h) ----------------------------------------------------------
+FE_OK, FE_ERR_INVALID, FE_ERR_OOM, FE_ERR_CUDA = 0, 1, 2, 3
+FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN, FE_ERR_TIMEOUT, FE_ERR_BUSY = 4, 5, 6, 7
+FE_LAPLACE, FE_MASS = 0, 1
+FE_F64, FE_F32, FE_BF16_F32ACC, FE_F16_F32ACC = 0, 1, 2, 3
+FE_GEOM_STORED, FE_GEOM_RECOMPUTE, FE_GEOM_AFFINE = 0, 1, 2
+FE_ASSEMBLE, FE_NATIVE_F64 = 1, 2
+
+STATUS_NAMES = {0: "FE_OK", 1: "FE_ERR_INVALID", 2: "FE_ERR_OOM", 3: "FE_ERR_CUDA",
+                4: "FE_ERR_NOT_CONVERGED", 5: "FE_ERR_BREAKDOWN", 6: "FE_ERR_TIMEOUT",
+                7: "FE_ERR_BUSY"}
+
+
+class fe_mesh_desc(ctypes.Structure):
+    _fields_ = [("mx", ctypes.c_int), ("my", ctypes.c_int), ("mz", ctypes.c_int),
+                ("degree", ctypes.c_int), ("deform_amp", ctypes.c_double),
+                ("geom_mode", ctypes.c_int), ("dirichlet", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class fe_layout(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_longlong), ("nodes_per_cell", ctypes.c_longlong),
+                ("cellwise_len", ctypes.c_longlong), ("unique_dofs", ctypes.c_longlong),
+                ("layout_id", ctypes.c_int)]
+
+
+class fe_cg_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("mixed", ctypes.c_int),
+                ("flexible", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
+
+
+class fe_cg_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+_vp, _i, _u, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double
+_MESH = ctypes.c_void_p
+_SIGS = {
+    "fe_mesh_create": [ctypes.POINTER(fe_mesh_desc), _vp, ctypes.POINTER(_MESH)],
+    "fe_mesh_destroy": [_MESH],
+    "fe_mesh_layout": [_MESH, ctypes.POINTER(fe_layout)],
+    "fe_gather": [_MESH, _vp, _vp, _vp],
+    "fe_apply": [_MESH, _i, _i, _vp, _vp, _u, _vp],
+    "fe_dss": [_MESH, _i, _vp, _vp, _vp],
+    "fe_diag": [_MESH, _i, _vp, _vp],
+    "fe_pairing": [_MESH, _i, _vp, _vp, _vp, _vp],
+    "fe_cg_solve": [_MESH, _vp, _vp, ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_cg_result), _vp],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.fe_last_error.argtypes = []
+_lib.fe_last_error.restype = ctypes.c_char_p
+
+EXPORTED = tuple(_SIGS) + ("fe_last_error",)
+
+
+class FeError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {fe_last_error()}")
+
+
+def fe_last_error() -> str:
+    return _lib.fe_last_error().decode()
+
+
+def _check(status: int, where: str) -> int:
+    if status != FE_OK:
+        raise FeError(status, where)
+    return status
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    return t if isinstance(t, int) else t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+# ---- calls with the C names ---------------------------------------------------------------------
+def fe_mesh_create(desc: fe_mesh_desc, stream=None) -> int:
+    h = _MESH()
+    _check(_lib.fe_mesh_create(ctypes.byref(desc), _stream(stream), ctypes.byref(h)), "fe_mesh_create")
+    return h.value
+
+
+def fe_mesh_destroy(mesh: int) -> None:
+    _check(_lib.fe_mesh_destroy(mesh), "fe_mesh_destroy")
+
+
+def fe_mesh_layout(mesh: int) -> fe_layout:
+    out = fe_layout()
+    _check(_lib.fe_mesh_layout(mesh, ctypes.byref(out)), "fe_mesh_layout")
+    return out
+
+
+def fe_gather(mesh: int, x_unique_host, x_cell_dev, stream=None) -> None:
+    import numpy as np
+    xu = np.ascontiguousarray(x_unique_host, dtype=np.float64)
+    _check(_lib.fe_gather(mesh, xu.ctypes.data, _ptr(x_cell_dev), _stream(stream)), "fe_gather")
+
+
+def fe_apply(mesh: int, op: int, prec: int, x, y, flags: int = 0, stream=None) -> None:
+    _check(_lib.fe_apply(mesh, op, prec, _ptr(x), _ptr(y), flags, _stream(stream)), "fe_apply")
+
+
+def fe_dss(mesh: int, prec: int, r, z, stream=None) -> None:
+    _check(_lib.fe_dss(mesh, prec, _ptr(r), _ptr(z), _stream(stream)), "fe_dss")
+
+
+def fe_diag(mesh: int, op: int, d, stream=None) -> None:
+    _check(_lib.fe_diag(mesh, op, _ptr(d), _stream(stream)), "fe_diag")
+
+
+def fe_pairing(mesh: int, prec: int, a, b, result_dev, stream=None) -> None:
+    _check(_lib.fe_pairing(mesh, prec, _ptr(a), _ptr(b), _ptr(result_dev), _stream(stream)),
+           "fe_pairing")
+
+
+def fe_cg_solve(mesh: int, b, x, opts: fe_cg_opts, stream=None) -> fe_cg_result:
+    """Returns the fe_cg_result; FE_ERR_NOT_CONVERGED / FE_ERR_BREAKDOWN are reported in
+    ``result.status`` instead of raising."""
+    res = fe_cg_result()
+    st = _lib.fe_cg_solve(mesh, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(res),
+                          _stream(stream))
+    if st not in (FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN):
+        raise FeError(st, "fe_cg_solve")
+    res.status = st
+    return res
+
+
+# ---- convenience object ---------------------------------------------------------------------------
+class Mesh:
+    """Owns an ``fe_mesh``; vectors are torch CUDA tensors of ``cellwise_len`` elements."""
+
+    def __init__(self, m, degree: int, deform_amp: float = 0.0, geom_mode: int = FE_GEOM_STORED,
+                 dirichlet: bool = False, device: int = 0, stream=None):
+        mx, my, mz = (m, m, m) if isinstance(m, int) else tuple(m)
+        self.desc = fe_mesh_desc(mx, my, mz, degree, deform_amp, geom_mode, int(dirichlet), device)
+        self.handle = fe_mesh_create(self.desc, stream)
+        lay = fe_mesh_layout(self.handle)
+        self.n_cells, self.nodes_per_cell = lay.n_cells, lay.nodes_per_cell
+        self.cellwise_len, self.unique_dofs = lay.cellwise_len, lay.unique_dofs
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fe_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, prec: int = FE_F64):
+        import torch
+        dt = torch.float64 if prec == FE_F64 else torch.float32
+        return torch.empty(self.cellwise_len, dtype=dt, device=f"cuda:{self.device}")
+
+    def gather(self, x_unique_host):
+        import torch
+        out = torch.empty(self.cellwise_len, dtype=torch.float64, device=f"cuda:{self.device}")
+        fe_gather(self.handle, x_unique_host, out)
+        return out
+
+    def apply(self, x, op=FE_LAPLACE, prec=FE_F64, flags=0, y=None, stream=None):
+        y = self.empty(prec) if y is None else y
+        fe_apply(self.handle, op, prec, x, y, flags, stream)
+        return y
+
+    def dss(self, r, prec=FE_F64, z=None, stream=None):
+        z = self.empty(prec) if z is None else z
+        fe_dss(self.handle, prec, r, z, stream)
+        return z
+
+    def diag(self, op=FE_LAPLACE, stream=None):
+        d = self.empty(FE_F64)
+        fe_diag(self.handle, op, d, stream)
+        return d
+
+    def pairing(self, a, b, prec=FE_F64, stream=None) -> float:
+        import torch
+        out = torch.empty(1, dtype=torch.float64, device=f"cuda:{self.device}")
+        fe_pairing(self.handle, prec, a, b, out, stream)
+        return float(out.item())
+
+    def cg_solve(self, b, x, rtol=1e-10, maxit=1000, mixed=0, flexible=False, inner_rtol=1e-4,
+                 stream=None) -> fe_cg_result:
+        o = fe_cg_opts(rtol, maxit, mixed, int(flexible), inner_rtol)
+        return fe_cg_solve(self.handle, b, x, o, stream)

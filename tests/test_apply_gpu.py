@@ -1,0 +1,205 @@
+"""Parity of the CUDA operator path (through the C ABI) with the FP64 CPU oracle.
+
+Bar (from the method's FP64 target): relative max-norm error <= 1e-12 for the FP64 path
+(double-word arithmetic on the FP32 pipe, and the native FP64 variant); FP32 path <= 2e-5
+(a few units of float rounding amplified by the ~n-term contractions and the metric).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2607_02335_gb300 import synth as S
+from tests.helpers import oracle_mesh, rel_max_err, sampled_assembled
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def fe():
+    from paper_2607_02335_gb300 import fe as F
+    return F
+
+
+def to_host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+# shapes chosen so that every degree spans several CTAs and ends on a ragged one
+SHAPES = {1: (5, 5, 5), 2: (5, 4, 3), 3: (5, 4, 3), 4: (7, 3, 3), 5: (5, 4, 3), 6: (7, 3, 3),
+          7: (3, 3, 2)}
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7])
+def test_local_apply_all_degrees(fe, p):
+    m = SHAPES[p]
+    amp = 0.1
+    om = oracle_mesh(m, p, amp=amp)
+    gm = fe.Mesh(m, p, deform_amp=amp)
+    xg = S.primal_unique(m, p, seed=0)
+    xc = O.gather(om, xg)
+    x = torch.from_numpy(xc).cuda()
+    for op in (fe.FE_LAPLACE, fe.FE_MASS):
+        yref = O.apply_local(om, op, xc)
+        y = to_host(gm.apply(x, op=op, prec=fe.FE_F64))
+        assert rel_max_err(y, yref) <= TOL64, (p, op)
+        if p in (2, 3, 7):
+            yn = to_host(gm.apply(x, op=op, prec=fe.FE_F64, flags=fe.FE_NATIVE_F64))
+            assert rel_max_err(yn, yref) <= TOL64, (p, op, "native")
+            y32 = to_host(gm.apply(x.float(), op=op, prec=fe.FE_F32))
+            assert rel_max_err(y32, yref) <= TOL32, (p, op, "fp32")
+
+
+def test_pr1_q2_affine_assembled_dirichlet_vs_csr(fe):
+    """8^3 affine Q2 Laplace, FP64, FE_ASSEMBLE + Dirichlet, x from seed 0 zeroed on the
+    boundary, against the oracle's assembled sparse SpMV."""
+    m, p = 8, 2
+    om = oracle_mesh(m, p, dirichlet=True)
+    csr = O.assemble_csr(om, O.LAPLACE)
+    xg = S.primal_unique(m, p, seed=0, dirichlet=True)
+    yg = O.apply_dirichlet_csr(om, csr, xg)
+    yref = O.gather(om, yg)
+    for mode in (fe.FE_GEOM_AFFINE, fe.FE_GEOM_STORED):
+        gm = fe.Mesh(m, p, geom_mode=mode, dirichlet=True)
+        x = gm.gather(xg)
+        y = to_host(gm.apply(x, op=fe.FE_LAPLACE, prec=fe.FE_F64, flags=fe.FE_ASSEMBLE))
+        assert rel_max_err(y, yref) <= TOL64, mode
+        assert gm.cellwise_len == 13824 and gm.unique_dofs == 4913
+
+
+@pytest.mark.parametrize("p,m", [(2, (4, 3, 5)), (3, (3, 4, 2)), (5, (2, 3, 2))])
+def test_assembled_deformed_dirichlet_vs_csr(fe, p, m):
+    om = oracle_mesh(m, p, amp=0.1, dirichlet=True)
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=True)
+    xg = S.primal_unique(m, p, seed=3, dirichlet=True)
+    x = gm.gather(xg)
+    for op in (O.LAPLACE, O.MASS):
+        csr = O.assemble_csr(om, op)
+        yref = O.gather(om, O.apply_dirichlet_csr(om, csr, xg))
+        y = to_host(gm.apply(x, op=op, prec=fe.FE_F64, flags=fe.FE_ASSEMBLE))
+        assert rel_max_err(y, yref) <= TOL64, op
+        # every copy of a node holds the same assembled value (bitwise)
+        gidx = O.gather(om, np.arange(om.n_unique, dtype=np.float64)).astype(np.int64)
+        hi = np.full(om.n_unique, -np.inf)
+        lo = np.full(om.n_unique, np.inf)
+        np.maximum.at(hi, gidx, y)
+        np.minimum.at(lo, gidx, y)
+        assert np.array_equal(hi, lo)
+
+
+def test_dss_multiplicity_and_random(fe):
+    m, p = (3, 4, 2), 3
+    om = oracle_mesh(m, p)
+    gm = fe.Mesh(m, p)
+    ones = torch.ones(gm.cellwise_len, dtype=torch.float64, device="cuda")
+    assert np.array_equal(to_host(gm.dss(ones)), O.multiplicity(om))
+    r = S.dual_cellwise(m, p, seed=5)
+    z = to_host(gm.dss(torch.from_numpy(r).cuda()))
+    assert rel_max_err(z, O.dss(om, r)) <= 1e-15
+    # in place, FP32
+    r32 = torch.from_numpy(r).float().cuda()
+    gm.dss(r32, prec=fe.FE_F32, z=r32)
+    assert rel_max_err(to_host(r32), O.dss(om, r)) <= 1e-6
+
+
+@pytest.mark.parametrize("p,amp,dirichlet", [(2, 0.1, True), (3, 0.1, False), (4, 0.0, True)])
+def test_diag_vs_oracle(fe, p, amp, dirichlet):
+    m = (3, 2, 4)
+    om = oracle_mesh(m, p, amp=amp, dirichlet=dirichlet)
+    for geom in ((fe.FE_GEOM_STORED, fe.FE_GEOM_AFFINE) if amp == 0 else (fe.FE_GEOM_STORED,)):
+        gm = fe.Mesh(m, p, deform_amp=amp, geom_mode=geom, dirichlet=dirichlet)
+        for op in (O.LAPLACE, O.MASS):
+            dref = O.gather(om, O.diag_global(om, op))
+            assert rel_max_err(to_host(gm.diag(op)), dref) <= TOL64
+
+
+def test_pairing_and_lemma(fe):
+    m, p = (4, 3, 3), 2
+    om = oracle_mesh(m, p)
+    gm = fe.Mesh(m, p)
+    f = S.dual_cellwise(m, p, seed=7)
+    u = S.primal_unique(m, p, seed=8)
+    uc = O.gather(om, u)
+    got = gm.pairing(torch.from_numpy(f).cuda(), torch.from_numpy(uc).cuda())
+    ref = float(np.sum(f * uc))
+    assert abs(got - ref) <= 1e-14 * np.abs(f * uc).sum()
+    # Lemma (Duality Pairing Identity): <f, G u> = <G^T f, u>
+    assert abs(got - O.scatter(om, f) @ u) <= 1e-13 * np.abs(f * uc).sum()
+    # bitwise reproducible
+    got2 = gm.pairing(torch.from_numpy(f).cuda(), torch.from_numpy(uc).cuda())
+    assert got == got2
+
+
+def test_edge_cases(fe):
+    # single cell: no interfaces, DSS is the identity
+    om = oracle_mesh(1, 4, amp=0.1)
+    gm = fe.Mesh(1, 4, deform_amp=0.1)
+    xc = S.dual_cellwise(1, 4, seed=1)
+    x = torch.from_numpy(xc).cuda()
+    y = to_host(gm.apply(x, flags=fe.FE_ASSEMBLE))
+    assert rel_max_err(y, O.apply_local(om, O.LAPLACE, xc)) <= TOL64
+    # thin meshes
+    for m in ((1, 1, 5), (6, 1, 1), (1, 7, 1)):
+        om = oracle_mesh(m, 2, amp=0.05, dirichlet=True)
+        gm = fe.Mesh(m, 2, deform_amp=0.05, dirichlet=True)
+        xg = S.primal_unique(m, 2, seed=2, dirichlet=True)
+        y = to_host(gm.apply(gm.gather(xg), flags=fe.FE_ASSEMBLE))
+        yref = O.gather(om, O.apply_dirichlet_csr(om, O.assemble_csr(om, O.LAPLACE), xg))
+        assert rel_max_err(y, yref) <= TOL64, m
+    # small input magnitudes keep their relative accuracy (the double-word range of the FP64
+    # path is |x| >= ~1e-20, see fe_internal.h)
+    om = oracle_mesh((2, 2, 2), 3, amp=0.1)
+    gm = fe.Mesh((2, 2, 2), 3, deform_amp=0.1)
+    xc = S.dual_cellwise((2, 2, 2), 3, seed=4) * 1e-20
+    y = to_host(gm.apply(torch.from_numpy(xc).cuda()))
+    assert rel_max_err(y, O.apply_local(om, O.LAPLACE, xc)) <= TOL64
+
+
+def test_invalid_arguments(fe):
+    d = fe.fe_mesh_desc(2, 2, 2, 8, 0.0, 0, 0, 0)
+    with pytest.raises(fe.FeError) as e:
+        fe.fe_mesh_create(d)
+    assert e.value.status == fe.FE_ERR_INVALID and "degree" in str(e.value)
+    gm = fe.Mesh(2, 2)
+    x = gm.empty()
+    with pytest.raises(fe.FeError):
+        fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_F64, x, x)  # overlap
+    with pytest.raises(fe.FeError):
+        fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_BF16_F32ACC, x, gm.empty())
+    with pytest.raises(fe.FeError):
+        fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_F64, 0, gm.empty())
+    with pytest.raises(fe.FeError):
+        fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_F64, x.data_ptr() + 8, gm.empty())
+
+
+FULL = [(2, 48), (3, 96), (7, 32)]
+
+
+@pytest.mark.parametrize("p,m", FULL)
+def test_full_size_sampled_parity(fe, p, m):
+    """Sweep sizes of the throughput benchmark (deformed, stored geometry, FE_ASSEMBLE): sampled
+    entries against the oracle's element rows, plus the constant-annihilation property."""
+    amp = 0.1
+    gm = fe.Mesh(m, p, deform_amp=amp)
+    om = oracle_mesh(m, p, amp=amp)
+    xg = S.primal_unique(m, p, seed=0)
+    x = gm.gather(xg)
+    rng = np.random.default_rng(p)
+    ncell = gm.n_cells
+    n3 = (p + 1) ** 3
+    samples = [(int(c), int(l)) for c, l in zip(rng.integers(0, ncell, 24), rng.integers(0, n3, 24))]
+    samples += [(0, 0), (ncell - 1, n3 - 1), (ncell // 2, n3 // 2)]
+    for op in (fe.FE_LAPLACE, fe.FE_MASS):
+        y = gm.apply(x, op=op, flags=fe.FE_ASSEMBLE)
+        got = np.array([y[c * n3 + l].item() for c, l in samples])
+        ref = sampled_assembled(om, op, xg, samples)
+        scale = y.abs().max().item()
+        assert np.abs(got - ref).max() <= TOL64 * scale, op
+        del y
+    ones = torch.ones(gm.cellwise_len, dtype=torch.float64, device="cuda")
+    y1 = gm.apply(ones, op=fe.FE_LAPLACE, flags=fe.FE_ASSEMBLE)
+    yx = gm.apply(x, op=fe.FE_LAPLACE, flags=fe.FE_ASSEMBLE)
+    assert y1.abs().max().item() <= 1e-12 * yx.abs().max().item()
