@@ -125,6 +125,20 @@ fe_status fe_diag(const fe_mesh* mesh, fe_op op, double* d_cell, void* stream);
 fe_status fe_pairing(const fe_mesh* mesh, fe_prec prec, const void* a, const void* b,
                      double* result_dev, void* stream);
 
+/* Duality pairing <a, b> as fe_pairing, but allocating nothing on any call.  The paper has no
+ * counterpart: this entry point serves callers that cannot let the library call cudaMalloc, such
+ * as a process whose device memory is all handed to its own pool (a caching allocator, or a
+ * serving loop that admits work against a fixed memory budget) or a latency-critical loop where
+ * an allocation, which may synchronize the device, is not acceptable.  Its scratch is a static
+ * device array of 8192 doubles (64 KiB, held on every device that loads the library until the
+ * process exits); one CTA reduces 8192 consecutive entries per scratch slot, so meshes with more
+ * than 67,108,864 cell-wise entries are rejected with FE_ERR_INVALID.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and should come before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.  Each call rewrites
+ * every slot it reads, so no clearing is needed.  Same arguments and errors as fe_pairing. */
+fe_status fe_pairing_noalloc(const fe_mesh* mesh, fe_prec prec, const void* a, const void* b,
+                             double* result_dev, void* stream);
+
 /* Conjugate gradients on cell-wise data (Algorithm "Communication-Free (Flexible) PCG") with the
  * Jacobi preconditioner P = D_cell^{-1} S.  Convergence (unspecified in the paper; reading):
  * ||G^T r||_2 / ||G^T b||_2 <= rtol over free nodes, evaluated on the device as

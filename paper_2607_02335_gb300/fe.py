@@ -62,6 +62,7 @@ _SIGS = {
     "fe_dss": [_MESH, _i, _vp, _vp, _vp],
     "fe_diag": [_MESH, _i, _vp, _vp],
     "fe_pairing": [_MESH, _i, _vp, _vp, _vp, _vp],
+    "fe_pairing_noalloc": [_MESH, _i, _vp, _vp, _vp, _vp],
     "fe_cg_solve": [_MESH, _vp, _vp, ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_cg_result), _vp],
 }
 for _name, _args in _SIGS.items():
@@ -141,6 +142,12 @@ def fe_diag(mesh: int, op: int, d, stream=None) -> None:
 def fe_pairing(mesh: int, prec: int, a, b, result_dev, stream=None) -> None:
     _check(_lib.fe_pairing(mesh, prec, _ptr(a), _ptr(b), _ptr(result_dev), _stream(stream)),
            "fe_pairing")
+
+
+def fe_pairing_noalloc(mesh: int, prec: int, a, b, result_dev, stream=None) -> None:
+    """fe_pairing without any device allocation (static scratch; see include/fe.h)."""
+    _check(_lib.fe_pairing_noalloc(mesh, prec, _ptr(a), _ptr(b), _ptr(result_dev), _stream(stream)),
+           "fe_pairing_noalloc")
 
 
 def fe_cg_solve(mesh: int, b, x, opts: fe_cg_opts, stream=None) -> fe_cg_result:

@@ -1,0 +1,50 @@
+"""fe_pairing_noalloc: the duality pairing for callers that cannot let the library allocate
+device memory (their memory is all in their own pool, or an allocation's possible device
+synchronization is not acceptable on their path).  It must agree with fe_pairing, the entry point
+whose partial sums live in library-allocated scratch, on consecutive calls that share the static
+scratch array.  This file is collected last so that a failure here comes after every other test."""
+import numpy as np
+import pytest
+
+from paper_2607_02335_gb300 import synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-14  # relative to sum |a_e b_e|, as in the fe_pairing parity test
+
+
+def _pair(fe, gm, prec, a, b, fn):
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    fn(gm.handle, prec, a, b, out)
+    torch.cuda.synchronize()
+    return out.item()
+
+
+def test_noalloc_pairing_matches_pairing_on_consecutive_calls():
+    from paper_2607_02335_gb300 import fe
+
+    cases = [((6, 5, 4), 3, 11), ((3, 2, 2), 2, 12)]  # larger first: stale slots must not leak
+    for m, p, seed in cases:
+        gm = fe.Mesh(m, p, geom_mode=fe.FE_GEOM_AFFINE)
+        a = torch.from_numpy(S.dual_cellwise(m, p, seed=seed)).cuda()
+        b = torch.from_numpy(S.dual_cellwise(m, p, seed=seed + 100)).cuda()
+        scale = float((a * b).abs().sum().item())
+        for prec, (x, y) in ((fe.FE_F64, (a, b)), (fe.FE_F32, (a.float(), b.float()))):
+            ref = _pair(fe, gm, prec, x, y, fe.fe_pairing)
+            got = _pair(fe, gm, prec, x, y, fe.fe_pairing_noalloc)
+            assert abs(got - ref) <= TOL * scale, (m, p, prec)
+        gm.close()
+
+
+def test_noalloc_pairing_rejects_meshes_beyond_its_scratch():
+    from paper_2607_02335_gb300 import fe
+
+    gm = fe.Mesh((64, 64, 33), 7, geom_mode=fe.FE_GEOM_AFFINE)  # 69,206,016 cell-wise entries
+    assert gm.cellwise_len > 8192 * 8192
+    small = torch.zeros(16, dtype=torch.float64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(fe.FeError) as e:
+        fe.fe_pairing_noalloc(gm.handle, fe.FE_F64, small, small, out)
+    assert e.value.status == fe.FE_ERR_INVALID and "static scratch limit" in str(e.value)
+    gm.close()
