@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="tiny sizes (plumbing check only)")
+    ap.add_argument("--profile-case", default=None,
+                    help="p,m,op: only run K+W applies of one case (for profiler captures)")
     return ap.parse_args()
 
 
@@ -355,8 +357,30 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """One (degree, cells, operator) case applied W+K times with FE_ASSEMBLE; no timing."""
+    import torch
+
+    from paper_2607_02335_gb300 import fe
+    from paper_2607_02335_gb300 import synth as S
+
+    p, m, opname = args.profile_case.split(",")
+    p, m = int(p), int(m)
+    op = fe.FE_LAPLACE if opname == "laplace" else fe.FE_MASS
+    gm = fe.Mesh(m, p, deform_amp=AMP)
+    x = gm.gather(S.primal_unique(m, p, seed=0))
+    y = gm.empty()
+    for _ in range(args.warmup + args.steps):
+        fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, fe.FE_ASSEMBLE)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "launches": args.warmup + args.steps}))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
