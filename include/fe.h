@@ -151,7 +151,10 @@ typedef struct {
   int maxit;         /* iteration cap (inner iterations in total for mixed) */
   int mixed;         /* 0 = FP64, FE_F32 = FP32 inner solve under FP64 refinement */
   int flexible;      /* 1 = FCG beta */
-  double inner_rtol; /* mixed only: relative reduction per inner solve */
+  double inner_rtol; /* mixed only: relative reduction per inner solve (<= 0: 1e-2); an inner
+                        solve also stops after 20 iterations without a 10% residual drop */
+  double* history;   /* nullable HOST array of 3*maxit doubles; FP64 solves write, for iteration
+                        k, alpha_k, beta_k and the relative residual after the update */
 } fe_cg_opts;
 typedef struct {
   int iters;        /* total CG iterations (inner iterations for mixed) */

@@ -128,6 +128,7 @@ struct ApplyArgs {
   int mx, my, mz;
   int dirichlet;
   V aff[4];  // affine mode: detJ/h_x^2, detJ/h_y^2, detJ/h_z^2, detJ
+  const int* skip;  // optional device flag: the whole launch returns at once when *skip != 0
   Tab1D<N, V> tab;
 };
 
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
   const Sm<V> s1(smraw, NARR, NARR > 1 ? 1 : 0, C::TILE);
   const Sm<V> s2(smraw, NARR, NARR > 2 ? 2 : 0, C::TILE);
 
+  if (a.skip && *(volatile const int*)a.skip) return;  // uniform over the grid
   const int t = threadIdx.x;
   const int cl = t / N2;
   const int lt = t - cl * N2;

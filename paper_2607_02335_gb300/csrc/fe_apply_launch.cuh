@@ -58,6 +58,7 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
   a.my = m->d.my;
   a.mz = m->d.mz;
   a.dirichlet = m->d.dirichlet;
+  a.skip = L.skip;
   const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / m->d.mz, det = hx * hy * hz;
   a.aff[0] = fe_cast<V>(det / (hx * hx));
   a.aff[1] = fe_cast<V>(det / (hy * hy));

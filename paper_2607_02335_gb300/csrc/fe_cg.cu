@@ -1,9 +1,642 @@
-// fe_cg.cu -- conjugate gradients on cell-wise data.
+// fe_cg.cu -- conjugate gradients on cell-wise data (Sec. 3.2, Algorithm "Communication-Free
+// (Flexible) PCG") with the Jacobi preconditioner P = D_cell^{-1} S (Sec. 3.3).
+//
+// Every vector of the iteration is cell-wise: u, p, z primal (continuous), r, q dual.  The only
+// inter-element step is the DSS inside the preconditioner; every scalar is a duality pairing of
+// one dual and one primal vector (Lemma "Duality Pairing Identity"), so the iterates equal those
+// of CG on the assembled system (Theorem "Equivalence of Communication-Free FCG").
+//
+// One iteration is a fixed launch sequence captured once into a CUDA graph:
+//   q = A p;  <q,p> -> alpha;  u += alpha p, r -= alpha q;  w = S r;
+//   z = D^{-1} w (0 on Dirichlet nodes) with sum w^2/mult, <r,z> (and <q,z> for FCG) -> beta;
+//   p = z + beta p.
+// alpha, beta, the residual and the stop flag stay in device memory; every kernel returns at once
+// when the flag is set, so the host replays the graph several times between two reads of the flag.
+// Convergence (unspecified in the paper): ||G^T r||_2 / ||G^T b||_2 <= rtol over free nodes, with
+// ||G^T r||^2 = sum_e (S r)_e^2 / mult_e.
+//
+// Mixed precision: FP64 iterative refinement.  r = b - A x with the FP64 apply, an FP32 PCG solves
+// A d = r (FP32 vectors and operator, FP64-accumulated pairings) to inner_rtol, x += d in FP64.
+#include <cmath>
+#include <cstring>
+#include <new>
+
 #include "fe_vec.cuh"
+
+namespace {
+
+struct CgScal {
+  double rz, rz_new, qp, qz, alpha, beta, rnorm2, bnorm2, relres;
+  double best;      // smallest relative residual so far
+  int done, status, iter, maxit;
+  int stall;        // iterations since `best` last dropped by 10%
+  int stall_limit;  // stop after this many iterations without progress (0 = never)
+};
+
+enum { FIN_INIT_B = 0, FIN_INIT_R = 1, FIN_ITER = 2 };
+
+// ---- element-wise kernels -------------------------------------------------------------------
+__global__ void k_invmult(float* __restrict__ out, long long ncells, int n, int mx, int my, int mz,
+                          int dirichlet) {
+  const int n3 = n * n * n, p = n - 1;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long c = warp; c < ncells; c += nwarps) {
+    const int cx = (int)(c % mx), cy = (int)((c / mx) % my), cz = (int)(c / ((long long)mx * my));
+    for (int l = lane; l < n3; l += 32) {
+      const int i = l % n, j = (l / n) % n, k = l / (n * n);
+      const int gx = cx * p + i, gy = cy * p + j, gz = cz * p + k;
+      int mult = 1;
+      if (gx % p == 0 && gx > 0 && gx < mx * p) mult *= 2;
+      if (gy % p == 0 && gy > 0 && gy < my * p) mult *= 2;
+      if (gz % p == 0 && gz > 0 && gz < mz * p) mult *= 2;
+      const bool bnd = dirichlet && (gx == 0 || gx == mx * p || gy == 0 || gy == my * p ||
+                                     gz == 0 || gz == mz * p);
+      out[c * n3 + l] = bnd ? 0.0f : 1.0f / (float)mult;
+    }
+  }
+}
+
+__global__ void k_invdiag(const double* __restrict__ d, const float* __restrict__ invmult,
+                          double* __restrict__ inv64, float* __restrict__ inv32, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double v = invmult[e] == 0.0f ? 0.0 : 1.0 / d[e];
+    inv64[e] = v;
+    inv32[e] = (float)v;
+  }
+}
+
+// r = b - q
+__global__ void k_residual(const double* __restrict__ b, const double* __restrict__ q,
+                           double* __restrict__ r, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    r[e] = b[e] - q[e];
+}
+
+// Inner right-hand side r32 = s * (S r) / mult, d32 = 0.  The dual residual r is unassembled: the
+// copies of a node hold partial integrals that cancel when summed, so near convergence single
+// copies are orders of magnitude larger than G^T r.  Rounding them to FP32 would destroy the
+// assembled value; the residual is therefore assembled in FP64 first (w = S r) and its value is
+// split evenly over the copies.  G^T r32 = s G^T r, and every pairing with a continuous vector is
+// unchanged (Lemma "Duality Pairing Identity").
+__global__ void k_to_inner(const double* __restrict__ w, const float* __restrict__ invmult,
+                           float* __restrict__ r32, float* __restrict__ d32, double s, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    r32[e] = (float)(s * w[e] * (double)invmult[e]);
+    d32[e] = 0.0f;
+  }
+}
+
+// x += d / s
+__global__ void k_correct(double* __restrict__ x, const float* __restrict__ d, double inv_s,
+                          long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e] += inv_s * (double)d[e];
+}
+
+// u += alpha p ; r -= alpha q
+template <class S, class U>
+__global__ void k_update_ur(U* __restrict__ u, S* __restrict__ r, const S* __restrict__ p,
+                            const S* __restrict__ q, const CgScal* __restrict__ sc, long long n) {
+  if (*(volatile const int*)&sc->done) return;
+  const double a = sc->alpha;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    u[e] = (U)((double)u[e] + a * (double)p[e]);
+    r[e] = (S)((double)r[e] - a * (double)q[e]);
+  }
+}
+
+template <>
+__global__ void k_update_ur<float, float>(float* __restrict__ u, float* __restrict__ r,
+                                          const float* __restrict__ p, const float* __restrict__ q,
+                                          const CgScal* __restrict__ sc, long long n) {
+  if (*(volatile const int*)&sc->done) return;
+  const float a = (float)sc->alpha;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    u[e] = fmaf(a, p[e], u[e]);
+    r[e] = fmaf(-a, q[e], r[e]);
+  }
+}
+
+// p = z + beta p
+template <class S>
+__global__ void k_update_p(S* __restrict__ p, const S* __restrict__ z, const CgScal* __restrict__ sc,
+                           long long n) {
+  if (*(volatile const int*)&sc->done) return;
+  const S b = (S)sc->beta;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    p[e] = z[e] + b * p[e];
+}
+
+template <class S>
+__device__ __forceinline__ dw prod_dw(S a, S b);
+template <>
+__device__ __forceinline__ dw prod_dw<double>(double a, double b) {
+  return dw_mul(dw_from_double(a), dw_from_double(b));
+}
+template <>
+__device__ __forceinline__ dw prod_dw<float>(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// partial of <q, p>  (slot 0)
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_qp(const S* __restrict__ q, const S* __restrict__ p, double* __restrict__ partials,
+         const CgScal* __restrict__ sc, long long n) {
+  if (*(volatile const int*)&sc->done) return;
+  __shared__ dw sh[32];
+  dw acc = {0.0f, 0.0f};
+  for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n;
+       e += (long long)RED_BLOCKS * RED_THREADS)
+    acc = dw_add(acc, prod_dw<S>(q[e], p[e]));
+  acc = block_reduce_dw(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = dw_to_double(acc);
+}
+
+// z = w * invdiag (when z != null); partials: slot 0 sum w^2 invmult, slot 1 <r,z>, slot 2 <q,z>
+// With `redistribute` the dual residual is replaced by its assembled value split evenly over the
+// copies, r = (S r) / mult (0 on Dirichlet nodes): the same G^T r and the same pairings with
+// continuous vectors, without the cancelling per-copy parts that FP32 cannot hold.
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_precond(const S* __restrict__ w, S* __restrict__ r, const S* __restrict__ q,
+              const S* __restrict__ invdiag, const float* __restrict__ invmult, S* __restrict__ z,
+              double* __restrict__ partials, const CgScal* __restrict__ sc, long long n,
+              int check_done, int redistribute) {
+  if (check_done && *(volatile const int*)&sc->done) return;
+  __shared__ dw sh[32];
+  dw a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
+  for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n;
+       e += (long long)RED_BLOCKS * RED_THREADS) {
+    const S we = w[e];
+    const dw w2 = prod_dw<S>(we, we);
+    const float im = invmult[e];  // a power of two or zero: exact scaling
+    a0 = dw_add(a0, {w2.h * im, w2.l * im});
+    if (z) {
+      const S ze = we * invdiag[e];
+      z[e] = ze;
+      S re;
+      if (redistribute) {
+        re = we * (S)im;
+        r[e] = re;
+      } else {
+        re = r[e];
+      }
+      a1 = dw_add(a1, prod_dw<S>(re, ze));
+      if (q) a2 = dw_add(a2, prod_dw<S>(q[e], ze));
+    }
+  }
+  a0 = block_reduce_dw(a0, sh);
+  if (threadIdx.x == 0) partials[0 * RED_BLOCKS + blockIdx.x] = dw_to_double(a0);
+  if (z) {
+    a1 = block_reduce_dw(a1, sh);
+    if (threadIdx.x == 0) partials[1 * RED_BLOCKS + blockIdx.x] = dw_to_double(a1);
+    if (q) {
+      a2 = block_reduce_dw(a2, sh);
+      if (threadIdx.x == 0) partials[2 * RED_BLOCKS + blockIdx.x] = dw_to_double(a2);
+    }
+  }
+}
+
+__device__ double sum_slot(const double* partials, int slot, dw* sh) {
+  dw acc = {0.0f, 0.0f};
+  for (int b = threadIdx.x; b < RED_BLOCKS; b += RED_THREADS)
+    acc = dw_add(acc, dw_from_double(partials[slot * RED_BLOCKS + b]));
+  acc = block_reduce_dw(acc, sh);
+  return dw_to_double(acc);  // valid in thread 0
+}
+
+// alpha = <r,z>/<q,p>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_fin_alpha(const double* __restrict__ partials, CgScal* __restrict__ sc, double* hist) {
+  if (*(volatile const int*)&sc->done) return;
+  __shared__ dw sh[32];
+  const double qp = sum_slot(partials, 0, sh);
+  if (threadIdx.x == 0) {
+    sc->qp = qp;
+    if (!(qp > 0.0) || !isfinite(qp) || !isfinite(sc->rz)) {
+      sc->status = FE_ERR_BREAKDOWN;
+      sc->done = 1;
+    } else {
+      sc->alpha = sc->rz / qp;
+      if (hist) hist[3 * sc->iter + 0] = sc->alpha;
+    }
+  }
+}
+
+// residual norm, convergence test and beta
+__global__ void __launch_bounds__(RED_THREADS)
+    k_fin_beta(const double* __restrict__ partials, CgScal* __restrict__ sc, double rtol, int mode,
+               int flexible, double* hist) {
+  if (mode == FIN_ITER && *(volatile const int*)&sc->done) return;
+  __shared__ dw sh[32];
+  const double rn2 = sum_slot(partials, 0, sh);
+  const double rz = (mode != FIN_INIT_B) ? sum_slot(partials, 1, sh) : 0.0;
+  const double qz = (mode == FIN_ITER && flexible) ? sum_slot(partials, 2, sh) : 0.0;
+  if (threadIdx.x != 0) return;
+  if (mode == FIN_INIT_B) {
+    sc->bnorm2 = rn2;
+    return;
+  }
+  sc->rnorm2 = rn2;
+  const double rel = sc->bnorm2 > 0.0 ? sqrt(rn2 / sc->bnorm2) : 0.0;
+  sc->relres = rel;
+  if (mode == FIN_INIT_R) {
+    sc->rz = rz;
+    sc->best = rel;
+    sc->stall = 0;
+    sc->iter = 0;
+    sc->status = FE_OK;
+    sc->done = (rel <= rtol) ? 1 : 0;
+    return;
+  }
+  const int k = sc->iter;
+  if (hist) hist[3 * k + 2] = rel;
+  sc->iter = k + 1;
+  if (!isfinite(rel)) {
+    sc->status = FE_ERR_BREAKDOWN;
+    sc->done = 1;
+    return;
+  }
+  if (rel <= rtol) {
+    sc->status = FE_OK;
+    sc->done = 1;
+    return;
+  }
+  // Stagnation guard of the FP32 inner solve: FP32 rounding makes the operator slightly
+  // non-symmetric, and CG then levels off near eps_32 * cond(A); the FP64 outer refinement takes
+  // over from there.
+  if (rel < 0.9 * sc->best) {
+    sc->best = rel;
+    sc->stall = 0;
+  } else if (sc->stall_limit > 0 && ++sc->stall >= sc->stall_limit) {
+    sc->status = FE_OK;
+    sc->done = 1;
+    return;
+  }
+  if (k + 1 >= sc->maxit) {
+    sc->status = FE_ERR_NOT_CONVERGED;
+    sc->done = 1;
+    return;
+  }
+  const double beta = flexible ? -qz / sc->qp : rz / sc->rz;
+  sc->beta = beta;
+  sc->rz = rz;
+  if (hist) hist[3 * k + 1] = beta;
+}
+
+unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---- workspace -------------------------------------------------------------------------------
+struct CgWork {
+  long long n = 0;
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *w = nullptr;
+  float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *w32 = nullptr,
+        *d32 = nullptr;
+  double* invdiag64 = nullptr;
+  float* invdiag32 = nullptr;
+  float* invmult = nullptr;
+  double* partials = nullptr;
+  CgScal* sc = nullptr;   // [0] outer / FP64 solve, [1] inner FP32 solve
+  CgScal* hsc = nullptr;  // pinned host mirror
+  double* hist = nullptr;
+  int hist_cap = 0;
+  int diag_op = -1;
+  cudaStream_t st = nullptr;
+  cudaGraphExec_t g64[2] = {nullptr, nullptr};  // [flexible]
+  cudaGraphExec_t g32[2] = {nullptr, nullptr};
+  double* g64_hist = nullptr;
+};
+
+void free_work(CgWork* w) {
+  if (!w) return;
+  for (int f = 0; f < 2; ++f) {
+    if (w->g64[f]) cudaGraphExecDestroy(w->g64[f]);
+    if (w->g32[f]) cudaGraphExecDestroy(w->g32[f]);
+  }
+  double* d[] = {w->x, w->r, w->z, w->p, w->q, w->w, w->invdiag64, w->partials, w->hist};
+  for (double* v : d) cudaFree(v);
+  float* f[] = {w->r32, w->z32, w->p32, w->q32, w->w32, w->d32, w->invdiag32, w->invmult};
+  for (float* v : f) cudaFree(v);
+  cudaFree(w->sc);
+  cudaFreeHost(w->hsc);
+  if (w->st) cudaStreamDestroy(w->st);
+  delete w;
+}
+
+fe_status get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
+  fe_mesh* m = const_cast<fe_mesh*>(cm);
+  CgWork* w = static_cast<CgWork*>(m->cg_work);
+  if (!w) {
+    w = new (std::nothrow) CgWork();
+    if (!w) {
+      fe_set_error("fe_cg_solve: host allocation failed");
+      return FE_ERR_OOM;
+    }
+    m->cg_work = w;
+    m->cg_free = [](void* p) { free_work(static_cast<CgWork*>(p)); };
+    const long long n = m->ncw;
+    w->n = n;
+    FE_CUDA(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking), "cg stream");
+    double** d[] = {&w->x, &w->r, &w->z, &w->p, &w->q, &w->w, &w->invdiag64};
+    for (double** v : d) FE_CUDA(cudaMalloc(v, n * sizeof(double)), "cudaMalloc cg vector");
+    FE_CUDA(cudaMalloc(&w->invdiag32, n * sizeof(float)), "cudaMalloc cg vector");
+    FE_CUDA(cudaMalloc(&w->invmult, n * sizeof(float)), "cudaMalloc cg vector");
+    FE_CUDA(cudaMalloc(&w->partials, (size_t)RED_BLOCKS * RED_SLOTS * sizeof(double)), "cudaMalloc");
+    FE_CUDA(cudaMalloc(&w->sc, 2 * sizeof(CgScal)), "cudaMalloc cg scalars");
+    FE_CUDA(cudaMallocHost(&w->hsc, 2 * sizeof(CgScal)), "cudaMallocHost cg scalars");
+    k_invmult<<<grid_for(m->ncells * 32), 256, 0, w->st>>>(w->invmult, m->ncells, m->n, m->d.mx,
+                                                           m->d.my, m->d.mz, m->d.dirichlet);
+    FE_CUDA(cudaGetLastError(), "invmult launch");
+  }
+  if (mixed && !w->r32) {
+    float** f[] = {&w->r32, &w->z32, &w->p32, &w->q32, &w->w32, &w->d32};
+    for (float** v : f) FE_CUDA(cudaMalloc(v, w->n * sizeof(float)), "cudaMalloc cg fp32 vector");
+  }
+  *out = w;
+  return FE_OK;
+}
+
+fe_status ensure_diag(const fe_mesh* m, CgWork* w, int op) {
+  if (w->diag_op == op) return FE_OK;
+  // w->q as scratch for the assembled diagonal
+  FE_TRY(fe_launch_diag(m, op, w->q, w->st));
+  k_invdiag<<<grid_for(w->n), 256, 0, w->st>>>(w->q, w->invmult, w->invdiag64, w->invdiag32, w->n);
+  FE_CUDA(cudaGetLastError(), "invdiag launch");
+  w->diag_op = op;
+  return FE_OK;
+}
+
+// one PCG iteration on vectors of type S, solution of type U, scalars sc
+template <class S, class U>
+fe_status enqueue_iteration(const fe_mesh* m, CgWork* w, int op, bool flexible, double rtol,
+                            U* u, S* r, S* z, S* p, S* q, S* wv, const S* invdiag, CgScal* sc,
+                            double* hist) {
+  const long long n = w->n;
+  ApplyLaunch L{m, op, p, q, w->st, &sc->done};
+  if (sizeof(S) == 8)
+    FE_TRY(fe_launch_apply_f64dw(L));
+  else
+    FE_TRY(fe_launch_apply_f32(L));
+  k_qp<S><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(q, p, w->partials, sc, n);
+  k_fin_alpha<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, hist);
+  k_update_ur<S, U><<<grid_for(n), 256, 0, w->st>>>(u, r, p, q, sc, n);
+  FE_CUDA(cudaMemcpyAsync(wv, r, n * sizeof(S), cudaMemcpyDeviceToDevice, w->st), "cg copy");
+  FE_TRY(fe_launch_dss(m, sizeof(S) == 8 ? FE_F64 : FE_F32, wv, w->st));
+  k_precond<S><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(wv, r, flexible ? q : nullptr, invdiag,
+                                                      w->invmult, z, w->partials, sc, n, 1,
+                                                      sizeof(S) == 4 ? 1 : 0);
+  k_fin_beta<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, rtol, FIN_ITER, flexible ? 1 : 0, hist);
+  k_update_p<S><<<grid_for(n), 256, 0, w->st>>>(p, z, sc, n);
+  return fe_cuda_check(cudaGetLastError(), "cg iteration launch");
+}
+
+template <class S, class U>
+fe_status build_graph(const fe_mesh* m, CgWork* w, int op, bool flexible, double rtol, U* u, S* r,
+                      S* z, S* p, S* q, S* wv, const S* invdiag, CgScal* sc, double* hist,
+                      cudaGraphExec_t* exec) {
+  cudaGraph_t g = nullptr;
+  {  // one uncaptured apply first, so that per-kernel attributes are set outside the capture
+    ApplyLaunch L{m, op, p, q, w->st, &sc->done};
+    FE_TRY(sizeof(S) == 8 ? fe_launch_apply_f64dw(L) : fe_launch_apply_f32(L));
+  }
+  FE_CUDA(cudaStreamBeginCapture(w->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  fe_status s = enqueue_iteration<S, U>(m, w, op, flexible, rtol, u, r, z, p, q, wv, invdiag, sc, hist);
+  cudaError_t e = cudaStreamEndCapture(w->st, &g);
+  if (s != FE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  FE_CUDA(e, "end capture");
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return fe_cuda_check(e, "graph instantiate");
+}
+
+// run graph replays until the flag is set; returns the host copy of the scalars
+fe_status run_until_done(CgWork* w, cudaGraphExec_t exec, int slot, CgScal* out) {
+  const int batch = 8;
+  for (;;) {
+    for (int b = 0; b < batch; ++b) FE_CUDA(cudaGraphLaunch(exec, w->st), "graph launch");
+    FE_CUDA(cudaMemcpyAsync(&w->hsc[slot], &w->sc[slot], sizeof(CgScal), cudaMemcpyDeviceToHost,
+                            w->st),
+            "scalar readback");
+    FE_CUDA(cudaStreamSynchronize(w->st), "cg synchronize");
+    if (w->hsc[slot].done) break;
+  }
+  *out = w->hsc[slot];
+  return FE_OK;
+}
+
+fe_status set_scal(CgWork* w, int slot, int maxit, int stall_limit = 0) {
+  CgScal s;
+  std::memset(&s, 0, sizeof(s));
+  s.maxit = maxit;
+  s.stall_limit = stall_limit;
+  w->hsc[slot] = s;
+  return fe_cuda_check(
+      cudaMemcpyAsync(&w->sc[slot], &w->hsc[slot], sizeof(CgScal), cudaMemcpyHostToDevice, w->st),
+      "scalar upload");
+}
+
+fe_status read_scal(CgWork* w, int slot, CgScal* out) {
+  FE_CUDA(cudaMemcpyAsync(&w->hsc[slot], &w->sc[slot], sizeof(CgScal), cudaMemcpyDeviceToHost, w->st),
+          "scalar readback");
+  FE_CUDA(cudaStreamSynchronize(w->st), "cg synchronize");
+  *out = w->hsc[slot];
+  return FE_OK;
+}
+
+// ||G^T v||^2 / bnorm into slot's scalars: w = S v, precond kernel without z
+template <class S>
+fe_status residual_norm(const fe_mesh* m, CgWork* w, const S* v, S* wv, CgScal* sc, int mode) {
+  FE_CUDA(cudaMemcpyAsync(wv, v, w->n * sizeof(S), cudaMemcpyDeviceToDevice, w->st), "cg copy");
+  FE_TRY(fe_launch_dss(m, sizeof(S) == 8 ? FE_F64 : FE_F32, wv, w->st));
+  k_precond<S><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(wv, nullptr, nullptr, nullptr, w->invmult,
+                                                      nullptr, w->partials, sc, w->n, 0, 0);
+  k_fin_beta<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, 0.0, mode, 0, nullptr);
+  return fe_cuda_check(cudaGetLastError(), "residual norm launch");
+}
+
+// initial preconditioned residual: w = S r, z = D^{-1} w, <r,z>, relres; p = z
+template <class S>
+fe_status init_direction(const fe_mesh* m, CgWork* w, S* r, S* z, S* p, S* wv, const S* invdiag,
+                         CgScal* sc, double rtol) {
+  FE_CUDA(cudaMemcpyAsync(wv, r, w->n * sizeof(S), cudaMemcpyDeviceToDevice, w->st), "cg copy");
+  FE_TRY(fe_launch_dss(m, sizeof(S) == 8 ? FE_F64 : FE_F32, wv, w->st));
+  k_precond<S><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(wv, r, nullptr, invdiag, w->invmult, z,
+                                                      w->partials, sc, w->n, 0, sizeof(S) == 4 ? 1 : 0);
+  k_fin_beta<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, rtol, FIN_INIT_R, 0, nullptr);
+  FE_CUDA(cudaMemcpyAsync(p, z, w->n * sizeof(S), cudaMemcpyDeviceToDevice, w->st), "cg copy");
+  return fe_cuda_check(cudaGetLastError(), "init launch");
+}
+
+}  // namespace
 
 extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
                                  const fe_cg_opts* opts, fe_cg_result* res, void* stream) {
-  (void)m; (void)b; (void)x; (void)opts; (void)res; (void)stream;
-  fe_set_error("fe_cg_solve: not available in this build");
-  return FE_ERR_INVALID;
+  if (!m || !b || !x || !opts || !res) {
+    fe_set_error("fe_cg_solve: null argument");
+    return FE_ERR_INVALID;
+  }
+  if (!fe_aligned(b) || !fe_aligned(x)) {
+    fe_set_error("fe_cg_solve: vectors must be 16-byte aligned");
+    return FE_ERR_INVALID;
+  }
+  if (opts->maxit < 1 || !(opts->rtol >= 0.0) || (opts->mixed != 0 && opts->mixed != FE_F32)) {
+    fe_set_error("fe_cg_solve: invalid options (maxit %d, rtol %g, mixed %d)", opts->maxit,
+                 opts->rtol, opts->mixed);
+    return FE_ERR_INVALID;
+  }
+  if (m->d.geom_mode == FE_GEOM_RECOMPUTE) {
+    fe_set_error("fe_cg_solve: needs stored or affine geometry");
+    return FE_ERR_INVALID;
+  }
+  std::memset(res, 0, sizeof(*res));
+  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  const bool mixed = opts->mixed == FE_F32;
+  const int op = FE_LAPLACE;
+  CgWork* w = nullptr;
+  FE_TRY(get_work(m, mixed, &w));
+  FE_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cg: caller stream");
+  FE_TRY(fe_ensure_geometry(m, FE_F64, false));
+  if (mixed) FE_TRY(fe_ensure_geometry(m, FE_F32, false));
+  FE_TRY(ensure_diag(m, w, op));
+  const long long n = w->n;
+  const int flex = opts->flexible ? 1 : 0;
+  if (opts->history && (!w->hist || w->hist_cap < opts->maxit)) {
+    cudaFree(w->hist);
+    w->hist = nullptr;
+    FE_CUDA(cudaMalloc(&w->hist, 3 * (size_t)opts->maxit * sizeof(double)), "cudaMalloc history");
+    w->hist_cap = opts->maxit;
+    for (int f = 0; f < 2; ++f)
+      if (w->g64[f]) {
+        cudaGraphExecDestroy(w->g64[f]);
+        w->g64[f] = nullptr;
+      }
+  }
+  double* hist = opts->history ? w->hist : nullptr;
+  if (w->g64_hist != hist) {  // graphs bake the history pointer in
+    for (int f = 0; f < 2; ++f)
+      if (w->g64[f]) {
+        cudaGraphExecDestroy(w->g64[f]);
+        w->g64[f] = nullptr;
+      }
+    w->g64_hist = hist;
+  }
+
+  // u := x, ||G^T b||
+  FE_CUDA(cudaMemcpyAsync(w->x, x, n * sizeof(double), cudaMemcpyDeviceToDevice, w->st), "cg copy");
+  FE_TRY(set_scal(w, 0, opts->maxit));
+  FE_TRY(residual_norm<double>(m, w, b, w->w, &w->sc[0], FIN_INIT_B));
+  CgScal h;
+  FE_TRY(read_scal(w, 0, &h));
+  const double bnorm2 = h.bnorm2;
+  if (!(bnorm2 > 0.0)) {  // zero right-hand side: the solution is zero
+    FE_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), w->st), "cg zero");
+    FE_CUDA(cudaStreamSynchronize(w->st), "cg synchronize");
+    res->iters = 0;
+    res->outer_iters = 0;
+    res->rel_res = 0.0;
+    res->status = FE_OK;
+    return FE_OK;
+  }
+  fe_status status = FE_OK;
+
+  if (!mixed) {
+    // r = b - A u, z = P r, p = z
+    ApplyLaunch L{m, op, w->x, w->q, w->st, nullptr};
+    FE_TRY(fe_launch_apply_f64dw(L));
+    k_residual<<<grid_for(n), 256, 0, w->st>>>(b, w->q, w->r, n);
+    FE_TRY(init_direction<double>(m, w, w->r, w->z, w->p, w->w, w->invdiag64, &w->sc[0], opts->rtol));
+    FE_TRY(read_scal(w, 0, &h));
+    if (!h.done) {
+      if (!w->g64[flex])
+        FE_TRY((build_graph<double, double>(m, w, op, flex, opts->rtol, w->x, w->r, w->z, w->p, w->q,
+                                            w->w, w->invdiag64, &w->sc[0], hist, &w->g64[flex])));
+      FE_TRY(run_until_done(w, w->g64[flex], 0, &h));
+    }
+    res->iters = h.iter;
+    res->outer_iters = 1;
+    res->rel_res = h.relres;
+    status = (fe_status)h.status;
+    if (hist && h.iter > 0)
+      FE_CUDA(cudaMemcpy(opts->history, hist, 3 * (size_t)h.iter * sizeof(double),
+                         cudaMemcpyDeviceToHost),
+              "history readback");
+  } else {
+    int total = 0, outer = 0;
+    for (;;) {
+      // FP64 residual of the current iterate
+      ApplyLaunch L{m, op, w->x, w->q, w->st, nullptr};
+      FE_TRY(fe_launch_apply_f64dw(L));
+      k_residual<<<grid_for(n), 256, 0, w->st>>>(b, w->q, w->r, n);
+      FE_TRY(residual_norm<double>(m, w, w->r, w->w, &w->sc[0], FIN_INIT_R));
+      FE_TRY(read_scal(w, 0, &h));
+      const double rel = sqrt(h.rnorm2 / bnorm2);
+      res->rel_res = rel;
+      if (rel <= opts->rtol) {
+        status = FE_OK;
+        break;
+      }
+      if (!std::isfinite(rel)) {
+        status = FE_ERR_BREAKDOWN;
+        break;
+      }
+      if (total >= opts->maxit) {
+        status = FE_ERR_NOT_CONVERGED;
+        break;
+      }
+      // inner FP32 PCG on A d = s r
+      const double s = 1.0 / sqrt(h.rnorm2);
+      k_to_inner<<<grid_for(n), 256, 0, w->st>>>(w->w, w->invmult, w->r32, w->d32, s, n);
+      FE_TRY(set_scal(w, 1, opts->maxit - total, 20));
+      FE_TRY(residual_norm<float>(m, w, w->r32, w->w32, &w->sc[1], FIN_INIT_B));
+      const double irtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 1e-2;
+      FE_TRY(init_direction<float>(m, w, w->r32, w->z32, w->p32, w->w32, w->invdiag32, &w->sc[1],
+                                   irtol));
+      FE_TRY(read_scal(w, 1, &h));
+      if (!h.done) {
+        if (!w->g32[flex])
+          FE_TRY((build_graph<float, float>(m, w, op, flex, irtol, w->d32, w->r32, w->z32, w->p32,
+                                            w->q32, w->w32, w->invdiag32, &w->sc[1], nullptr,
+                                            &w->g32[flex])));
+        FE_TRY(run_until_done(w, w->g32[flex], 1, &h));
+      }
+      if (h.status == FE_ERR_BREAKDOWN && h.iter == 0) {
+        status = FE_ERR_BREAKDOWN;
+        break;
+      }
+      total += h.iter;
+      ++outer;
+      k_correct<<<grid_for(n), 256, 0, w->st>>>(w->x, w->d32, 1.0 / s, n);
+      FE_CUDA(cudaGetLastError(), "correction launch");
+      if (outer > 200) {
+        status = FE_ERR_NOT_CONVERGED;
+        break;
+      }
+    }
+    res->iters = total;
+    res->outer_iters = outer;
+  }
+  FE_CUDA(cudaMemcpyAsync(x, w->x, n * sizeof(double), cudaMemcpyDeviceToDevice, w->st), "cg copy");
+  FE_CUDA(cudaStreamSynchronize(w->st), "cg synchronize");
+  res->status = status;
+  if (status == FE_ERR_NOT_CONVERGED) fe_set_error("fe_cg_solve: not converged");
+  if (status == FE_ERR_BREAKDOWN) fe_set_error("fe_cg_solve: breakdown");
+  return status;
 }

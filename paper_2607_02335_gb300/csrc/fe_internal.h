@@ -199,6 +199,9 @@ struct fe_mesh {
   // reduction scratch
   double* red = nullptr;
   int red_len = 0;
+  // conjugate-gradient workspace (fe_cg.cu), released through cg_free
+  void* cg_work = nullptr;
+  void (*cg_free)(void*) = nullptr;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -222,6 +225,7 @@ struct ApplyLaunch {
   const void* x;
   void* y;
   cudaStream_t st;
+  const int* skip = nullptr;  // optional device flag that turns the launch into a no-op
 };
 fe_status fe_launch_apply_f64dw(const ApplyLaunch& a);
 fe_status fe_launch_apply_f64native(const ApplyLaunch& a);

@@ -218,6 +218,7 @@ fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
 // ---------------------------------------------------------------------------------------------
 static void free_mesh(fe_mesh* m) {
   if (!m) return;
+  if (m->cg_work && m->cg_free) m->cg_free(m->cg_work);
   cudaFree(m->geo64);
   cudaFree(m->geodw);
   cudaFree(m->geo32);

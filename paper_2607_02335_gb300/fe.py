@@ -43,7 +43,8 @@ class fe_layout(ctypes.Structure):
 
 class fe_cg_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("mixed", ctypes.c_int),
-                ("flexible", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
+                ("flexible", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("history", ctypes.c_void_p)]
 
 
 class fe_cg_result(ctypes.Structure):
@@ -219,7 +220,14 @@ class Mesh:
         fe_pairing(self.handle, prec, a, b, out, stream)
         return float(out.item())
 
-    def cg_solve(self, b, x, rtol=1e-10, maxit=1000, mixed=0, flexible=False, inner_rtol=1e-4,
-                 stream=None) -> fe_cg_result:
-        o = fe_cg_opts(rtol, maxit, mixed, int(flexible), inner_rtol)
-        return fe_cg_solve(self.handle, b, x, o, stream)
+    def cg_solve(self, b, x, rtol=1e-10, maxit=1000, mixed=0, flexible=False, inner_rtol=1e-2,
+                 history=False, stream=None):
+        """Returns the fe_cg_result, or (result, history[iters, 3]) with history=True."""
+        import numpy as np
+        hist = np.zeros(3 * maxit) if history else None
+        o = fe_cg_opts(rtol, maxit, mixed, int(flexible), inner_rtol,
+                       hist.ctypes.data if history else None)
+        res = fe_cg_solve(self.handle, b, x, o, stream)
+        if history:
+            return res, hist.reshape(maxit, 3)[: res.iters]
+        return res

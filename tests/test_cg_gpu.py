@@ -1,0 +1,125 @@
+"""Cell-wise CG (Algorithm "Communication-Free (Flexible) PCG") against the oracle's assembled
+Jacobi-PCG: the Equivalence theorem says the iterates coincide, so alpha_k, beta_k and the
+relative residuals must agree up to rounding; solutions, exact quadratic reproduction, mixed
+precision to an FP64 residual of 1e-10 checked by the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2607_02335_gb300 import synth as S
+from tests.helpers import oracle_mesh, rel_max_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fe():
+    from paper_2607_02335_gb300 import fe as F
+    return F
+
+
+def unique_from_cellwise(om, xc):
+    gidx = O.gather(om, np.arange(om.n_unique, dtype=np.float64)).astype(np.int64)
+    xg = np.zeros(om.n_unique)
+    xg[gidx] = xc
+    return xg, gidx
+
+
+def oracle_relres(om, b_cell, x_cell):
+    """||G^T b - A_D x_glob|| / ||G^T b|| over free nodes, in FP64 on the CPU."""
+    xg, _ = unique_from_cellwise(om, x_cell)
+    bg = O.scatter(om, b_cell)
+    bnd = O.boundary_global(om)
+    bg[bnd] = 0.0
+    csr = O.assemble_csr(om, O.LAPLACE)
+    r = bg - O.apply_dirichlet_csr(om, csr, xg)
+    return np.linalg.norm(r) / np.linalg.norm(bg)
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+def test_equivalence_theorem_iterates(fe, flexible):
+    m, p = (4, 3, 5), 3
+    om = oracle_mesh(m, p, amp=0.1, dirichlet=True)
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=True)
+    bc = S.dual_cellwise(m, p, seed=21)
+    ref = O.cg(om, O.LAPLACE, O.scatter(om, bc), rtol=1e-12, maxit=500, flexible=flexible)
+    assert ref["status"] == 0
+    x = torch.zeros(gm.cellwise_len, dtype=torch.float64, device="cuda")
+    res, hist = gm.cg_solve(torch.from_numpy(bc).cuda(), x, rtol=1e-12, maxit=500,
+                            flexible=flexible, history=True)
+    assert res.status == fe.FE_OK
+    assert abs(res.iters - ref["iters"]) <= 1
+    k = 25
+    assert np.allclose(hist[:k, 0], ref["alpha"][:k], rtol=1e-9, atol=0)
+    assert np.allclose(hist[:k - 1, 1], ref["beta"][:k - 1], rtol=1e-8, atol=0)
+    assert np.allclose(hist[:k, 2], ref["relres"][1:k + 1], rtol=1e-9, atol=0)
+    # the iterate is continuous and equals G x_glob of the assembled solve
+    xc = x.cpu().numpy()
+    xg, gidx = unique_from_cellwise(om, xc)
+    assert np.array_equal(xc, xg[gidx])
+    assert rel_max_err(xg, ref["x"]) <= 1e-9
+    assert oracle_relres(om, bc, xc) <= 1.5e-12
+
+
+def test_quadratic_solution_reproduced(fe):
+    m, p = 4, 2
+    om = oracle_mesh(m, p, dirichlet=True)
+    for geom in (fe.FE_GEOM_AFFINE, fe.FE_GEOM_STORED):
+        gm = fe.Mesh(m, p, geom_mode=geom, dirichlet=True)
+        b = torch.from_numpy(O.rhs(om, O.RHS_QUADRATIC)).cuda()
+        x = torch.zeros_like(b)
+        res = gm.cg_solve(b, x, rtol=1e-13, maxit=1000)
+        assert res.status == fe.FE_OK
+        uex = O.gather(om, O.exact_nodal(om, O.RHS_QUADRATIC))
+        assert np.abs(x.cpu().numpy() - uex).max() <= 1e-11
+
+
+@pytest.mark.parametrize("p,m", [(2, (6, 5, 4)), (3, (4, 4, 3)), (5, (2, 3, 2))])
+def test_mixed_precision_reaches_fp64_residual(fe, p, m):
+    om = oracle_mesh(m, p, amp=0.1, dirichlet=True)
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=True)
+    bc = O.rhs(om, O.RHS_SINE)
+    b = torch.from_numpy(bc).cuda()
+    x64 = torch.zeros_like(b)
+    r64 = gm.cg_solve(b, x64, rtol=1e-10, maxit=3000)
+    x32 = torch.zeros_like(b)
+    r32 = gm.cg_solve(b, x32, rtol=1e-10, maxit=3000, mixed=fe.FE_F32)
+    # a tight inner tolerance stalls near eps_32 * cond(A); the stagnation guard hands over
+    xt = torch.zeros_like(b)
+    rt = gm.cg_solve(b, xt, rtol=1e-10, maxit=3000, mixed=fe.FE_F32, inner_rtol=1e-6)
+    assert r64.status == fe.FE_OK and r32.status == fe.FE_OK and rt.status == fe.FE_OK
+    assert oracle_relres(om, bc, xt.cpu().numpy()) <= 1.2e-10
+    assert r32.outer_iters >= 2 and r32.rel_res <= 1e-10
+    assert oracle_relres(om, bc, x64.cpu().numpy()) <= 1.2e-10
+    assert oracle_relres(om, bc, x32.cpu().numpy()) <= 1.2e-10
+    e64 = O.l2_error(om, x64.cpu().numpy(), O.RHS_SINE)
+    e32 = O.l2_error(om, x32.cpu().numpy(), O.RHS_SINE)
+    assert abs(e64 - e32) <= 1e-6 * e64
+
+
+def test_cg_statuses(fe):
+    m, p = (3, 3, 3), 2
+    gm = fe.Mesh(m, p, deform_amp=0.05, dirichlet=True)
+    b = torch.from_numpy(S.dual_cellwise(m, p, seed=3)).cuda()
+    x = torch.zeros_like(b)
+    res = gm.cg_solve(b, x, rtol=1e-14, maxit=3)
+    assert res.status == fe.FE_ERR_NOT_CONVERGED and res.iters == 3
+    z = torch.zeros_like(b)
+    x.fill_(1.0)
+    res = gm.cg_solve(z, x, rtol=1e-10, maxit=10)
+    assert res.status == fe.FE_OK and res.iters == 0 and float(x.abs().max()) == 0.0
+    with pytest.raises(fe.FeError):
+        gm.cg_solve(b, x, rtol=1e-10, maxit=0)
+
+
+def test_cg_reproducible_and_warm_start(fe):
+    m, p = (5, 4, 3), 3
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=True)
+    b = torch.from_numpy(S.dual_cellwise(m, p, seed=9)).cuda()
+    x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+    r1 = gm.cg_solve(b, x1, rtol=1e-11, maxit=2000)
+    r2 = gm.cg_solve(b, x2, rtol=1e-11, maxit=2000)
+    assert r1.iters == r2.iters and torch.equal(x1, x2)
+    r3 = gm.cg_solve(b, x1, rtol=1e-11, maxit=2000)  # already converged start
+    assert r3.status == fe.FE_OK and r3.iters <= 2
