@@ -324,6 +324,8 @@ def run_ours(args, rank, world):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_value = units_per_step * world / e2e_s / 1e9
 
+    solve = None if args.small else mixed_vs_fp64_solve(fe, torch)
+
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -341,6 +343,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
+        "solve_mixed_vs_fp64": solve,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -355,6 +358,37 @@ def run_ours(args, rank, world):
                                 "kind": "oracle", "sample": smp.describe()}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def mixed_vs_fp64_solve(fe, torch, m=64, p=3, rtol=1e-10):
+    """Poisson -Laplace u = f, u = sin sin sin, Q3 on the deformed 64^3 mesh: Jacobi-PCG in FP64
+    vs FP32 PCG under FP64 iterative refinement, both to a relative FP64 residual of 1e-10.
+    Each solve is run twice and the second run is timed (the first builds the CUDA graphs)."""
+    gm = fe.Mesh(m, p, deform_amp=AMP, dirichlet=True)
+    b = gm.rhs(fe.FE_RHS_SINE)
+    out = {"workload": f"Q{p}, {m}^3 deformed (amp {AMP}), sine manufactured solution, "
+                       f"Jacobi-PCG to rtol {rtol}", "unique_dofs": gm.unique_dofs,
+           "cellwise_dofs": gm.cellwise_len}
+    sols = {}
+    variants = (("fp64", 0, False), ("mixed_fp32_in_fp64_ir", fe.FE_F32, False),
+                ("mixed_fp64_fcg_fp32_pcg_precond", fe.FE_F32, True))
+    for name, mixed, flex in variants:
+        for rep in range(2):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = gm.cg_solve(b, x, rtol=rtol, maxit=20000, mixed=mixed, flexible=flex)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        sols[name] = x
+        out[name] = {"status": fe.STATUS_NAMES[res.status], "iters": res.iters,
+                     "outer_iters": res.outer_iters, "rel_res_fp64": res.rel_res,
+                     "seconds": round(dt, 4), "l2_error_vs_exact": gm.l2_error(x)}
+    for name, _, _ in variants[1:]:
+        out[name]["max_abs_diff_vs_fp64"] = float((sols[name] - sols["fp64"]).abs().max())
+        out[name]["speedup_over_fp64"] = round(out["fp64"]["seconds"] / out[name]["seconds"], 3)
+    gm.close()
+    return out
 
 
 def run_profile_case(args):

@@ -139,12 +139,27 @@ fe_status fe_pairing(const fe_mesh* mesh, fe_prec prec, const void* a, const voi
 fe_status fe_pairing_noalloc(const fe_mesh* mesh, fe_prec prec, const void* a, const void* b,
                              double* result_dev, void* stream);
 
+/* Manufactured Poisson problems -Laplace(u) = f, u = 0 on the boundary of the unit cube:
+ * FE_RHS_SINE (u = sin(pi x) sin(pi y) sin(pi z), f = 3 pi^2 u) and FE_RHS_QUADRATIC
+ * (u = prod x_a (1 - x_a)).  fe_rhs writes the unassembled load vector b~ (dual, cell-wise:
+ * b_K,i = sum_q w_q detJ f(x(xi_q)) phi_i(xi_q)), the right-hand side of Eq. (constrained_system),
+ * into the device array b (cellwise_len doubles).  fe_l2_error computes the L2 norm of u_h - u for
+ * a cell-wise FP64 solution u (device) with an (n+2)-point Gauss rule per direction and writes it
+ * to the HOST double *err (synchronous).  FP64 arithmetic. */
+#define FE_RHS_SINE 0
+#define FE_RHS_QUADRATIC 1
+fe_status fe_rhs(const fe_mesh* mesh, int kind, double* b, void* stream);
+fe_status fe_l2_error(const fe_mesh* mesh, int kind, const double* u, double* err, void* stream);
+
 /* Conjugate gradients on cell-wise data (Algorithm "Communication-Free (Flexible) PCG") with the
  * Jacobi preconditioner P = D_cell^{-1} S.  Convergence (unspecified in the paper; reading):
  * ||G^T r||_2 / ||G^T b||_2 <= rtol over free nodes, evaluated on the device as
- * sum_e (S r)_e^2 / mult_e.  mixed = 0: FP64 throughout.  mixed = FE_F32: FP64 iterative
- * refinement (r = b - A x in FP64, x += d in FP64) around an FP32 inner PCG solved to
- * inner_rtol.  flexible = 1 uses the FCG beta.  b (dual) and x (primal, in/out) are device
+ * sum_e (S r)_e^2 / mult_e.  mixed = 0: FP64 throughout; flexible = 1 uses the FCG beta.
+ * mixed = FE_F32, flexible = 0: FP64 iterative refinement (r = b - A x in FP64, x += d in FP64)
+ * around an FP32 inner PCG solved to inner_rtol.  mixed = FE_F32, flexible = 1: FP64 FCG whose
+ * (variable) preconditioner is the FP32 inner PCG solve, the reduced-precision preconditioner
+ * that motivates FCG in Sec. 3.2.  The FP32 inner solve receives the residual assembled in FP64
+ * and split evenly over the copies of each node.  b (dual) and x (primal, in/out) are device
  * arrays of cellwise_len doubles.  Synchronous: returns after the solve. */
 typedef struct {
   double rtol;       /* relative residual target */

@@ -33,7 +33,7 @@ struct CgScal {
   int stall_limit;  // stop after this many iterations without progress (0 = never)
 };
 
-enum { FIN_INIT_B = 0, FIN_INIT_R = 1, FIN_ITER = 2 };
+enum { FIN_INIT_B = 0, FIN_INIT_R = 1, FIN_ITER = 2, FIN_NORM = 3 };
 
 // ---- element-wise kernels -------------------------------------------------------------------
 __global__ void k_invmult(float* __restrict__ out, long long ncells, int n, int mx, int my, int mz,
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   if (mode == FIN_ITER && *(volatile const int*)&sc->done) return;
   __shared__ dw sh[32];
   const double rn2 = sum_slot(partials, 0, sh);
-  const double rz = (mode != FIN_INIT_B) ? sum_slot(partials, 1, sh) : 0.0;
+  const double rz = (mode == FIN_INIT_R || mode == FIN_ITER) ? sum_slot(partials, 1, sh) : 0.0;
   const double qz = (mode == FIN_ITER && flexible) ? sum_slot(partials, 2, sh) : 0.0;
   if (threadIdx.x != 0) return;
   if (mode == FIN_INIT_B) {
@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   sc->rnorm2 = rn2;
   const double rel = sc->bnorm2 > 0.0 ? sqrt(rn2 / sc->bnorm2) : 0.0;
   sc->relres = rel;
+  if (mode == FIN_NORM) return;
   if (mode == FIN_INIT_R) {
     sc->rz = rz;
     sc->best = rel;
@@ -293,6 +294,45 @@ __global__ void __launch_bounds__(RED_THREADS)
   sc->beta = beta;
   sc->rz = rz;
   if (hist) hist[3 * k + 1] = beta;
+}
+
+// z = d / s (FP64 primal correction from the FP32 inner solve)
+__global__ void k_from_inner(double* __restrict__ z, const float* __restrict__ d, double inv_s,
+                             long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    z[e] = inv_s * (double)d[e];
+}
+
+// partials: slot 1 <r, z>, slot 2 <q, z> (q may be null)
+__global__ void __launch_bounds__(RED_THREADS)
+    k_zpairs(const double* __restrict__ r, const double* __restrict__ q,
+             const double* __restrict__ z, double* __restrict__ partials, long long n) {
+  __shared__ dw sh[32];
+  dw a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
+  for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n;
+       e += (long long)RED_BLOCKS * RED_THREADS) {
+    const double ze = z[e];
+    a1 = dw_add(a1, prod_dw<double>(r[e], ze));
+    if (q) a2 = dw_add(a2, prod_dw<double>(q[e], ze));
+  }
+  a1 = block_reduce_dw(a1, sh);
+  if (threadIdx.x == 0) partials[1 * RED_BLOCKS + blockIdx.x] = dw_to_double(a1);
+  if (q) {
+    a2 = block_reduce_dw(a2, sh);
+    if (threadIdx.x == 0) partials[2 * RED_BLOCKS + blockIdx.x] = dw_to_double(a2);
+  }
+}
+
+// outer FCG scalars: init rz = <r,z>; iteration beta = -<q,z>/<q,p>, rz = <r,z>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_fin_fcg(const double* __restrict__ partials, CgScal* __restrict__ sc, int init) {
+  __shared__ dw sh[32];
+  const double rz = sum_slot(partials, 1, sh);
+  const double qz = init ? 0.0 : sum_slot(partials, 2, sh);
+  if (threadIdx.x != 0) return;
+  if (!init) sc->beta = -qz / sc->qp;
+  sc->rz = rz;
 }
 
 unsigned grid_for(long long n) {
@@ -485,6 +525,99 @@ fe_status init_direction(const fe_mesh* m, CgWork* w, S* r, S* z, S* p, S* wv, c
   return fe_cuda_check(cudaGetLastError(), "init launch");
 }
 
+// Inner FP32 PCG on A d = s S(r)/mult with s = 1/||G^T r|| (w must hold S r in FP64, rnorm2
+// its squared norm).  Returns the inner iteration count in *iters and the scale s.
+fe_status inner_solve(const fe_mesh* m, CgWork* w, int op, int flex, double rnorm2, double irtol,
+                      int maxit, int* iters, double* s_out) {
+  const long long n = w->n;
+  const double s = 1.0 / sqrt(rnorm2);
+  k_to_inner<<<grid_for(n), 256, 0, w->st>>>(w->w, w->invmult, w->r32, w->d32, s, n);
+  FE_TRY(set_scal(w, 1, maxit, 20));
+  FE_TRY(residual_norm<float>(m, w, w->r32, w->w32, &w->sc[1], FIN_INIT_B));
+  FE_TRY(init_direction<float>(m, w, w->r32, w->z32, w->p32, w->w32, w->invdiag32, &w->sc[1], irtol));
+  CgScal h;
+  FE_TRY(read_scal(w, 1, &h));
+  if (!h.done) {
+    if (!w->g32[flex])
+      FE_TRY((build_graph<float, float>(m, w, op, flex, irtol, w->d32, w->r32, w->z32, w->p32, w->q32,
+                                        w->w32, w->invdiag32, &w->sc[1], nullptr, &w->g32[flex])));
+    FE_TRY(run_until_done(w, w->g32[flex], 1, &h));
+  }
+  *iters = h.iter;
+  *s_out = s;
+  if (h.status == FE_ERR_BREAKDOWN && h.iter == 0) {
+    fe_set_error("fe_cg_solve: inner breakdown");
+    return FE_ERR_BREAKDOWN;
+  }
+  return FE_OK;
+}
+
+// FP64 flexible CG whose preconditioner is an FP32 PCG solve: z = P(r) = d / s.  P consumes r only
+// through S r = G (G^T r) and returns a continuous vector, the consistency the Equivalence theorem
+// asks of a (variable) preconditioner; FCG (Notay) absorbs the variation between applications.
+fe_status solve_fcg_outer(const fe_mesh* m, CgWork* w, int op, const double* b, double bnorm2,
+                          const fe_cg_opts* opts, fe_cg_result* res, fe_status* status) {
+  const long long n = w->n;
+  const double irtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 1e-2;
+  CgScal h;
+  int total = 0, outer = 0, its = 0;
+  double s = 1.0;
+  // r = b - A x ; ||G^T r||
+  {
+    ApplyLaunch L{m, op, w->x, w->q, w->st, nullptr};
+    FE_TRY(fe_launch_apply_f64dw(L));
+  }
+  k_residual<<<grid_for(n), 256, 0, w->st>>>(b, w->q, w->r, n);
+  FE_TRY(residual_norm<double>(m, w, w->r, w->w, &w->sc[0], FIN_NORM));
+  FE_TRY(read_scal(w, 0, &h));
+  res->rel_res = sqrt(h.rnorm2 / bnorm2);
+  if (res->rel_res <= opts->rtol) {
+    *status = FE_OK;
+    return FE_OK;
+  }
+  // z = P(r), p = z, rz = <r, z>
+  FE_TRY(inner_solve(m, w, op, 0, h.rnorm2, irtol, opts->maxit, &its, &s));
+  total += its;
+  k_from_inner<<<grid_for(n), 256, 0, w->st>>>(w->z, w->d32, 1.0 / s, n);
+  k_zpairs<<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(w->r, nullptr, w->z, w->partials, n);
+  k_fin_fcg<<<1, RED_THREADS, 0, w->st>>>(w->partials, &w->sc[0], 1);
+  FE_CUDA(cudaMemcpyAsync(w->p, w->z, n * sizeof(double), cudaMemcpyDeviceToDevice, w->st), "copy");
+  *status = FE_ERR_NOT_CONVERGED;
+  while (total < opts->maxit) {
+    ApplyLaunch L{m, op, w->p, w->q, w->st, nullptr};
+    FE_TRY(fe_launch_apply_f64dw(L));
+    k_qp<double><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(w->q, w->p, w->partials, &w->sc[0], n);
+    k_fin_alpha<<<1, RED_THREADS, 0, w->st>>>(w->partials, &w->sc[0], nullptr);
+    k_update_ur<double, double><<<grid_for(n), 256, 0, w->st>>>(w->x, w->r, w->p, w->q, &w->sc[0], n);
+    FE_TRY(residual_norm<double>(m, w, w->r, w->w, &w->sc[0], FIN_NORM));
+    FE_TRY(read_scal(w, 0, &h));
+    ++outer;
+    res->rel_res = h.relres;
+    if (h.done) {  // breakdown flagged by k_fin_alpha
+      *status = (fe_status)h.status;
+      break;
+    }
+    if (!std::isfinite(h.relres)) {
+      *status = FE_ERR_BREAKDOWN;
+      break;
+    }
+    if (h.relres <= opts->rtol) {
+      *status = FE_OK;
+      break;
+    }
+    FE_TRY(inner_solve(m, w, op, 0, h.rnorm2, irtol, opts->maxit - total, &its, &s));
+    total += its;
+    k_from_inner<<<grid_for(n), 256, 0, w->st>>>(w->z, w->d32, 1.0 / s, n);
+    k_zpairs<<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(w->r, w->q, w->z, w->partials, n);
+    k_fin_fcg<<<1, RED_THREADS, 0, w->st>>>(w->partials, &w->sc[0], 0);
+    k_update_p<double><<<grid_for(n), 256, 0, w->st>>>(w->p, w->z, &w->sc[0], n);
+    FE_CUDA(cudaGetLastError(), "fcg launch");
+  }
+  res->iters = total;
+  res->outer_iters = outer;
+  return FE_OK;
+}
+
 }  // namespace
 
 extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
@@ -578,6 +711,8 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
       FE_CUDA(cudaMemcpy(opts->history, hist, 3 * (size_t)h.iter * sizeof(double),
                          cudaMemcpyDeviceToHost),
               "history readback");
+  } else if (flex) {
+    FE_TRY(solve_fcg_outer(m, w, op, b, bnorm2, opts, res, &status));
   } else {
     int total = 0, outer = 0;
     for (;;) {

@@ -23,6 +23,7 @@ FE_LAPLACE, FE_MASS = 0, 1
 FE_F64, FE_F32, FE_BF16_F32ACC, FE_F16_F32ACC = 0, 1, 2, 3
 FE_GEOM_STORED, FE_GEOM_RECOMPUTE, FE_GEOM_AFFINE = 0, 1, 2
 FE_ASSEMBLE, FE_NATIVE_F64 = 1, 2
+FE_RHS_SINE, FE_RHS_QUADRATIC = 0, 1
 
 STATUS_NAMES = {0: "FE_OK", 1: "FE_ERR_INVALID", 2: "FE_ERR_OOM", 3: "FE_ERR_CUDA",
                 4: "FE_ERR_NOT_CONVERGED", 5: "FE_ERR_BREAKDOWN", 6: "FE_ERR_TIMEOUT",
@@ -65,6 +66,8 @@ _SIGS = {
     "fe_pairing": [_MESH, _i, _vp, _vp, _vp, _vp],
     "fe_pairing_noalloc": [_MESH, _i, _vp, _vp, _vp, _vp],
     "fe_cg_solve": [_MESH, _vp, _vp, ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_cg_result), _vp],
+    "fe_rhs": [_MESH, _i, _vp, _vp],
+    "fe_l2_error": [_MESH, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -151,6 +154,16 @@ def fe_pairing_noalloc(mesh: int, prec: int, a, b, result_dev, stream=None) -> N
            "fe_pairing_noalloc")
 
 
+def fe_rhs(mesh: int, kind: int, b, stream=None) -> None:
+    _check(_lib.fe_rhs(mesh, kind, _ptr(b), _stream(stream)), "fe_rhs")
+
+
+def fe_l2_error(mesh: int, kind: int, u, stream=None) -> float:
+    err = ctypes.c_double(0.0)
+    _check(_lib.fe_l2_error(mesh, kind, _ptr(u), ctypes.byref(err), _stream(stream)), "fe_l2_error")
+    return err.value
+
+
 def fe_cg_solve(mesh: int, b, x, opts: fe_cg_opts, stream=None) -> fe_cg_result:
     """Returns the fe_cg_result; FE_ERR_NOT_CONVERGED / FE_ERR_BREAKDOWN are reported in
     ``result.status`` instead of raising."""
@@ -219,6 +232,14 @@ class Mesh:
         out = torch.empty(1, dtype=torch.float64, device=f"cuda:{self.device}")
         fe_pairing(self.handle, prec, a, b, out, stream)
         return float(out.item())
+
+    def rhs(self, kind=FE_RHS_SINE, stream=None):
+        b = self.empty(FE_F64)
+        fe_rhs(self.handle, kind, b, stream)
+        return b
+
+    def l2_error(self, u, kind=FE_RHS_SINE, stream=None) -> float:
+        return fe_l2_error(self.handle, kind, u, stream)
 
     def cg_solve(self, b, x, rtol=1e-10, maxit=1000, mixed=0, flexible=False, inner_rtol=1e-2,
                  history=False, stream=None):

@@ -88,8 +88,13 @@ def test_mixed_precision_reaches_fp64_residual(fe, p, m):
     # a tight inner tolerance stalls near eps_32 * cond(A); the stagnation guard hands over
     xt = torch.zeros_like(b)
     rt = gm.cg_solve(b, xt, rtol=1e-10, maxit=3000, mixed=fe.FE_F32, inner_rtol=1e-6)
+    # FP64 FCG with the FP32 PCG as variable preconditioner
+    xf = torch.zeros_like(b)
+    rf = gm.cg_solve(b, xf, rtol=1e-10, maxit=3000, mixed=fe.FE_F32, flexible=True)
     assert r64.status == fe.FE_OK and r32.status == fe.FE_OK and rt.status == fe.FE_OK
+    assert rf.status == fe.FE_OK and rf.rel_res <= 1e-10
     assert oracle_relres(om, bc, xt.cpu().numpy()) <= 1.2e-10
+    assert oracle_relres(om, bc, xf.cpu().numpy()) <= 1.2e-10
     assert r32.outer_iters >= 2 and r32.rel_res <= 1e-10
     assert oracle_relres(om, bc, x64.cpu().numpy()) <= 1.2e-10
     assert oracle_relres(om, bc, x32.cpu().numpy()) <= 1.2e-10
@@ -123,3 +128,18 @@ def test_cg_reproducible_and_warm_start(fe):
     assert r1.iters == r2.iters and torch.equal(x1, x2)
     r3 = gm.cg_solve(b, x1, rtol=1e-11, maxit=2000)  # already converged start
     assert r3.status == fe.FE_OK and r3.iters <= 2
+
+
+@pytest.mark.parametrize("p,m,amp", [(1, (3, 2, 4), 0.1), (2, (3, 4, 2), 0.1), (3, (2, 3, 2), 0.0),
+                                     (5, (2, 2, 1), 0.15), (7, (1, 2, 1), 0.1)])
+def test_rhs_and_l2_error_vs_oracle(fe, p, m, amp):
+    om = oracle_mesh(m, p, amp=amp, dirichlet=True)
+    gm = fe.Mesh(m, p, deform_amp=amp, dirichlet=True)
+    for kind in (O.RHS_SINE, O.RHS_QUADRATIC):
+        bref = O.rhs(om, kind)
+        b = gm.rhs(kind)
+        assert rel_max_err(b.cpu().numpy(), bref) <= 1e-12, kind
+        u = S.primal_unique(m, p, seed=4)
+        uc = O.gather(om, u)
+        e = gm.l2_error(torch.from_numpy(uc).cuda(), kind)
+        assert abs(e - O.l2_error(om, uc, kind)) <= 1e-12 * abs(e)
