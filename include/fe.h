@@ -180,6 +180,19 @@ typedef struct {
 fe_status fe_cg_solve(const fe_mesh* mesh, const double* b, double* x, const fe_cg_opts* opts,
                       fe_cg_result* res, void* stream);
 
+/* Batched solve of nprob independent problems (each its own mesh, degree and right-hand side)
+ * with the options of fe_cg_solve (mixed = 0: FP64 PCG; mixed = FE_F32: FP64 FCG preconditioned by
+ * an FP32 PCG solve, whatever `flexible` says).  Every CG iteration applies the operators of all
+ * unconverged problems in one persistent launch over (problem, cell-tile) work items; vector
+ * kernels run over (problem, chunk) items and every problem's scalars are reduced in a fixed
+ * order, so each result is bitwise the same alone and in any mix.  meshes must be distinct and on
+ * one device; b[i] (dual) and x[i] (primal, in/out) are device arrays of each mesh's
+ * cellwise_len doubles; res[i] receives each result.  Synchronous.  Returns FE_OK when every
+ * problem converged, else the first failing status (all results are still filled in). */
+fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes, const double* const* b,
+                              double* const* x, const fe_cg_opts* opts, fe_cg_result* res,
+                              void* stream);
+
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char* fe_last_error(void);
 

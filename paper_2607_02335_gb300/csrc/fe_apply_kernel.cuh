@@ -119,8 +119,9 @@ __device__ __forceinline__ void tile_sweep(const Sm<V>& s, int cbase, int a, int
   for (int r = 0; r < N; ++r) s.put(cbase + (AX == 0 ? xl<N>(a, b, r) : yl<N>(a, b, r)), out[r]);
 }
 
+// Everything an apply needs except the 1D tables.
 template <int N, class V>
-struct ApplyArgs {
+struct CellArgs {
   const typename NT<V>::SV* x;
   typename NT<V>::SV* y;
   const typename NT<V>::GV* geo;  // [cell][7][N3]: w detJ J^-1 J^-T (xx,yy,zz,xy,xz,yz), w detJ
@@ -128,32 +129,40 @@ struct ApplyArgs {
   int mx, my, mz;
   int dirichlet;
   V aff[4];  // affine mode: detJ/h_x^2, detJ/h_y^2, detJ/h_z^2, detJ
+};
+
+template <int N, class V>
+struct ApplyArgs {
+  CellArgs<N, V> c;
   const int* skip;  // optional device flag: the whole launch returns at once when *skip != 0
   Tab1D<N, V> tab;
 };
 
 enum { GEOM_STORED_K = 0, GEOM_AFFINE_K = 2 };
 
+// The cells cell0 .. cell0 + CPB - 1 (those below ncells), applied by the CTA's first CPB*n^2
+// threads.  Threads beyond that (a CTA wider than the tile, as in the batched persistent kernel)
+// work on a spare slot of the tile that nobody reads and still reach every barrier; the caller
+// then sizes each array tile_stride = TILE + CS.
 template <int N, class V, int OP, int GEOM>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
-    k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
+__device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
+                                            long long cell0, unsigned char* smraw,
+                                            int tile_stride) {
   using T = NT<V>;
   using C = Cfg<N>;
   constexpr int N2 = C::N2, N3 = C::N3;
-  extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NARR = (OP == FE_LAPLACE) ? 3 : 1;
-  const Sm<V> s0(smraw, NARR, 0, C::TILE);
-  const Sm<V> s1(smraw, NARR, NARR > 1 ? 1 : 0, C::TILE);
-  const Sm<V> s2(smraw, NARR, NARR > 2 ? 2 : 0, C::TILE);
+  const Sm<V> s0(smraw, NARR, 0, tile_stride);
+  const Sm<V> s1(smraw, NARR, NARR > 1 ? 1 : 0, tile_stride);
+  const Sm<V> s2(smraw, NARR, NARR > 2 ? 2 : 0, tile_stride);
 
-  if (a.skip && *(volatile const int*)a.skip) return;  // uniform over the grid
   const int t = threadIdx.x;
   const int cl = t / N2;
   const int lt = t - cl * N2;
   const int la = lt % N, lb = lt / N;  // line coordinates (a, b) of this thread
   const int cb = cl * C::CS;           // this cell's offset in the tile
-  const long long cell = (long long)blockIdx.x * C::CPB + cl;
-  const bool active = cell < a.ncells;
+  const long long cell = cell0 + cl;
+  const bool active = cl < C::CPB && cell < a.ncells;
   const long long gbase = cell * N3;
 
   // Dirichlet masks of this thread's z-line (i = la, j = lb)
@@ -177,13 +186,13 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
     V v = active ? T::load_stream(a.x + gbase + k * N2 + lt) : T::zero();
     u[k] = masked(k) ? T::zero() : v;
   }
-  mv<N, V>(a.tab.V_, u, w);
+  mv<N, V>(tab.V_, u, w);
 #pragma unroll
   for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
   __syncthreads();
-  tile_sweep<N, V, 0, false>(s0, cb, la, lb, a.tab.V_);  // x
+  tile_sweep<N, V, 0, false>(s0, cb, la, lb, tab.V_);  // x
   __syncthreads();
-  tile_sweep<N, V, 1, false>(s0, cb, la, lb, a.tab.V_);  // y
+  tile_sweep<N, V, 1, false>(s0, cb, la, lb, tab.V_);  // y
   __syncthreads();
   // s0 now holds u at the Gauss points
 
@@ -193,17 +202,17 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
       V in[N], out[N];
 #pragma unroll
       for (int r = 0; r < N; ++r) in[r] = s0.get(cb + xl<N>(la, lb, r));
-      mv<N, V>(a.tab.D_, in, out);
+      mv<N, V>(tab.D_, in, out);
 #pragma unroll
       for (int r = 0; r < N; ++r) s1.put(cb + xl<N>(la, lb, r), out[r]);
 #pragma unroll
       for (int r = 0; r < N; ++r) in[r] = s0.get(cb + yl<N>(la, lb, r));
-      mv<N, V>(a.tab.D_, in, out);
+      mv<N, V>(tab.D_, in, out);
 #pragma unroll
       for (int r = 0; r < N; ++r) s2.put(cb + yl<N>(la, lb, r), out[r]);
 #pragma unroll
       for (int r = 0; r < N; ++r) in[r] = s0.get(cb + zl<N>(la, lb, r));
-      mv<N, V>(a.tab.D_, in, u);  // u := d/dz along the z-line
+      mv<N, V>(tab.D_, in, u);  // u := d/dz along the z-line
     }
     __syncthreads();
     // ---- pointwise metric: g = G grad u (z-line owner)
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
       V gxx, gyy, gzz, gxy, gxz, gyz;
       if constexpr (GEOM == GEOM_AFFINE_K) {
         const int q1 = la, q2 = lb;
-        const V wq = T::mul(T::mul(a.tab.W_[q1], a.tab.W_[q2]), a.tab.W_[k]);
+        const V wq = T::mul(T::mul(tab.W_[q1], tab.W_[q2]), tab.W_[k]);
         gxx = T::mul(wq, a.aff[0]);
         gyy = T::mul(wq, a.aff[1]);
         gzz = T::mul(wq, a.aff[2]);
@@ -245,9 +254,9 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
     }
     __syncthreads();
     // ---- transposed derivative: t = D^T gx (x) + D^T gy (y) + D^T gz (z)
-    tile_sweep<N, V, 0, true>(s1, cb, la, lb, a.tab.D_);
-    tile_sweep<N, V, 1, true>(s2, cb, la, lb, a.tab.D_);
-    mtv<N, V>(a.tab.D_, u, w);
+    tile_sweep<N, V, 0, true>(s1, cb, la, lb, tab.D_);
+    tile_sweep<N, V, 1, true>(s2, cb, la, lb, tab.D_);
+    mtv<N, V>(tab.D_, u, w);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -261,7 +270,7 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
       const V uq = s0.get(cb + zl<N>(la, lb, k));
       V jw;
       if constexpr (GEOM == GEOM_AFFINE_K) {
-        jw = T::mul(T::mul(T::mul(a.tab.W_[la], a.tab.W_[lb]), a.tab.W_[k]), a.aff[3]);
+        jw = T::mul(T::mul(T::mul(tab.W_[la], tab.W_[lb]), tab.W_[k]), a.aff[3]);
       } else {
         jw = active ? T::geo(a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + 6 * N3 + k * N2 + lt)
                     : T::zero();
@@ -271,13 +280,13 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
   }
 
   // ---- transposed interpolation: z in registers, then x and y in the tile
-  mtv<N, V>(a.tab.V_, u, w);
+  mtv<N, V>(tab.V_, u, w);
 #pragma unroll
   for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
   __syncthreads();
-  tile_sweep<N, V, 0, true>(s0, cb, la, lb, a.tab.V_);
+  tile_sweep<N, V, 0, true>(s0, cb, la, lb, tab.V_);
   __syncthreads();
-  tile_sweep<N, V, 1, true>(s0, cb, la, lb, a.tab.V_);
+  tile_sweep<N, V, 1, true>(s0, cb, la, lb, tab.V_);
   __syncthreads();
   if (active) {
 #pragma unroll
@@ -287,6 +296,14 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
       T::store(a.y + gbase + k * N2 + lt, v);
     }
   }
+}
+
+template <int N, class V, int OP, int GEOM>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+    k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (a.skip && *(volatile const int*)a.skip) return;  // uniform over the grid
+  apply_cells<N, V, OP, GEOM>(a.c, a.tab, (long long)blockIdx.x * Cfg<N>::CPB, smraw, Cfg<N>::TILE);
 }
 
 template <int N, class V>

@@ -40,7 +40,7 @@ static fe_status launch_one(const ApplyArgs<N, V>& a, cudaStream_t st) {
             "apply smem attribute");
     attr_done = true;
   }
-  const long long blocks = (a.ncells + C::CPB - 1) / C::CPB;
+  const long long blocks = (a.c.ncells + C::CPB - 1) / C::CPB;
   if (blocks > 0) kern<<<(unsigned)blocks, C::THREADS, smem, st>>>(a);
   return fe_cuda_check(cudaGetLastError(), "apply kernel launch");
 }
@@ -50,20 +50,20 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
   const fe_mesh* m = L.m;
   ApplyArgs<N, V> a;
   std::memset(&a, 0, sizeof(a));
-  a.x = static_cast<const typename NT<V>::SV*>(L.x);
-  a.y = static_cast<typename NT<V>::SV*>(L.y);
-  a.geo = geo;
-  a.ncells = m->ncells;
-  a.mx = m->d.mx;
-  a.my = m->d.my;
-  a.mz = m->d.mz;
-  a.dirichlet = m->d.dirichlet;
+  a.c.x = static_cast<const typename NT<V>::SV*>(L.x);
+  a.c.y = static_cast<typename NT<V>::SV*>(L.y);
+  a.c.geo = geo;
+  a.c.ncells = m->ncells;
+  a.c.mx = m->d.mx;
+  a.c.my = m->d.my;
+  a.c.mz = m->d.mz;
+  a.c.dirichlet = m->d.dirichlet;
   a.skip = L.skip;
   const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / m->d.mz, det = hx * hy * hz;
-  a.aff[0] = fe_cast<V>(det / (hx * hx));
-  a.aff[1] = fe_cast<V>(det / (hy * hy));
-  a.aff[2] = fe_cast<V>(det / (hz * hz));
-  a.aff[3] = fe_cast<V>(det);
+  a.c.aff[0] = fe_cast<V>(det / (hx * hx));
+  a.c.aff[1] = fe_cast<V>(det / (hy * hy));
+  a.c.aff[2] = fe_cast<V>(det / (hz * hz));
+  a.c.aff[3] = fe_cast<V>(det);
   a.tab = make_tab<N, V>(m->tab);
   const bool affine = m->d.geom_mode == FE_GEOM_AFFINE;
   if (L.op == FE_LAPLACE)

@@ -1,0 +1,898 @@
+// fe_batch.cu -- many independent solves advanced together (batched CG, and the engine of the
+// request server).
+//
+// Each problem keeps its own mesh, geometry and cell-wise state; the engine advances all active
+// problems in lockstep.  Every CG iteration applies the operators of all problems in ONE
+// persistent launch over a work list of (problem, cell-tile) items with a per-item degree switch
+// into the degree-templated cell kernel; the vector kernels run over lists of (problem, chunk)
+// items, and per-problem scalars are reduced one CTA per problem over that problem's chunk
+// partials in a fixed order.  A problem's arithmetic therefore never depends on which other
+// problems share the launch: its result is bitwise the same alone and in a mix.
+//
+// Precisions: FP64 Jacobi-PCG (double-word apply), or the mixed scheme of fe_cg_solve with
+// mixed = FE_F32, flexible = 1: FP64 FCG whose preconditioner is an FP32 Jacobi-PCG solve.  The
+// phases (outer FP64 step, inner FP32 iterations) are global: a problem whose inner solve ends
+// early waits for the others, which changes nothing in its own sequence of operations.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fe_apply_launch.cuh"
+#include "fe_batch.h"
+#include "fe_vec.cuh"
+
+namespace {
+
+constexpr int BT = 256;            // threads of every batched CTA
+constexpr long long CHUNK = 16384;  // elements (or DSS pairs) per work item
+
+// ---- 1D tables of every degree, in constant memory -------------------------------------------
+template <class V>
+struct AllTabs {
+  Tab1D<2, V> t2;
+  Tab1D<3, V> t3;
+  Tab1D<4, V> t4;
+  Tab1D<5, V> t5;
+  Tab1D<6, V> t6;
+  Tab1D<7, V> t7;
+  Tab1D<8, V> t8;
+};
+__constant__ AllTabs<dw> c_tabs_dw;
+__constant__ AllTabs<float> c_tabs_f32;
+
+template <int N, class V>
+__device__ __forceinline__ const Tab1D<N, V>& tab_of();
+#define FE_TAB_OF(NN)                                                            \
+  template <>                                                                    \
+  __device__ __forceinline__ const Tab1D<NN, dw>& tab_of<NN, dw>() {             \
+    return c_tabs_dw.t##NN;                                                      \
+  }                                                                              \
+  template <>                                                                    \
+  __device__ __forceinline__ const Tab1D<NN, float>& tab_of<NN, float>() {       \
+    return c_tabs_f32.t##NN;                                                     \
+  }
+FE_TAB_OF(2)
+FE_TAB_OF(3)
+FE_TAB_OF(4)
+FE_TAB_OF(5)
+FE_TAB_OF(6)
+FE_TAB_OF(7)
+FE_TAB_OF(8)
+#undef FE_TAB_OF
+
+std::mutex g_tab_mu;
+bool g_tab_ready[64] = {};
+
+fe_status ensure_tables(int dev) {
+  std::lock_guard<std::mutex> lock(g_tab_mu);
+  if (dev < 0 || dev >= 64) return FE_ERR_INVALID;
+  if (g_tab_ready[dev]) return FE_OK;
+  AllTabs<dw> tdw;
+  AllTabs<float> t32;
+  HostTab h[8];
+  for (int p = 1; p <= 7; ++p) fe_host_tables(p, &h[p]);
+  tdw.t2 = make_tab<2, dw>(h[1]);
+  tdw.t3 = make_tab<3, dw>(h[2]);
+  tdw.t4 = make_tab<4, dw>(h[3]);
+  tdw.t5 = make_tab<5, dw>(h[4]);
+  tdw.t6 = make_tab<6, dw>(h[5]);
+  tdw.t7 = make_tab<7, dw>(h[6]);
+  tdw.t8 = make_tab<8, dw>(h[7]);
+  t32.t2 = make_tab<2, float>(h[1]);
+  t32.t3 = make_tab<3, float>(h[2]);
+  t32.t4 = make_tab<4, float>(h[3]);
+  t32.t5 = make_tab<5, float>(h[4]);
+  t32.t6 = make_tab<6, float>(h[5]);
+  t32.t7 = make_tab<7, float>(h[6]);
+  t32.t8 = make_tab<8, float>(h[7]);
+  FE_CUDA(cudaMemcpyToSymbol(c_tabs_dw, &tdw, sizeof(tdw)), "batch tables");
+  FE_CUDA(cudaMemcpyToSymbol(c_tabs_f32, &t32, sizeof(t32)), "batch tables");
+  g_tab_ready[dev] = true;
+  return FE_OK;
+}
+
+// ---- work items ------------------------------------------------------------------------------
+struct Tile {
+  int prob;
+  int pad;
+  long long cell0;
+};
+struct Chunk {
+  int prob;
+  int pad;
+  long long lo, hi;
+};
+
+// ---- persistent apply ------------------------------------------------------------------------
+template <int N, class V>
+__device__ __forceinline__ void apply_item(const BProb& P, int prec, int src, long long cell0,
+                                           unsigned char* sm) {
+  CellArgs<N, V> a;
+  if (prec == FE_F64) {
+    a.x = reinterpret_cast<const typename NT<V>::SV*>(src ? P.x64 : P.p64);
+    a.y = reinterpret_cast<typename NT<V>::SV*>(P.q64);
+    a.geo = reinterpret_cast<const typename NT<V>::GV*>(P.geodw);
+  } else {
+    a.x = reinterpret_cast<const typename NT<V>::SV*>(P.p32);
+    a.y = reinterpret_cast<typename NT<V>::SV*>(P.q32);
+    a.geo = reinterpret_cast<const typename NT<V>::GV*>(P.geo32);
+  }
+  a.ncells = P.ncells;
+  a.mx = P.mx;
+  a.my = P.my;
+  a.mz = P.mz;
+  a.dirichlet = P.dirichlet;
+  for (int c = 0; c < 4; ++c) {
+    if constexpr (sizeof(V) == sizeof(dw))
+      a.aff[c] = dw_from_double(P.aff[c]);
+    else
+      a.aff[c] = (V)P.aff[c];
+  }
+  constexpr int stride = Cfg<N>::TILE + Cfg<N>::CS;
+  if (P.affine)
+    apply_cells<N, V, FE_LAPLACE, GEOM_AFFINE_K>(a, tab_of<N, V>(), cell0, sm, stride);
+  else
+    apply_cells<N, V, FE_LAPLACE, GEOM_STORED_K>(a, tab_of<N, V>(), cell0, sm, stride);
+}
+
+template <class V>
+__global__ void __launch_bounds__(BT)
+    kb_apply(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, long long ntiles,
+             int slot, int prec, int src, unsigned long long* counter) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ long long item;
+  for (;;) {
+    if (threadIdx.x == 0) item = (long long)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const long long it = item;
+    __syncthreads();
+    if (it >= ntiles) break;
+    const Tile T = tiles[it];
+    const BProb& P = probs[T.prob];
+    if (*(volatile const int*)&P.sc[slot].done) continue;  // uniform over the CTA
+    switch (P.n) {
+      case 2: apply_item<2, V>(P, prec, src, T.cell0, sm); break;
+      case 3: apply_item<3, V>(P, prec, src, T.cell0, sm); break;
+      case 4: apply_item<4, V>(P, prec, src, T.cell0, sm); break;
+      case 5: apply_item<5, V>(P, prec, src, T.cell0, sm); break;
+      case 6: apply_item<6, V>(P, prec, src, T.cell0, sm); break;
+      case 7: apply_item<7, V>(P, prec, src, T.cell0, sm); break;
+      case 8: apply_item<8, V>(P, prec, src, T.cell0, sm); break;
+    }
+    __syncthreads();  // the next tile reuses the shared-memory tile
+  }
+}
+
+template <int N, class V>
+constexpr size_t tile_bytes() {
+  return (size_t)3 * (Cfg<N>::TILE + Cfg<N>::CS) * Sm<V>::BYTES;
+}
+template <class V>
+size_t max_tile_bytes() {
+  size_t b = tile_bytes<2, V>();
+  b = std::max(b, tile_bytes<3, V>());
+  b = std::max(b, tile_bytes<4, V>());
+  b = std::max(b, tile_bytes<5, V>());
+  b = std::max(b, tile_bytes<6, V>());
+  b = std::max(b, tile_bytes<7, V>());
+  b = std::max(b, tile_bytes<8, V>());
+  return b;
+}
+
+// ---- vector kernels over chunks ----------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ S* vec(const BProb& P, int which);
+// which: 0 x/d, 1 r, 2 z, 3 p, 4 q, 5 w
+template <>
+__device__ __forceinline__ double* vec<double>(const BProb& P, int which) {
+  switch (which) {
+    case 0: return P.x64;
+    case 1: return P.r64;
+    case 2: return P.z64;
+    case 3: return P.p64;
+    case 4: return P.q64;
+    case 5: return P.w64;
+    default: return const_cast<double*>(P.b64);
+  }
+}
+template <>
+__device__ __forceinline__ float* vec<float>(const BProb& P, int which) {
+  switch (which) {
+    case 0: return P.d32;
+    case 1: return P.r32;
+    case 2: return P.z32;
+    case 3: return P.p32;
+    case 4: return P.q32;
+    default: return P.w32;
+  }
+}
+
+template <class S>
+__device__ __forceinline__ dw prod2(S a, S b);
+template <>
+__device__ __forceinline__ dw prod2<double>(double a, double b) {
+  return dw_mul(dw_from_double(a), dw_from_double(b));
+}
+template <>
+__device__ __forceinline__ dw prod2<float>(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// partials[chunk*4 + 0] = sum q p
+template <class S>
+__global__ void __launch_bounds__(BT)
+    kb_qp(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks, int slot,
+          double* __restrict__ partials) {
+  __shared__ dw sh[32];
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[slot].done) continue;
+    const S* q = vec<S>(P, 4);
+    const S* p = vec<S>(P, 3);
+    dw acc = {0.0f, 0.0f};
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) acc = dw_add(acc, prod2<S>(q[e], p[e]));
+    acc = block_reduce_dw(acc, sh);
+    if (threadIdx.x == 0) partials[(size_t)c * 4 + 0] = dw_to_double(acc);
+  }
+}
+
+// u += alpha p ; r -= alpha q ; w = r
+template <class S>
+__global__ void __launch_bounds__(BT)
+    kb_update_ur(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks,
+                 int slot) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[slot].done) continue;
+    const double a = P.sc[slot].alpha;
+    S* u = vec<S>(P, 0);
+    S* r = vec<S>(P, 1);
+    const S* p = vec<S>(P, 3);
+    const S* q = vec<S>(P, 4);
+    S* w = vec<S>(P, 5);
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
+      u[e] = (S)((double)u[e] + a * (double)p[e]);
+      const S re = (S)((double)r[e] - a * (double)q[e]);
+      r[e] = re;
+      w[e] = re;
+    }
+  }
+}
+
+// structured DSS pass over every problem's interface node pairs of one axis
+template <class S>
+__global__ void __launch_bounds__(BT)
+    kb_dss(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks, int slot,
+           int axis) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[slot].done) continue;
+    S* v = vec<S>(P, 5);
+    const int n = P.n, p = n - 1, n2 = n * n, n3 = n2 * n, mx = P.mx, my = P.my;
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
+      const int f = (int)(e % n2);
+      const long long q = e / n2;
+      const int fa = f % n, fb = f / n;
+      long long L, R;
+      int locL, locR;
+      if (axis == 0) {
+        const long long cxL = q % (mx - 1), r = q / (mx - 1);
+        L = r * mx + cxL;
+        R = L + 1;
+        locL = (fb * n + fa) * n + p;
+        locR = (fb * n + fa) * n;
+      } else if (axis == 1) {
+        const long long cx = q % mx, r = q / mx, cyL = r % (my - 1), cz = r / (my - 1);
+        L = (cz * my + cyL) * mx + cx;
+        R = L + mx;
+        locL = (fb * n + p) * n + fa;
+        locR = (fb * n) * n + fa;
+      } else {
+        L = q;
+        R = L + (long long)mx * my;
+        locL = (p * n + fb) * n + fa;
+        locR = fb * n + fa;
+      }
+      S* pl = v + L * n3 + locL;
+      S* pr = v + R * n3 + locR;
+      const S s = *pl + *pr;
+      *pl = s;
+      *pr = s;
+    }
+  }
+}
+
+// z = w * invdiag (mode & 1), r = w * invmult (mode & 2, redistribute); partials slot 0 sum w^2/mult,
+// slot 1 <r,z>, slot 2 <q,z> (mode & 4)
+template <class S>
+__global__ void __launch_bounds__(BT)
+    kb_precond(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks,
+               int slot, int mode, double* __restrict__ partials) {
+  __shared__ dw sh[32];
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[slot].done) continue;
+    const S* w = vec<S>(P, 5);
+    S* r = vec<S>(P, 1);
+    S* z = vec<S>(P, 2);
+    const S* q = vec<S>(P, 4);
+    const S* idg = (sizeof(S) == 8) ? (const S*)P.invdiag64 : (const S*)P.invdiag32;
+    dw a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
+      const S we = w[e];
+      const dw w2 = prod2<S>(we, we);
+      const float im = P.invmult[e];
+      a0 = dw_add(a0, {w2.h * im, w2.l * im});
+      if (mode & 1) {
+        const S ze = we * idg[e];
+        z[e] = ze;
+        S re;
+        if (mode & 2) {
+          re = we * (S)im;
+          r[e] = re;
+        } else {
+          re = r[e];
+        }
+        a1 = dw_add(a1, prod2<S>(re, ze));
+        if (mode & 4) a2 = dw_add(a2, prod2<S>(q[e], ze));
+      }
+    }
+    a0 = block_reduce_dw(a0, sh);
+    if (threadIdx.x == 0) partials[(size_t)c * 4 + 0] = dw_to_double(a0);
+    if (mode & 1) {
+      a1 = block_reduce_dw(a1, sh);
+      if (threadIdx.x == 0) partials[(size_t)c * 4 + 1] = dw_to_double(a1);
+      if (mode & 4) {
+        a2 = block_reduce_dw(a2, sh);
+        if (threadIdx.x == 0) partials[(size_t)c * 4 + 2] = dw_to_double(a2);
+      }
+    }
+  }
+}
+
+// p = z + beta p
+template <class S>
+__global__ void __launch_bounds__(BT)
+    kb_update_p(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks,
+                int slot) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[slot].done) continue;
+    const S b = (S)P.sc[slot].beta;
+    S* p = vec<S>(P, 3);
+    const S* z = vec<S>(P, 2);
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) p[e] = z[e] + b * p[e];
+  }
+}
+
+// dst = src (which -> which)
+template <class S>
+__global__ void __launch_bounds__(BT)
+    kb_copy(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks, int slot,
+            int dst, int src) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[slot].done) continue;
+    S* d = vec<S>(P, dst);
+    const S* s = vec<S>(P, src);
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) d[e] = s[e];
+  }
+}
+
+// inner start: r32 = s (S r64) / mult with s = 1/sqrt(rnorm2) (w64 holds S r64), d32 = 0
+__global__ void __launch_bounds__(BT)
+    kb_to_inner(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[0].done) continue;
+    const double s = 1.0 / sqrt(P.sc[0].rnorm2);
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
+      P.r32[e] = (float)(s * P.w64[e] * (double)P.invmult[e]);
+      P.d32[e] = 0.0f;
+    }
+  }
+}
+
+// z64 = d32 / s ; partials slot 1 <r64, z64>, slot 2 <q64, z64> (with_q)
+__global__ void __launch_bounds__(BT)
+    kb_from_inner(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks,
+                  int with_q, double* __restrict__ partials) {
+  __shared__ dw sh[32];
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[0].done) continue;
+    const double inv_s = sqrt(P.sc[0].rnorm2);
+    dw a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
+      const double ze = inv_s * (double)P.d32[e];
+      P.z64[e] = ze;
+      a1 = dw_add(a1, prod2<double>(P.r64[e], ze));
+      if (with_q) a2 = dw_add(a2, prod2<double>(P.q64[e], ze));
+    }
+    a1 = block_reduce_dw(a1, sh);
+    if (threadIdx.x == 0) partials[(size_t)c * 4 + 1] = dw_to_double(a1);
+    if (with_q) {
+      a2 = block_reduce_dw(a2, sh);
+      if (threadIdx.x == 0) partials[(size_t)c * 4 + 2] = dw_to_double(a2);
+    }
+  }
+}
+
+// ---- per-problem finishing kernels (one CTA per problem) --------------------------------------
+__device__ double sum_chunks(const double* partials, int c0, int c1, int slot, dw* sh) {
+  dw acc = {0.0f, 0.0f};
+  for (int c = c0 + threadIdx.x; c < c1; c += BT)
+    acc = dw_add(acc, dw_from_double(partials[(size_t)c * 4 + slot]));
+  acc = block_reduce_dw(acc, sh);
+  return dw_to_double(acc);
+}
+
+__global__ void __launch_bounds__(BT)
+    kb_fin_alpha(BProb* __restrict__ probs, int slot, const double* __restrict__ partials) {
+  __shared__ dw sh[32];
+  BProb& P = probs[blockIdx.x];
+  CgScal* sc = &P.sc[slot];
+  if (*(volatile int*)&sc->done) return;
+  const double qp = sum_chunks(partials, P.chunk0, P.chunk1, 0, sh);
+  if (threadIdx.x != 0) return;
+  sc->qp = qp;
+  if (!(qp > 0.0) || !isfinite(qp) || !isfinite(sc->rz)) {
+    sc->status = FE_ERR_BREAKDOWN;
+    sc->done = 1;
+  } else {
+    sc->alpha = sc->rz / qp;
+  }
+}
+
+// mode: FIN_INIT_B, FIN_INIT_R, FIN_ITER, FIN_NORM (as in fe_cg.cu)
+__global__ void __launch_bounds__(BT)
+    kb_fin_beta(BProb* __restrict__ probs, int slot, double rtol, int mode, int flexible,
+                const double* __restrict__ partials) {
+  __shared__ dw sh[32];
+  BProb& P = probs[blockIdx.x];
+  CgScal* sc = &P.sc[slot];
+  if (*(volatile int*)&sc->done) return;
+  const double rn2 = sum_chunks(partials, P.chunk0, P.chunk1, 0, sh);
+  const double rz = (mode == FIN_INIT_R || mode == FIN_ITER) ? sum_chunks(partials, P.chunk0, P.chunk1, 1, sh) : 0.0;
+  const double qz = (mode == FIN_ITER && flexible) ? sum_chunks(partials, P.chunk0, P.chunk1, 2, sh) : 0.0;
+  if (threadIdx.x != 0) return;
+  fin_scalars(sc, rn2, rz, qz, rtol, mode, flexible);
+}
+
+// outer FCG scalars: init rz; iteration beta = -<q,z>/<q,p>, rz
+__global__ void __launch_bounds__(BT)
+    kb_fin_fcg(BProb* __restrict__ probs, int init, const double* __restrict__ partials) {
+  __shared__ dw sh[32];
+  BProb& P = probs[blockIdx.x];
+  CgScal* sc = &P.sc[0];
+  if (*(volatile int*)&sc->done) return;
+  const double rz = sum_chunks(partials, P.chunk0, P.chunk1, 1, sh);
+  const double qz = init ? 0.0 : sum_chunks(partials, P.chunk0, P.chunk1, 2, sh);
+  if (threadIdx.x != 0) return;
+  if (!init) sc->beta = -qz / sc->qp;
+  sc->rz = rz;
+}
+
+// reset the inner scalars for a new inner solve (done mirrors the outer state)
+__global__ void kb_reset_inner(BProb* __restrict__ probs, int nprob, int maxit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  CgScal* o = &probs[i].sc[0];
+  CgScal* in = &probs[i].sc[1];
+  const int spent = in->stall_total;  // inner iterations so far
+  if (!o->done && spent >= maxit) {
+    o->status = FE_ERR_NOT_CONVERGED;
+    o->done = 1;
+  }
+  CgScal s;
+  memset(&s, 0, sizeof(s));
+  s.maxit = maxit - spent > 0 ? maxit - spent : 1;
+  s.stall_limit = 20;
+  s.stall_total = spent;
+  s.done = o->done;
+  *in = s;
+}
+
+// accumulate the finished inner iteration count
+__global__ void kb_count_inner(BProb* __restrict__ probs, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  CgScal* in = &probs[i].sc[1];
+  if (!probs[i].sc[0].done) in->stall_total += in->iter;
+}
+
+// r = b - q
+__global__ void __launch_bounds__(BT)
+    kb_residual(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[0].done) continue;
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) P.r64[e] = P.b64[e] - P.q64[e];
+  }
+}
+
+// fresh scalars for a solve
+__global__ void kb_init_scal(BProb* __restrict__ probs, int nprob, int maxit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  CgScal s;
+  memset(&s, 0, sizeof(s));
+  s.maxit = maxit;
+  probs[i].sc[0] = s;
+  probs[i].sc[1] = s;
+}
+
+unsigned grid_chunks(int n) { return (unsigned)std::max(1, std::min(n, 152 * 8)); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// host engine
+// ---------------------------------------------------------------------------------------------
+fe_status fe_batch_build(FeBatch* B) {
+  const int np = (int)B->hp.size();
+  std::vector<Tile> tiles;
+  std::vector<Chunk> vch;
+  std::vector<Chunk> dch[3];
+  for (int i = 0; i < np; ++i) {
+    BProb& P = B->hp[i];
+    const int n = P.n;
+    int cpb = 0;
+    switch (n) {
+      case 2: cpb = Cfg<2>::CPB; break;
+      case 3: cpb = Cfg<3>::CPB; break;
+      case 4: cpb = Cfg<4>::CPB; break;
+      case 5: cpb = Cfg<5>::CPB; break;
+      case 6: cpb = Cfg<6>::CPB; break;
+      case 7: cpb = Cfg<7>::CPB; break;
+      case 8: cpb = Cfg<8>::CPB; break;
+    }
+    if (!B->active[i]) {
+      P.chunk0 = P.chunk1 = (int)vch.size();
+      continue;
+    }
+    for (long long c = 0; c < P.ncells; c += cpb) tiles.push_back({i, 0, c});
+    P.chunk0 = (int)vch.size();
+    for (long long e = 0; e < P.ncw; e += CHUNK) vch.push_back({i, 0, e, std::min(P.ncw, e + CHUNK)});
+    P.chunk1 = (int)vch.size();
+    const long long n2 = (long long)n * n;
+    const long long work[3] = {(long long)(P.mx - 1) * P.my * P.mz * n2,
+                               (long long)P.mx * (P.my - 1) * P.mz * n2,
+                               (long long)P.mx * P.my * (P.mz - 1) * n2};
+    for (int a = 0; a < 3; ++a)
+      for (long long e = 0; e < work[a]; e += CHUNK) dch[a].push_back({i, 0, e, std::min(work[a], e + CHUNK)});
+  }
+  // interleave tiles of different problems so that neighbouring items spread over the mix
+  B->ntiles = (long long)tiles.size();
+  B->nvch = (int)vch.size();
+  for (int a = 0; a < 3; ++a) B->ndch[a] = (int)dch[a].size();
+  auto up = [&](void** dst, size_t* cap, const void* src, size_t bytes) -> fe_status {
+    if (bytes > *cap) {
+      cudaFree(*dst);
+      *dst = nullptr;
+      FE_CUDA(cudaMalloc(dst, std::max<size_t>(bytes, 256)), "batch work list");
+      *cap = std::max<size_t>(bytes, 256);
+    }
+    if (bytes) FE_CUDA(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, B->st), "batch upload");
+    return FE_OK;
+  };
+  FE_TRY(up(&B->d_tiles, &B->cap_tiles, tiles.data(), tiles.size() * sizeof(Tile)));
+  FE_TRY(up(&B->d_vch, &B->cap_vch, vch.data(), vch.size() * sizeof(Chunk)));
+  for (int a = 0; a < 3; ++a)
+    FE_TRY(up(&B->d_dch[a], &B->cap_dch[a], dch[a].data(), dch[a].size() * sizeof(Chunk)));
+  FE_TRY(up((void**)&B->d_probs, &B->cap_probs, B->hp.data(), np * sizeof(BProb)));
+  const size_t pbytes = std::max<size_t>(1, vch.size()) * 4 * sizeof(double);
+  if (pbytes > B->cap_partials) {
+    cudaFree(B->d_partials);
+    B->d_partials = nullptr;
+    FE_CUDA(cudaMalloc(&B->d_partials, pbytes), "batch partials");
+    B->cap_partials = pbytes;
+  }
+  if (!B->d_counter) FE_CUDA(cudaMalloc(&B->d_counter, 64 * sizeof(unsigned long long)), "counter");
+  return FE_OK;
+}
+
+template <class S>
+static fe_status launch_apply_batched(FeBatch* B, int slot, int src = 0) {
+  using V = typename std::conditional<sizeof(S) == 8, dw, float>::type;
+  const size_t smem = max_tile_bytes<V>();
+  static bool attr[2] = {false, false};
+  if (!attr[sizeof(S) == 8]) {
+    FE_CUDA(cudaFuncSetAttribute(kb_apply<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "batch apply attribute");
+    attr[sizeof(S) == 8] = true;
+  }
+  FE_CUDA(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), B->st), "counter reset");
+  int per_sm = 0;
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_apply<V>, BT, smem), "occupancy");
+  const long long grid = std::max(1LL, std::min<long long>(B->ntiles, 152LL * std::max(1, per_sm)));
+  if (B->ntiles > 0)
+    kb_apply<V><<<(unsigned)grid, BT, smem, B->st>>>(B->d_probs, (const Tile*)B->d_tiles, B->ntiles, slot,
+                                                     sizeof(S) == 8 ? FE_F64 : FE_F32, src,
+                                                     B->d_counter);
+  return fe_cuda_check(cudaGetLastError(), "batch apply launch");
+}
+
+template <class S>
+static fe_status launch_dss_batched(FeBatch* B, int slot) {
+  for (int axis = 2; axis >= 0; --axis)
+    if (B->ndch[axis] > 0)
+      kb_dss<S><<<grid_chunks(B->ndch[axis]), BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_dch[axis],
+                                                              B->ndch[axis], slot, axis);
+  return fe_cuda_check(cudaGetLastError(), "batch dss launch");
+}
+
+// one PCG iteration of every active problem on vectors of type S, scalars `slot`
+template <class S>
+fe_status fe_batch_iteration(FeBatch* B, int slot, double rtol, int flexible, int redistribute) {
+  const int np = (int)B->hp.size();
+  const unsigned g = grid_chunks(B->nvch);
+  const Chunk* ch = (const Chunk*)B->d_vch;
+  FE_TRY(launch_apply_batched<S>(B, slot));
+  kb_qp<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot, B->d_partials);
+  kb_fin_alpha<<<np, BT, 0, B->st>>>(B->d_probs, slot, B->d_partials);
+  kb_update_ur<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot);
+  FE_TRY(launch_dss_batched<S>(B, slot));
+  kb_precond<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot,
+                                     1 | (redistribute ? 2 : 0) | (flexible ? 4 : 0), B->d_partials);
+  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, slot, rtol, FIN_ITER, flexible, B->d_partials);
+  kb_update_p<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot);
+  return fe_cuda_check(cudaGetLastError(), "batch iteration launch");
+}
+template fe_status fe_batch_iteration<double>(FeBatch*, int, double, int, int);
+template fe_status fe_batch_iteration<float>(FeBatch*, int, double, int, int);
+
+// w = S(src) and the norm (and, with init_dir, z = D^{-1} w, p = z, <r,z>) of every active problem
+template <class S>
+fe_status fe_batch_norm(FeBatch* B, int slot, int src, int mode, double rtol, int redistribute) {
+  const int np = (int)B->hp.size();
+  const unsigned g = grid_chunks(B->nvch);
+  const Chunk* ch = (const Chunk*)B->d_vch;
+  kb_copy<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot, 5, src);
+  FE_TRY(launch_dss_batched<S>(B, slot));
+  const int pm = (mode == FIN_INIT_R) ? (1 | (redistribute ? 2 : 0)) : 0;
+  kb_precond<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot, pm, B->d_partials);
+  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, slot, rtol, mode, 0, B->d_partials);
+  if (mode == FIN_INIT_R) kb_copy<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot, 3, 2);
+  return fe_cuda_check(cudaGetLastError(), "batch norm launch");
+}
+template fe_status fe_batch_norm<double>(FeBatch*, int, int, int, double, int);
+template fe_status fe_batch_norm<float>(FeBatch*, int, int, int, double, int);
+
+fe_status fe_batch_read(FeBatch* B) {
+  const int np = (int)B->hp.size();
+  for (int i = 0; i < np; ++i)
+    FE_CUDA(cudaMemcpyAsync(&B->hsc[2 * i], B->hp[i].sc, 2 * sizeof(CgScal), cudaMemcpyDeviceToHost,
+                            B->st),
+            "batch scalar readback");
+  return fe_cuda_check(cudaStreamSynchronize(B->st), "batch synchronize");
+}
+
+fe_status fe_batch_inner_start(FeBatch* B, int maxit) {
+  const int np = (int)B->hp.size();
+  kb_reset_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np, maxit);
+  kb_to_inner<<<grid_chunks(B->nvch), BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch);
+  FE_TRY(fe_batch_norm<float>(B, 1, 1, FIN_INIT_B, 0.0, 0));
+  return fe_batch_norm<float>(B, 1, 1, FIN_INIT_R, B->inner_rtol, 1);
+}
+
+fe_status fe_batch_inner_finish(FeBatch* B, int first) {
+  const int np = (int)B->hp.size();
+  const unsigned g = grid_chunks(B->nvch);
+  kb_count_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
+  kb_from_inner<<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch, first ? 0 : 1,
+                                     B->d_partials);
+  kb_fin_fcg<<<np, BT, 0, B->st>>>(B->d_probs, first ? 1 : 0, B->d_partials);
+  if (first)
+    kb_copy<double><<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch, 0, 3, 2);
+  else
+    kb_update_p<double><<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch, 0);
+  return fe_cuda_check(cudaGetLastError(), "batch inner finish");
+}
+
+// outer FCG step A: q = A p, alpha, x += alpha p, r -= alpha q, ||G^T r||, convergence
+fe_status fe_batch_outer_step(FeBatch* B, double rtol) {
+  const int np = (int)B->hp.size();
+  const unsigned g = grid_chunks(B->nvch);
+  const Chunk* ch = (const Chunk*)B->d_vch;
+  FE_TRY(launch_apply_batched<double>(B, 0));
+  kb_qp<double><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 0, B->d_partials);
+  kb_fin_alpha<<<np, BT, 0, B->st>>>(B->d_probs, 0, B->d_partials);
+  kb_update_ur<double><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 0);
+  FE_TRY(launch_dss_batched<double>(B, 0));
+  kb_precond<double><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 0, 0, B->d_partials);
+  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, 0, rtol, FIN_OUTER, 0, B->d_partials);
+  return fe_cuda_check(cudaGetLastError(), "batch outer step");
+}
+
+fe_status fe_batch_prepare() {
+  int dev = 0;
+  FE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  return ensure_tables(dev);
+}
+
+FeBatch::~FeBatch() {
+  cudaFree(d_probs);
+  cudaFree(d_tiles);
+  cudaFree(d_vch);
+  for (int a = 0; a < 3; ++a) cudaFree(d_dch[a]);
+  cudaFree(d_partials);
+  cudaFree(d_counter);
+  cudaFreeHost(hsc);
+  if (st) cudaStreamDestroy(st);
+}
+
+fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const double* b) {
+  BProb& P = B->hp[i];
+  std::memset(&P, 0, sizeof(P));
+  P.n = m->n;
+  P.affine = m->d.geom_mode == FE_GEOM_AFFINE;
+  P.ncells = m->ncells;
+  P.ncw = m->ncw;
+  P.mx = m->d.mx;
+  P.my = m->d.my;
+  P.mz = m->d.mz;
+  P.dirichlet = m->d.dirichlet;
+  const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / m->d.mz, det = hx * hy * hz;
+  P.aff[0] = det / (hx * hx);
+  P.aff[1] = det / (hy * hy);
+  P.aff[2] = det / (hz * hz);
+  P.aff[3] = det;
+  P.geodw = m->geodw;
+  P.geo32 = m->geo32;
+  P.x64 = w->x;
+  P.r64 = w->r;
+  P.z64 = w->z;
+  P.p64 = w->p;
+  P.q64 = w->q;
+  P.w64 = w->w;
+  P.b64 = b;
+  P.d32 = w->d32;
+  P.r32 = w->r32;
+  P.z32 = w->z32;
+  P.p32 = w->p32;
+  P.q32 = w->q32;
+  P.w32 = w->w32;
+  P.invdiag64 = w->invdiag64;
+  P.invdiag32 = w->invdiag32;
+  P.invmult = w->invmult;
+  P.sc = w->sc;
+  return FE_OK;
+}
+
+fe_status fe_batch_setup(FeBatch* B, int maxit) {
+  const int np = (int)B->hp.size();
+  const unsigned g = grid_chunks(B->nvch);
+  const Chunk* ch = (const Chunk*)B->d_vch;
+  kb_init_scal<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np, maxit);
+  FE_TRY(fe_batch_norm<double>(B, 0, 6, FIN_INIT_B, 0.0, 0));  // ||G^T b||
+  FE_TRY(launch_apply_batched<double>(B, 0, 1));               // q = A x
+  kb_residual<<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch);
+  return fe_cuda_check(cudaGetLastError(), "batch setup");
+}
+
+static bool all_done(FeBatch* B, int slot) {
+  for (size_t i = 0; i < B->hp.size(); ++i)
+    if (B->active[i] && !B->hsc[2 * i + slot].done) return false;
+  return true;
+}
+
+fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts) {
+  const int flex = opts->flexible ? 1 : 0;
+  const int batch = 8;
+  FE_TRY(fe_batch_setup(B, opts->maxit));
+  if (opts->mixed != FE_F32) {
+    FE_TRY(fe_batch_norm<double>(B, 0, 1, FIN_INIT_R, opts->rtol, 0));
+    FE_TRY(fe_batch_read(B));
+    while (!all_done(B, 0)) {
+      for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<double>(B, 0, opts->rtol, flex, 0));
+      FE_TRY(fe_batch_read(B));
+    }
+    return FE_OK;
+  }
+  // mixed: FP64 FCG, preconditioner = FP32 PCG solve
+  B->inner_rtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 1e-2;
+  FE_TRY(fe_batch_norm<double>(B, 0, 1, FIN_NORM, 0.0, 0));
+  {  // problems already converged at the start
+    const int np = (int)B->hp.size();
+    kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, 0, opts->rtol, FIN_OUTER, 0, B->d_partials);
+    FE_CUDA(cudaGetLastError(), "batch start check");
+  }
+  int first = 1;
+  for (;;) {
+    FE_TRY(fe_batch_read(B));
+    if (all_done(B, 0)) break;
+    FE_TRY(fe_batch_inner_start(B, opts->maxit));
+    FE_TRY(fe_batch_read(B));
+    while (!all_done(B, 1)) {
+      for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<float>(B, 1, B->inner_rtol, 0, 1));
+      FE_TRY(fe_batch_read(B));
+    }
+    FE_TRY(fe_batch_inner_finish(B, first));
+    first = 0;
+    FE_TRY(fe_batch_outer_step(B, opts->rtol));
+  }
+  return FE_OK;
+}
+
+extern "C" fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes,
+                                         const double* const* b, double* const* x,
+                                         const fe_cg_opts* opts, fe_cg_result* res, void* stream) {
+  if (nprob < 1 || !meshes || !b || !x || !opts || !res) {
+    fe_set_error("fe_cg_solve_batched: null argument or nprob < 1");
+    return FE_ERR_INVALID;
+  }
+  if (opts->maxit < 1 || !(opts->rtol >= 0.0) || (opts->mixed != 0 && opts->mixed != FE_F32)) {
+    fe_set_error("fe_cg_solve_batched: invalid options");
+    return FE_ERR_INVALID;
+  }
+  for (int i = 0; i < nprob; ++i) {
+    if (!meshes[i] || !b[i] || !x[i] || !fe_aligned(b[i]) || !fe_aligned(x[i])) {
+      fe_set_error("fe_cg_solve_batched: problem %d: null or misaligned argument", i);
+      return FE_ERR_INVALID;
+    }
+    if (meshes[i]->d.geom_mode == FE_GEOM_RECOMPUTE || meshes[i]->d.device != meshes[0]->d.device) {
+      fe_set_error("fe_cg_solve_batched: problem %d: needs stored/affine geometry on one device", i);
+      return FE_ERR_INVALID;
+    }
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i]) {
+        fe_set_error("fe_cg_solve_batched: mesh %d appears twice", i);
+        return FE_ERR_INVALID;
+      }
+  }
+  FE_CUDA(cudaSetDevice(meshes[0]->d.device), "cudaSetDevice");
+  FE_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "caller stream");
+  const bool mixed = opts->mixed == FE_F32;
+  FE_TRY(fe_batch_prepare());
+  FeBatch B;
+  FE_CUDA(cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking), "batch stream");
+  B.hp.resize(nprob);
+  B.active.assign(nprob, 1);
+  FE_CUDA(cudaMallocHost(&B.hsc, 2 * nprob * sizeof(CgScal)), "batch scalars");
+  B.cap_hsc = 2 * nprob;
+  for (int i = 0; i < nprob; ++i) {
+    CgWork* w = nullptr;
+    FE_TRY(fe_cg_get_work(meshes[i], mixed, &w));
+    FE_TRY(fe_ensure_geometry(meshes[i], FE_F64, false));
+    if (mixed) FE_TRY(fe_ensure_geometry(meshes[i], FE_F32, false));
+    FE_TRY(fe_cg_ensure_diag(meshes[i], w, FE_LAPLACE));
+    FE_CUDA(cudaStreamSynchronize(w->st), "workspace set-up");
+    FE_CUDA(cudaMemcpyAsync(w->x, x[i], meshes[i]->ncw * sizeof(double), cudaMemcpyDeviceToDevice,
+                            B.st),
+            "batch copy x");
+    FE_TRY(fe_batch_fill(&B, i, meshes[i], w, b[i]));
+  }
+  FE_TRY(fe_batch_build(&B));
+  FE_TRY(fe_batch_solve(&B, opts));
+  FE_TRY(fe_batch_read(&B));
+  fe_status worst = FE_OK;
+  for (int i = 0; i < nprob; ++i) {
+    FE_CUDA(cudaMemcpyAsync(x[i], B.hp[i].x64, meshes[i]->ncw * sizeof(double),
+                            cudaMemcpyDeviceToDevice, B.st),
+            "batch copy x back");
+    const CgScal& o = B.hsc[2 * i];
+    const CgScal& in = B.hsc[2 * i + 1];
+    res[i].status = (fe_status)o.status;
+    res[i].rel_res = o.relres;
+    res[i].iters = mixed ? in.stall_total : o.iter;
+    res[i].outer_iters = mixed ? o.iter : 1;
+    if (o.status != FE_OK && worst == FE_OK) worst = (fe_status)o.status;
+  }
+  FE_CUDA(cudaStreamSynchronize(B.st), "batch synchronize");
+  if (worst != FE_OK) fe_set_error("fe_cg_solve_batched: some problems did not converge");
+  return worst;
+}

@@ -21,19 +21,10 @@
 #include <cstring>
 #include <new>
 
+#include "fe_cgcore.h"
 #include "fe_vec.cuh"
 
 namespace {
-
-struct CgScal {
-  double rz, rz_new, qp, qz, alpha, beta, rnorm2, bnorm2, relres;
-  double best;      // smallest relative residual so far
-  int done, status, iter, maxit;
-  int stall;        // iterations since `best` last dropped by 10%
-  int stall_limit;  // stop after this many iterations without progress (0 = never)
-};
-
-enum { FIN_INIT_B = 0, FIN_INIT_R = 1, FIN_ITER = 2, FIN_NORM = 3 };
 
 // ---- element-wise kernels -------------------------------------------------------------------
 __global__ void k_invmult(float* __restrict__ out, long long ncells, int n, int mx, int my, int mz,
@@ -238,62 +229,18 @@ __global__ void __launch_bounds__(RED_THREADS)
 __global__ void __launch_bounds__(RED_THREADS)
     k_fin_beta(const double* __restrict__ partials, CgScal* __restrict__ sc, double rtol, int mode,
                int flexible, double* hist) {
-  if (mode == FIN_ITER && *(volatile const int*)&sc->done) return;
+  if ((mode == FIN_ITER || mode == FIN_OUTER) && *(volatile const int*)&sc->done) return;
   __shared__ dw sh[32];
   const double rn2 = sum_slot(partials, 0, sh);
   const double rz = (mode == FIN_INIT_R || mode == FIN_ITER) ? sum_slot(partials, 1, sh) : 0.0;
   const double qz = (mode == FIN_ITER && flexible) ? sum_slot(partials, 2, sh) : 0.0;
   if (threadIdx.x != 0) return;
-  if (mode == FIN_INIT_B) {
-    sc->bnorm2 = rn2;
-    return;
-  }
-  sc->rnorm2 = rn2;
-  const double rel = sc->bnorm2 > 0.0 ? sqrt(rn2 / sc->bnorm2) : 0.0;
-  sc->relres = rel;
-  if (mode == FIN_NORM) return;
-  if (mode == FIN_INIT_R) {
-    sc->rz = rz;
-    sc->best = rel;
-    sc->stall = 0;
-    sc->iter = 0;
-    sc->status = FE_OK;
-    sc->done = (rel <= rtol) ? 1 : 0;
-    return;
-  }
   const int k = sc->iter;
-  if (hist) hist[3 * k + 2] = rel;
-  sc->iter = k + 1;
-  if (!isfinite(rel)) {
-    sc->status = FE_ERR_BREAKDOWN;
-    sc->done = 1;
-    return;
+  fin_scalars(sc, rn2, rz, qz, rtol, mode, flexible);
+  if (hist && mode == FIN_ITER) {
+    hist[3 * k + 2] = sc->relres;
+    if (!sc->done) hist[3 * k + 1] = sc->beta;
   }
-  if (rel <= rtol) {
-    sc->status = FE_OK;
-    sc->done = 1;
-    return;
-  }
-  // Stagnation guard of the FP32 inner solve: FP32 rounding makes the operator slightly
-  // non-symmetric, and CG then levels off near eps_32 * cond(A); the FP64 outer refinement takes
-  // over from there.
-  if (rel < 0.9 * sc->best) {
-    sc->best = rel;
-    sc->stall = 0;
-  } else if (sc->stall_limit > 0 && ++sc->stall >= sc->stall_limit) {
-    sc->status = FE_OK;
-    sc->done = 1;
-    return;
-  }
-  if (k + 1 >= sc->maxit) {
-    sc->status = FE_ERR_NOT_CONVERGED;
-    sc->done = 1;
-    return;
-  }
-  const double beta = flexible ? -qz / sc->qp : rz / sc->rz;
-  sc->beta = beta;
-  sc->rz = rz;
-  if (hist) hist[3 * k + 1] = beta;
 }
 
 // z = d / s (FP64 primal correction from the FP32 inner solve)
@@ -342,27 +289,9 @@ unsigned grid_for(long long n) {
 }
 
 // ---- workspace -------------------------------------------------------------------------------
-struct CgWork {
-  long long n = 0;
-  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *w = nullptr;
-  float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *w32 = nullptr,
-        *d32 = nullptr;
-  double* invdiag64 = nullptr;
-  float* invdiag32 = nullptr;
-  float* invmult = nullptr;
-  double* partials = nullptr;
-  CgScal* sc = nullptr;   // [0] outer / FP64 solve, [1] inner FP32 solve
-  CgScal* hsc = nullptr;  // pinned host mirror
-  double* hist = nullptr;
-  int hist_cap = 0;
-  int diag_op = -1;
-  cudaStream_t st = nullptr;
-  cudaGraphExec_t g64[2] = {nullptr, nullptr};  // [flexible]
-  cudaGraphExec_t g32[2] = {nullptr, nullptr};
-  double* g64_hist = nullptr;
-};
+}  // namespace
 
-void free_work(CgWork* w) {
+static void free_work(CgWork* w) {
   if (!w) return;
   for (int f = 0; f < 2; ++f) {
     if (w->g64[f]) cudaGraphExecDestroy(w->g64[f]);
@@ -378,7 +307,7 @@ void free_work(CgWork* w) {
   delete w;
 }
 
-fe_status get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
+fe_status fe_cg_get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
   fe_mesh* m = const_cast<fe_mesh*>(cm);
   CgWork* w = static_cast<CgWork*>(m->cg_work);
   if (!w) {
@@ -411,7 +340,7 @@ fe_status get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
   return FE_OK;
 }
 
-fe_status ensure_diag(const fe_mesh* m, CgWork* w, int op) {
+fe_status fe_cg_ensure_diag(const fe_mesh* m, CgWork* w, int op) {
   if (w->diag_op == op) return FE_OK;
   // w->q as scratch for the assembled diagonal
   FE_TRY(fe_launch_diag(m, op, w->q, w->st));
@@ -420,6 +349,8 @@ fe_status ensure_diag(const fe_mesh* m, CgWork* w, int op) {
   w->diag_op = op;
   return FE_OK;
 }
+
+namespace {
 
 // one PCG iteration on vectors of type S, solution of type U, scalars sc
 template <class S, class U>
@@ -644,11 +575,11 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
   const bool mixed = opts->mixed == FE_F32;
   const int op = FE_LAPLACE;
   CgWork* w = nullptr;
-  FE_TRY(get_work(m, mixed, &w));
+  FE_TRY(fe_cg_get_work(m, mixed, &w));
   FE_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cg: caller stream");
   FE_TRY(fe_ensure_geometry(m, FE_F64, false));
   if (mixed) FE_TRY(fe_ensure_geometry(m, FE_F32, false));
-  FE_TRY(ensure_diag(m, w, op));
+  FE_TRY(fe_cg_ensure_diag(m, w, op));
   const long long n = w->n;
   const int flex = opts->flexible ? 1 : 0;
   if (opts->history && (!w->hist || w->hist_cap < opts->maxit)) {

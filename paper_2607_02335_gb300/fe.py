@@ -67,6 +67,8 @@ _SIGS = {
     "fe_pairing_noalloc": [_MESH, _i, _vp, _vp, _vp, _vp],
     "fe_cg_solve": [_MESH, _vp, _vp, ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_cg_result), _vp],
     "fe_rhs": [_MESH, _i, _vp, _vp],
+    "fe_cg_solve_batched": [_i, ctypes.POINTER(_MESH), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                            ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_cg_result), _vp],
     "fe_l2_error": [_MESH, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp],
 }
 for _name, _args in _SIGS.items():
@@ -174,6 +176,20 @@ def fe_cg_solve(mesh: int, b, x, opts: fe_cg_opts, stream=None) -> fe_cg_result:
         raise FeError(st, "fe_cg_solve")
     res.status = st
     return res
+
+
+def fe_cg_solve_batched(meshes, b, x, opts: fe_cg_opts, stream=None):
+    """meshes: list of mesh handles; b, x: lists of device tensors (or pointers).  Returns the list
+    of fe_cg_result; non-convergence is reported per problem in result.status."""
+    n = len(meshes)
+    hs = (_MESH * n)(*meshes)
+    bs = (_vp * n)(*[_ptr(v) for v in b])
+    xs = (_vp * n)(*[_ptr(v) for v in x])
+    res = (fe_cg_result * n)()
+    st = _lib.fe_cg_solve_batched(n, hs, bs, xs, ctypes.byref(opts), res, _stream(stream))
+    if st not in (FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN):
+        raise FeError(st, "fe_cg_solve_batched")
+    return list(res)
 
 
 # ---- convenience object ---------------------------------------------------------------------------
