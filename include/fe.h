@@ -193,6 +193,32 @@ fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes, const dou
                               double* const* x, const fe_cg_opts* opts, fe_cg_result* res,
                               void* stream);
 
+/* Request server with continuous batching (the paper has no serving; this follows the same
+ * batched engine as fe_cg_solve_batched).  A worker thread admits submitted solves in arrival
+ * order while one of max_slots slots is free and the request's device-memory estimate fits
+ * mem_budget bytes, builds its mesh and workspace, and joins it to the running batch: FP64
+ * requests at once, mixed-precision requests at the next outer-iteration boundary.  One
+ * persistent launch per iteration applies the operators of every solve in the batch; converged
+ * solves retire, copy their solution to host memory and free their device memory (a library-owned
+ * stream-ordered pool).  Each result is bitwise the same as when the request is served alone.
+ *  fe_serve_create: device is the CUDA device the server uses.
+ *  fe_serve_submit: desc describes the mesh (geom_mode STORED or AFFINE, device = the server's);
+ *    b_host is a HOST cell-wise dual right-hand side of the mesh's cellwise_len doubles, copied at
+ *    submission, or NULL for the manufactured sine load (FE_RHS_SINE); opts as in fe_cg_solve
+ *    (mixed = FE_F32 runs FP64 FCG preconditioned by an FP32 PCG solve).  *ticket identifies the
+ *    request.  FE_ERR_OOM if the request alone exceeds the budget.
+ *  fe_serve_poll: FE_ERR_BUSY while pending; FE_OK fills *res and, if x_host is not NULL, copies
+ *    the solution (cellwise_len doubles) and forgets the ticket.  Non-blocking.
+ *  fe_serve_stats: p50 and p99 of (completion - submission) over completed requests, in seconds,
+ *    and completed solves per second since the first submission.
+ *  fe_serve_destroy: finishes every admitted and queued request, then frees the server. */
+fe_status fe_serve_create(size_t mem_budget, int max_slots, int device, fe_server** out);
+fe_status fe_serve_submit(fe_server* server, const fe_mesh_desc* desc, const double* b_host,
+                          const fe_cg_opts* opts, long long* ticket);
+fe_status fe_serve_poll(fe_server* server, long long ticket, fe_cg_result* res, double* x_host);
+fe_status fe_serve_stats(fe_server* server, double* p50_s, double* p99_s, double* solves_per_s);
+fe_status fe_serve_destroy(fe_server* server);
+
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char* fe_last_error(void);
 

@@ -456,14 +456,16 @@ __global__ void __launch_bounds__(BT)
   }
 }
 
-// mode: FIN_INIT_B, FIN_INIT_R, FIN_ITER, FIN_NORM (as in fe_cg.cu)
+// mode: FIN_INIT_B, FIN_INIT_R, FIN_ITER, FIN_NORM, FIN_OUTER (fe_cgcore.h); tolerances and the
+// FCG switch are per problem (slot 0: the outer or FP64 solve, slot 1: the inner FP32 solve)
 __global__ void __launch_bounds__(BT)
-    kb_fin_beta(BProb* __restrict__ probs, int slot, double rtol, int mode, int flexible,
-                const double* __restrict__ partials) {
+    kb_fin_beta(BProb* __restrict__ probs, int slot, int mode, const double* __restrict__ partials) {
   __shared__ dw sh[32];
   BProb& P = probs[blockIdx.x];
   CgScal* sc = &P.sc[slot];
   if (*(volatile int*)&sc->done) return;
+  const int flexible = slot == 0 ? P.flexible : 0;
+  const double rtol = slot == 0 ? P.rtol : P.irtol;
   const double rn2 = sum_chunks(partials, P.chunk0, P.chunk1, 0, sh);
   const double rz = (mode == FIN_INIT_R || mode == FIN_ITER) ? sum_chunks(partials, P.chunk0, P.chunk1, 1, sh) : 0.0;
   const double qz = (mode == FIN_ITER && flexible) ? sum_chunks(partials, P.chunk0, P.chunk1, 2, sh) : 0.0;
@@ -471,13 +473,15 @@ __global__ void __launch_bounds__(BT)
   fin_scalars(sc, rn2, rz, qz, rtol, mode, flexible);
 }
 
-// outer FCG scalars: init rz; iteration beta = -<q,z>/<q,p>, rz
+// outer FCG scalars: a problem's first preconditioned residual (sc[0].pad set) only records
+// rz = <r,z>; later ones give beta = -<q,z>/<q,p> and rz
 __global__ void __launch_bounds__(BT)
-    kb_fin_fcg(BProb* __restrict__ probs, int init, const double* __restrict__ partials) {
+    kb_fin_fcg(BProb* __restrict__ probs, const double* __restrict__ partials) {
   __shared__ dw sh[32];
   BProb& P = probs[blockIdx.x];
   CgScal* sc = &P.sc[0];
   if (*(volatile int*)&sc->done) return;
+  const int init = sc->pad;
   const double rz = sum_chunks(partials, P.chunk0, P.chunk1, 1, sh);
   const double qz = init ? 0.0 : sum_chunks(partials, P.chunk0, P.chunk1, 2, sh);
   if (threadIdx.x != 0) return;
@@ -485,10 +489,28 @@ __global__ void __launch_bounds__(BT)
   sc->rz = rz;
 }
 
+// p = z (first direction of a problem) or p = z + beta p
+__global__ void __launch_bounds__(BT)
+    kb_update_p_fcg(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[0].done) continue;
+    const double b = P.sc[0].pad ? 0.0 : P.sc[0].beta;
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) P.p64[e] = P.z64[e] + b * P.p64[e];
+  }
+}
+
+__global__ void kb_clear_first(BProb* __restrict__ probs, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nprob) probs[i].sc[0].pad = 0;
+}
+
 // reset the inner scalars for a new inner solve (done mirrors the outer state)
-__global__ void kb_reset_inner(BProb* __restrict__ probs, int nprob, int maxit) {
+__global__ void kb_reset_inner(BProb* __restrict__ probs, int nprob) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nprob) return;
+  const int maxit = probs[i].maxit;
   CgScal* o = &probs[i].sc[0];
   CgScal* in = &probs[i].sc[1];
   const int spent = in->stall_total;  // inner iterations so far
@@ -525,14 +547,24 @@ __global__ void __launch_bounds__(BT)
 }
 
 // fresh scalars for a solve
-__global__ void kb_init_scal(BProb* __restrict__ probs, int nprob, int maxit) {
+__global__ void kb_init_scal(BProb* __restrict__ probs, int nprob) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nprob) return;
+  const int maxit = probs[i].maxit;
   CgScal s;
   memset(&s, 0, sizeof(s));
   s.maxit = maxit;
-  probs[i].sc[0] = s;
   probs[i].sc[1] = s;
+  s.pad = 1;  // first outer direction still to come
+  probs[i].sc[0] = s;
+}
+
+// contiguous copy of every problem's two scalar records, for one readback
+__global__ void kb_gather_sc(const BProb* __restrict__ probs, int nprob, CgScal* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  out[2 * i] = probs[i].sc[0];
+  out[2 * i + 1] = probs[i].sc[1];
 }
 
 unsigned grid_chunks(int n) { return (unsigned)std::max(1, std::min(n, 152 * 8)); }
@@ -581,10 +613,11 @@ fe_status fe_batch_build(FeBatch* B) {
   for (int a = 0; a < 3; ++a) B->ndch[a] = (int)dch[a].size();
   auto up = [&](void** dst, size_t* cap, const void* src, size_t bytes) -> fe_status {
     if (bytes > *cap) {
-      cudaFree(*dst);
+      fe_dfree(*dst, B->st);
       *dst = nullptr;
-      FE_CUDA(cudaMalloc(dst, std::max<size_t>(bytes, 256)), "batch work list");
-      *cap = std::max<size_t>(bytes, 256);
+      const size_t nb = std::max<size_t>(bytes + bytes / 2, 256);
+      FE_TRY(fe_dalloc(dst, nb, B->st, "batch work list"));
+      *cap = nb;
     }
     if (bytes) FE_CUDA(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, B->st), "batch upload");
     return FE_OK;
@@ -596,12 +629,20 @@ fe_status fe_batch_build(FeBatch* B) {
   FE_TRY(up((void**)&B->d_probs, &B->cap_probs, B->hp.data(), np * sizeof(BProb)));
   const size_t pbytes = std::max<size_t>(1, vch.size()) * 4 * sizeof(double);
   if (pbytes > B->cap_partials) {
-    cudaFree(B->d_partials);
+    fe_dfree(B->d_partials, B->st);
     B->d_partials = nullptr;
-    FE_CUDA(cudaMalloc(&B->d_partials, pbytes), "batch partials");
-    B->cap_partials = pbytes;
+    FE_TRY(fe_dalloc((void**)&B->d_partials, pbytes + pbytes / 2, B->st, "batch partials"));
+    B->cap_partials = pbytes + pbytes / 2;
   }
-  if (!B->d_counter) FE_CUDA(cudaMalloc(&B->d_counter, 64 * sizeof(unsigned long long)), "counter");
+  if (!B->d_counter)
+    FE_TRY(fe_dalloc((void**)&B->d_counter, 64 * sizeof(unsigned long long), B->st, "counter"));
+  FE_TRY(up((void**)&B->d_sc, &B->cap_sc, nullptr, 0));
+  if (B->cap_sc < 2 * np * sizeof(CgScal)) {
+    fe_dfree(B->d_sc, B->st);
+    B->d_sc = nullptr;
+    B->cap_sc = 2 * (size_t)np * sizeof(CgScal) + 64 * sizeof(CgScal);
+    FE_TRY(fe_dalloc((void**)&B->d_sc, B->cap_sc, B->st, "batch scalar gather"));
+  }
   return FE_OK;
 }
 
@@ -637,7 +678,8 @@ static fe_status launch_dss_batched(FeBatch* B, int slot) {
 
 // one PCG iteration of every active problem on vectors of type S, scalars `slot`
 template <class S>
-fe_status fe_batch_iteration(FeBatch* B, int slot, double rtol, int flexible, int redistribute) {
+fe_status fe_batch_iteration(FeBatch* B, int slot, int redistribute) {
+  const int flexible = slot == 0 ? B->any_flexible : 0;
   const int np = (int)B->hp.size();
   const unsigned g = grid_chunks(B->nvch);
   const Chunk* ch = (const Chunk*)B->d_vch;
@@ -648,16 +690,16 @@ fe_status fe_batch_iteration(FeBatch* B, int slot, double rtol, int flexible, in
   FE_TRY(launch_dss_batched<S>(B, slot));
   kb_precond<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot,
                                      1 | (redistribute ? 2 : 0) | (flexible ? 4 : 0), B->d_partials);
-  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, slot, rtol, FIN_ITER, flexible, B->d_partials);
+  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, slot, FIN_ITER, B->d_partials);
   kb_update_p<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot);
   return fe_cuda_check(cudaGetLastError(), "batch iteration launch");
 }
-template fe_status fe_batch_iteration<double>(FeBatch*, int, double, int, int);
-template fe_status fe_batch_iteration<float>(FeBatch*, int, double, int, int);
+template fe_status fe_batch_iteration<double>(FeBatch*, int, int);
+template fe_status fe_batch_iteration<float>(FeBatch*, int, int);
 
 // w = S(src) and the norm (and, with init_dir, z = D^{-1} w, p = z, <r,z>) of every active problem
 template <class S>
-fe_status fe_batch_norm(FeBatch* B, int slot, int src, int mode, double rtol, int redistribute) {
+fe_status fe_batch_norm(FeBatch* B, int slot, int src, int mode, int redistribute) {
   const int np = (int)B->hp.size();
   const unsigned g = grid_chunks(B->nvch);
   const Chunk* ch = (const Chunk*)B->d_vch;
@@ -665,46 +707,43 @@ fe_status fe_batch_norm(FeBatch* B, int slot, int src, int mode, double rtol, in
   FE_TRY(launch_dss_batched<S>(B, slot));
   const int pm = (mode == FIN_INIT_R) ? (1 | (redistribute ? 2 : 0)) : 0;
   kb_precond<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot, pm, B->d_partials);
-  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, slot, rtol, mode, 0, B->d_partials);
+  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, slot, mode, B->d_partials);
   if (mode == FIN_INIT_R) kb_copy<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot, 3, 2);
   return fe_cuda_check(cudaGetLastError(), "batch norm launch");
 }
-template fe_status fe_batch_norm<double>(FeBatch*, int, int, int, double, int);
-template fe_status fe_batch_norm<float>(FeBatch*, int, int, int, double, int);
+template fe_status fe_batch_norm<double>(FeBatch*, int, int, int, int);
+template fe_status fe_batch_norm<float>(FeBatch*, int, int, int, int);
 
 fe_status fe_batch_read(FeBatch* B) {
   const int np = (int)B->hp.size();
-  for (int i = 0; i < np; ++i)
-    FE_CUDA(cudaMemcpyAsync(&B->hsc[2 * i], B->hp[i].sc, 2 * sizeof(CgScal), cudaMemcpyDeviceToHost,
-                            B->st),
-            "batch scalar readback");
+  if (np == 0) return FE_OK;
+  kb_gather_sc<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np, B->d_sc);
+  FE_CUDA(cudaMemcpyAsync(B->hsc, B->d_sc, 2 * np * sizeof(CgScal), cudaMemcpyDeviceToHost, B->st),
+          "batch scalar readback");
   return fe_cuda_check(cudaStreamSynchronize(B->st), "batch synchronize");
 }
 
-fe_status fe_batch_inner_start(FeBatch* B, int maxit) {
+fe_status fe_batch_inner_start(FeBatch* B) {
   const int np = (int)B->hp.size();
-  kb_reset_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np, maxit);
+  kb_reset_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
   kb_to_inner<<<grid_chunks(B->nvch), BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch);
-  FE_TRY(fe_batch_norm<float>(B, 1, 1, FIN_INIT_B, 0.0, 0));
-  return fe_batch_norm<float>(B, 1, 1, FIN_INIT_R, B->inner_rtol, 1);
+  FE_TRY(fe_batch_norm<float>(B, 1, 1, FIN_INIT_B, 0));
+  return fe_batch_norm<float>(B, 1, 1, FIN_INIT_R, 1);
 }
 
-fe_status fe_batch_inner_finish(FeBatch* B, int first) {
+fe_status fe_batch_inner_finish(FeBatch* B) {
   const int np = (int)B->hp.size();
   const unsigned g = grid_chunks(B->nvch);
   kb_count_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
-  kb_from_inner<<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch, first ? 0 : 1,
-                                     B->d_partials);
-  kb_fin_fcg<<<np, BT, 0, B->st>>>(B->d_probs, first ? 1 : 0, B->d_partials);
-  if (first)
-    kb_copy<double><<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch, 0, 3, 2);
-  else
-    kb_update_p<double><<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch, 0);
+  kb_from_inner<<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch, 1, B->d_partials);
+  kb_fin_fcg<<<np, BT, 0, B->st>>>(B->d_probs, B->d_partials);
+  kb_update_p_fcg<<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch);
+  kb_clear_first<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
   return fe_cuda_check(cudaGetLastError(), "batch inner finish");
 }
 
 // outer FCG step A: q = A p, alpha, x += alpha p, r -= alpha q, ||G^T r||, convergence
-fe_status fe_batch_outer_step(FeBatch* B, double rtol) {
+fe_status fe_batch_outer_step(FeBatch* B) {
   const int np = (int)B->hp.size();
   const unsigned g = grid_chunks(B->nvch);
   const Chunk* ch = (const Chunk*)B->d_vch;
@@ -714,7 +753,7 @@ fe_status fe_batch_outer_step(FeBatch* B, double rtol) {
   kb_update_ur<double><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 0);
   FE_TRY(launch_dss_batched<double>(B, 0));
   kb_precond<double><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 0, 0, B->d_partials);
-  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, 0, rtol, FIN_OUTER, 0, B->d_partials);
+  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, 0, FIN_OUTER, B->d_partials);
   return fe_cuda_check(cudaGetLastError(), "batch outer step");
 }
 
@@ -725,19 +764,27 @@ fe_status fe_batch_prepare() {
 }
 
 FeBatch::~FeBatch() {
-  cudaFree(d_probs);
-  cudaFree(d_tiles);
-  cudaFree(d_vch);
-  for (int a = 0; a < 3; ++a) cudaFree(d_dch[a]);
-  cudaFree(d_partials);
-  cudaFree(d_counter);
+  if (st) cudaStreamSynchronize(st);
+  fe_dfree(d_probs, st);
+  fe_dfree(d_tiles, st);
+  fe_dfree(d_vch, st);
+  for (int a = 0; a < 3; ++a) fe_dfree(d_dch[a], st);
+  fe_dfree(d_partials, st);
+  fe_dfree(d_counter, st);
+  fe_dfree(d_sc, st);
+  if (st) cudaStreamSynchronize(st);
   cudaFreeHost(hsc);
-  if (st) cudaStreamDestroy(st);
+  if (st && own_stream) cudaStreamDestroy(st);
 }
 
-fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const double* b) {
+fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const double* b,
+                        const fe_cg_opts* opts) {
   BProb& P = B->hp[i];
   std::memset(&P, 0, sizeof(P));
+  P.rtol = opts->rtol;
+  P.irtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 1e-2;
+  P.maxit = opts->maxit;
+  P.flexible = (opts->mixed == 0 && opts->flexible) ? 1 : 0;
   P.n = m->n;
   P.affine = m->d.geom_mode == FE_GEOM_AFFINE;
   P.ncells = m->ncells;
@@ -773,57 +820,56 @@ fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const do
   return FE_OK;
 }
 
-fe_status fe_batch_setup(FeBatch* B, int maxit) {
+fe_status fe_batch_setup(FeBatch* B) {
   const int np = (int)B->hp.size();
   const unsigned g = grid_chunks(B->nvch);
   const Chunk* ch = (const Chunk*)B->d_vch;
-  kb_init_scal<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np, maxit);
-  FE_TRY(fe_batch_norm<double>(B, 0, 6, FIN_INIT_B, 0.0, 0));  // ||G^T b||
+  kb_init_scal<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
+  FE_TRY(fe_batch_norm<double>(B, 0, 6, FIN_INIT_B, 0));  // ||G^T b||
   FE_TRY(launch_apply_batched<double>(B, 0, 1));               // q = A x
   kb_residual<<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch);
   return fe_cuda_check(cudaGetLastError(), "batch setup");
 }
 
-static bool all_done(FeBatch* B, int slot) {
+bool fe_batch_all_done(FeBatch* B, int slot) {
   for (size_t i = 0; i < B->hp.size(); ++i)
     if (B->active[i] && !B->hsc[2 * i + slot].done) return false;
   return true;
 }
 
+fe_status fe_batch_start(FeBatch* B, bool mixed) {
+  FE_TRY(fe_batch_setup(B));
+  if (!mixed) return fe_batch_norm<double>(B, 0, 1, FIN_INIT_R, 0);
+  FE_TRY(fe_batch_norm<double>(B, 0, 1, FIN_NORM, 0));
+  const int np = (int)B->hp.size();
+  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, 0, FIN_OUTER, B->d_partials);  // converged at x0?
+  return fe_cuda_check(cudaGetLastError(), "batch start");
+}
+
 fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts) {
-  const int flex = opts->flexible ? 1 : 0;
   const int batch = 8;
-  FE_TRY(fe_batch_setup(B, opts->maxit));
-  if (opts->mixed != FE_F32) {
-    FE_TRY(fe_batch_norm<double>(B, 0, 1, FIN_INIT_R, opts->rtol, 0));
+  const bool mixed = opts->mixed == FE_F32;
+  FE_TRY(fe_batch_start(B, mixed));
+  if (!mixed) {
     FE_TRY(fe_batch_read(B));
-    while (!all_done(B, 0)) {
-      for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<double>(B, 0, opts->rtol, flex, 0));
+    while (!fe_batch_all_done(B, 0)) {
+      for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<double>(B, 0, 0));
       FE_TRY(fe_batch_read(B));
     }
     return FE_OK;
   }
   // mixed: FP64 FCG, preconditioner = FP32 PCG solve
-  B->inner_rtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 1e-2;
-  FE_TRY(fe_batch_norm<double>(B, 0, 1, FIN_NORM, 0.0, 0));
-  {  // problems already converged at the start
-    const int np = (int)B->hp.size();
-    kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, 0, opts->rtol, FIN_OUTER, 0, B->d_partials);
-    FE_CUDA(cudaGetLastError(), "batch start check");
-  }
-  int first = 1;
   for (;;) {
     FE_TRY(fe_batch_read(B));
-    if (all_done(B, 0)) break;
-    FE_TRY(fe_batch_inner_start(B, opts->maxit));
+    if (fe_batch_all_done(B, 0)) break;
+    FE_TRY(fe_batch_inner_start(B));
     FE_TRY(fe_batch_read(B));
-    while (!all_done(B, 1)) {
-      for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<float>(B, 1, B->inner_rtol, 0, 1));
+    while (!fe_batch_all_done(B, 1)) {
+      for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<float>(B, 1, 1));
       FE_TRY(fe_batch_read(B));
     }
-    FE_TRY(fe_batch_inner_finish(B, first));
-    first = 0;
-    FE_TRY(fe_batch_outer_step(B, opts->rtol));
+    FE_TRY(fe_batch_inner_finish(B));
+    FE_TRY(fe_batch_outer_step(B));
   }
   return FE_OK;
 }
@@ -874,8 +920,9 @@ extern "C" fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes
     FE_CUDA(cudaMemcpyAsync(w->x, x[i], meshes[i]->ncw * sizeof(double), cudaMemcpyDeviceToDevice,
                             B.st),
             "batch copy x");
-    FE_TRY(fe_batch_fill(&B, i, meshes[i], w, b[i]));
+    FE_TRY(fe_batch_fill(&B, i, meshes[i], w, b[i], opts));
   }
+  B.any_flexible = (!mixed && opts->flexible) ? 1 : 0;
   FE_TRY(fe_batch_build(&B));
   FE_TRY(fe_batch_solve(&B, opts));
   FE_TRY(fe_batch_read(&B));

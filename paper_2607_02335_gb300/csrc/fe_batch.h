@@ -20,6 +20,9 @@ struct BProb {
   const float* invmult;
   CgScal* sc;  // [0] outer / FP64, [1] inner FP32
   int chunk0, chunk1;
+  double rtol, irtol;  // outer (or FP64) and inner relative tolerances
+  int maxit;           // iteration cap (inner iterations in total for mixed)
+  int flexible;        // FP64 solves: FCG beta
 };
 
 struct FeBatch {
@@ -39,24 +42,32 @@ struct FeBatch {
   double* d_partials = nullptr;
   size_t cap_partials = 0;
   unsigned long long* d_counter = nullptr;
+  CgScal* d_sc = nullptr;  // gathered scalar records for one readback
+  size_t cap_sc = 0;
   cudaStream_t st = nullptr;
+  bool own_stream = true;
   CgScal* hsc = nullptr;  // pinned, 2 per problem
   size_t cap_hsc = 0;
-  double inner_rtol = 1e-2;
+  int any_flexible = 0;
   ~FeBatch();
 };
 
 fe_status fe_batch_prepare();
 fe_status fe_batch_build(FeBatch* B);
 fe_status fe_batch_read(FeBatch* B);
-fe_status fe_batch_setup(FeBatch* B, int maxit);  // ||G^T b||, r = b - A x
+fe_status fe_batch_setup(FeBatch* B);  // fresh scalars, ||G^T b||, r = b - A x
+bool fe_batch_all_done(FeBatch* B, int slot);
 template <class S>
-fe_status fe_batch_iteration(FeBatch* B, int slot, double rtol, int flexible, int redistribute);
+fe_status fe_batch_iteration(FeBatch* B, int slot, int redistribute);
 template <class S>
-fe_status fe_batch_norm(FeBatch* B, int slot, int src, int mode, double rtol, int redistribute);
-fe_status fe_batch_inner_start(FeBatch* B, int maxit);
-fe_status fe_batch_inner_finish(FeBatch* B, int first);
-fe_status fe_batch_outer_step(FeBatch* B, double rtol);
-fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const double* b);
+fe_status fe_batch_norm(FeBatch* B, int slot, int src, int mode, int redistribute);
+fe_status fe_batch_inner_start(FeBatch* B);
+fe_status fe_batch_inner_finish(FeBatch* B);
+fe_status fe_batch_outer_step(FeBatch* B);
+fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const double* b,
+                        const fe_cg_opts* opts);
+// first steps of a solve for every problem of B: fresh scalars, ||G^T b||, r = b - A x, and the
+// initial preconditioned direction (FP64) or the initial residual check (mixed)
+fe_status fe_batch_start(FeBatch* B, bool mixed);
 // run a full solve of every active problem (FP64 PCG or the mixed FCG scheme)
 fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts);

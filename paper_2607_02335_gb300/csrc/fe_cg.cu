@@ -291,17 +291,15 @@ unsigned grid_for(long long n) {
 // ---- workspace -------------------------------------------------------------------------------
 }  // namespace
 
-static void free_work(CgWork* w) {
+static void free_work(CgWork* w, cudaStream_t st) {
   if (!w) return;
   for (int f = 0; f < 2; ++f) {
     if (w->g64[f]) cudaGraphExecDestroy(w->g64[f]);
     if (w->g32[f]) cudaGraphExecDestroy(w->g32[f]);
   }
-  double* d[] = {w->x, w->r, w->z, w->p, w->q, w->w, w->invdiag64, w->partials, w->hist};
-  for (double* v : d) cudaFree(v);
-  float* f[] = {w->r32, w->z32, w->p32, w->q32, w->w32, w->d32, w->invdiag32, w->invmult};
-  for (float* v : f) cudaFree(v);
-  cudaFree(w->sc);
+  void* bufs[] = {w->x, w->r, w->z, w->p, w->q, w->w, w->invdiag64, w->partials, w->hist,
+                  w->r32, w->z32, w->p32, w->q32, w->w32, w->d32, w->invdiag32, w->invmult, w->sc};
+  for (void* b : bufs) fe_dfree(b, st);
   cudaFreeHost(w->hsc);
   if (w->st) cudaStreamDestroy(w->st);
   delete w;
@@ -317,16 +315,17 @@ fe_status fe_cg_get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
       return FE_ERR_OOM;
     }
     m->cg_work = w;
-    m->cg_free = [](void* p) { free_work(static_cast<CgWork*>(p)); };
+    m->cg_free = [](void* p, cudaStream_t st) { free_work(static_cast<CgWork*>(p), st); };
     const long long n = m->ncw;
     w->n = n;
     FE_CUDA(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking), "cg stream");
     double** d[] = {&w->x, &w->r, &w->z, &w->p, &w->q, &w->w, &w->invdiag64};
-    for (double** v : d) FE_CUDA(cudaMalloc(v, n * sizeof(double)), "cudaMalloc cg vector");
-    FE_CUDA(cudaMalloc(&w->invdiag32, n * sizeof(float)), "cudaMalloc cg vector");
-    FE_CUDA(cudaMalloc(&w->invmult, n * sizeof(float)), "cudaMalloc cg vector");
-    FE_CUDA(cudaMalloc(&w->partials, (size_t)RED_BLOCKS * RED_SLOTS * sizeof(double)), "cudaMalloc");
-    FE_CUDA(cudaMalloc(&w->sc, 2 * sizeof(CgScal)), "cudaMalloc cg scalars");
+    for (double** v : d) FE_TRY(fe_dalloc((void**)v, n * sizeof(double), w->st, "cg vector"));
+    FE_TRY(fe_dalloc((void**)&w->invdiag32, n * sizeof(float), w->st, "cg vector"));
+    FE_TRY(fe_dalloc((void**)&w->invmult, n * sizeof(float), w->st, "cg vector"));
+    FE_TRY(fe_dalloc((void**)&w->partials, (size_t)RED_BLOCKS * RED_SLOTS * sizeof(double), w->st,
+                     "cg partials"));
+    FE_TRY(fe_dalloc((void**)&w->sc, 2 * sizeof(CgScal), w->st, "cg scalars"));
     FE_CUDA(cudaMallocHost(&w->hsc, 2 * sizeof(CgScal)), "cudaMallocHost cg scalars");
     k_invmult<<<grid_for(m->ncells * 32), 256, 0, w->st>>>(w->invmult, m->ncells, m->n, m->d.mx,
                                                            m->d.my, m->d.mz, m->d.dirichlet);
@@ -334,7 +333,7 @@ fe_status fe_cg_get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
   }
   if (mixed && !w->r32) {
     float** f[] = {&w->r32, &w->z32, &w->p32, &w->q32, &w->w32, &w->d32};
-    for (float** v : f) FE_CUDA(cudaMalloc(v, w->n * sizeof(float)), "cudaMalloc cg fp32 vector");
+    for (float** v : f) FE_TRY(fe_dalloc((void**)v, w->n * sizeof(float), w->st, "cg fp32 vector"));
   }
   *out = w;
   return FE_OK;
@@ -583,9 +582,9 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
   const long long n = w->n;
   const int flex = opts->flexible ? 1 : 0;
   if (opts->history && (!w->hist || w->hist_cap < opts->maxit)) {
-    cudaFree(w->hist);
+    fe_dfree(w->hist, w->st);
     w->hist = nullptr;
-    FE_CUDA(cudaMalloc(&w->hist, 3 * (size_t)opts->maxit * sizeof(double)), "cudaMalloc history");
+    FE_TRY(fe_dalloc((void**)&w->hist, 3 * (size_t)opts->maxit * sizeof(double), w->st, "history"));
     w->hist_cap = opts->maxit;
     for (int f = 0; f < 2; ++f)
       if (w->g64[f]) {

@@ -201,7 +201,8 @@ struct fe_mesh {
   int red_len = 0;
   // conjugate-gradient workspace (fe_cg.cu), released through cg_free
   void* cg_work = nullptr;
-  void (*cg_free)(void*) = nullptr;
+  void (*cg_free)(void*, cudaStream_t) = nullptr;
+  cudaStream_t st = nullptr;  // stream of the mesh's own set-up work
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -217,6 +218,18 @@ fe_status fe_cuda_check(cudaError_t e, const char* what);
 #define FE_CUDA(expr, what) FE_TRY(fe_cuda_check((expr), (what)))
 
 fe_status fe_ensure_geometry(const fe_mesh* m, int prec, bool native);  // fe_mesh.cu
+
+// Stream-ordered device memory from a library-owned pool of the current device (fe_mesh.cu).
+// Frees never synchronize the device; the pool keeps freed memory for reuse until fe_pool_trim.
+fe_status fe_dalloc(void** p, size_t bytes, cudaStream_t st, const char* what);
+void fe_dfree(void* p, cudaStream_t st);
+void fe_pool_trim();
+// destroy a mesh without synchronizing the device: frees are ordered on `st`, which must carry
+// (or follow) every use of the mesh
+void fe_mesh_release_async(fe_mesh* m, cudaStream_t st);
+// drop the FP64 copy of the stored geometry once the double-word / FP32 copies and the Jacobi
+// diagonal exist (the server keeps only what its solves read)
+void fe_mesh_drop_geo64(fe_mesh* m, cudaStream_t st);
 
 // apply (fe_apply.cu / fe_apply_*.cu)
 struct ApplyLaunch {

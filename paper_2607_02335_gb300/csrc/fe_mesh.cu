@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "fe_internal.h"
@@ -33,6 +34,53 @@ fe_status fe_cuda_check(cudaError_t e, const char* what) {
 }
 
 extern "C" const char* fe_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------------------------
+// library memory pool (one per device)
+// ---------------------------------------------------------------------------------------------
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static fe_status pool_of_current(cudaMemPool_t* out) {
+  int dev = 0;
+  FE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 64) {
+    fe_set_error("device ordinal %d out of range", dev);
+    return FE_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    FE_CUDA(cudaMemPoolCreate(&g_pool[dev], &props), "cudaMemPoolCreate");
+    unsigned long long thr = ~0ULL;
+    FE_CUDA(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr),
+            "pool release threshold");
+  }
+  *out = g_pool[dev];
+  return FE_OK;
+}
+
+fe_status fe_dalloc(void** p, size_t bytes, cudaStream_t st, const char* what) {
+  *p = nullptr;
+  cudaMemPool_t pool;
+  FE_TRY(pool_of_current(&pool));
+  return fe_cuda_check(cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 16, pool, st), what);
+}
+
+void fe_dfree(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+void fe_pool_trim() {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && g_pool[dev])
+    cudaMemPoolTrimTo(g_pool[dev], 0);
+}
 
 // ---------------------------------------------------------------------------------------------
 // geometry kernel: one CTA per cell, n^3 threads (one per node, then one per Gauss point)
@@ -197,17 +245,24 @@ fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
   fe_mesh* m = const_cast<fe_mesh*>(cm);
   if (m->d.geom_mode != FE_GEOM_STORED) return FE_OK;
   const long long n = m->ncells * FE_GEO_COMPS * m->n3;
+  if ((prec == FE_F64 && !native && !m->geodw) || (prec == FE_F32 && !m->geo32) ||
+      (prec == FE_F64 && native && !m->geo64)) {
+    if (!m->geo64) {
+      fe_set_error("geometry: the FP64 copy was released and the requested copy does not exist");
+      return FE_ERR_INVALID;
+    }
+  }
   if (prec == FE_F64 && !native) {
     if (!m->geodw) {
-      FE_CUDA(cudaMalloc(&m->geodw, n * sizeof(float2)), "cudaMalloc geometry (double-word)");
-      k_split_dw<<<grid_for(n, 256), 256>>>(m->geo64, m->geodw, n);
-      FE_CUDA(cudaDeviceSynchronize(), "geometry double-word split");
+      FE_TRY(fe_dalloc((void**)&m->geodw, n * sizeof(float2), m->st, "geometry (double-word)"));
+      k_split_dw<<<grid_for(n, 256), 256, 0, m->st>>>(m->geo64, m->geodw, n);
+      FE_CUDA(cudaStreamSynchronize(m->st), "geometry double-word split");
     }
   } else if (prec == FE_F32) {
     if (!m->geo32) {
-      FE_CUDA(cudaMalloc(&m->geo32, n * sizeof(float)), "cudaMalloc geometry (fp32)");
-      k_to_f32<<<grid_for(n, 256), 256>>>(m->geo64, m->geo32, n);
-      FE_CUDA(cudaDeviceSynchronize(), "geometry fp32 copy");
+      FE_TRY(fe_dalloc((void**)&m->geo32, n * sizeof(float), m->st, "geometry (fp32)"));
+      k_to_f32<<<grid_for(n, 256), 256, 0, m->st>>>(m->geo64, m->geo32, n);
+      FE_CUDA(cudaStreamSynchronize(m->st), "geometry fp32 copy");
     }
   }
   return FE_OK;
@@ -216,23 +271,22 @@ fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
 // ---------------------------------------------------------------------------------------------
 // mesh object
 // ---------------------------------------------------------------------------------------------
-static void free_mesh(fe_mesh* m) {
+static void free_mesh(fe_mesh* m, cudaStream_t st) {
   if (!m) return;
-  if (m->cg_work && m->cg_free) m->cg_free(m->cg_work);
-  cudaFree(m->geo64);
-  cudaFree(m->geodw);
-  cudaFree(m->geo32);
-  cudaFree(m->xyz64);
-  cudaFree(m->xyzdw);
-  cudaFree(m->xyz32);
-  for (int o = 0; o < 2; ++o) {
-    cudaFree(m->diag64[o]);
-    cudaFree(m->invdiag32[o]);
-    cudaFree(m->invdiag64[o]);
-  }
-  cudaFree(m->invmult64);
-  cudaFree(m->red);
+  if (m->cg_work && m->cg_free) m->cg_free(m->cg_work, st);
+  void* bufs[] = {m->geo64, m->geodw, m->geo32, m->xyz64, m->xyzdw, m->xyz32, m->diag64[0],
+                  m->diag64[1], m->invdiag32[0], m->invdiag32[1], m->invdiag64[0],
+                  m->invdiag64[1], m->invmult64, m->red};
+  for (void* b : bufs) fe_dfree(b, st);
+  if (m->st) cudaStreamDestroy(m->st);
   delete m;
+}
+
+void fe_mesh_release_async(fe_mesh* m, cudaStream_t st) { free_mesh(m, st); }
+
+void fe_mesh_drop_geo64(fe_mesh* m, cudaStream_t st) {
+  fe_dfree(m->geo64, st);
+  m->geo64 = nullptr;
 }
 
 extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh** out) {
@@ -282,6 +336,13 @@ extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh
   m->nu = (long long)(d->mx * m->p + 1) * (d->my * m->p + 1) * (d->mz * m->p + 1);
   fe_host_tables(m->p, &m->tab);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    fe_status cs = fe_cuda_check(cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking), "mesh stream");
+    if (cs != FE_OK) {
+      delete m;
+      return cs;
+    }
+  }
 
   GeoArgs g;
   std::memset(&g, 0, sizeof(g));
@@ -300,11 +361,10 @@ extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh
   }
   fe_status s = FE_OK;
   if (d->geom_mode == FE_GEOM_STORED) {
-    s = fe_cuda_check(cudaMalloc(&m->geo64, m->ncw * FE_GEO_COMPS * sizeof(double)),
-                      "cudaMalloc geometry");
+    s = fe_dalloc((void**)&m->geo64, m->ncw * FE_GEO_COMPS * sizeof(double), st, "geometry");
     g.geo = m->geo64;
   } else if (d->geom_mode == FE_GEOM_RECOMPUTE) {
-    s = fe_cuda_check(cudaMalloc(&m->xyz64, m->ncw * 3 * sizeof(double)), "cudaMalloc coordinates");
+    s = fe_dalloc((void**)&m->xyz64, m->ncw * 3 * sizeof(double), st, "coordinates");
     g.xyz = m->xyz64;
   }
   if (s == FE_OK && d->geom_mode != FE_GEOM_AFFINE) {
@@ -321,7 +381,8 @@ extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh
   if (s == FE_OK) s = fe_cuda_check(cudaStreamSynchronize(st), "geometry synchronize");
   if (s == FE_OK) s = fe_ensure_geometry(m, FE_F64, false);
   if (s != FE_OK) {
-    free_mesh(m);
+    cudaStreamSynchronize(st);
+    free_mesh(m, st);
     return s;
   }
   *out = m;
@@ -331,8 +392,10 @@ extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh
 extern "C" fe_status fe_mesh_destroy(fe_mesh* m) {
   if (!m) return FE_OK;
   cudaSetDevice(m->d.device);
+  cudaDeviceSynchronize();  // the mesh may have been used on any stream
+  free_mesh(m, nullptr);
   cudaDeviceSynchronize();
-  free_mesh(m);
+  fe_pool_trim();
   return FE_OK;
 }
 

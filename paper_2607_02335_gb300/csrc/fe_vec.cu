@@ -294,8 +294,9 @@ __global__ void __launch_bounds__(RED_THREADS)
 fe_status fe_ensure_reduction(const fe_mesh* cm) {
   fe_mesh* m = const_cast<fe_mesh*>(cm);
   if (!m->red) {
-    FE_CUDA(cudaMalloc(&m->red, (size_t)RED_BLOCKS * RED_SLOTS * sizeof(double)),
-            "cudaMalloc reduction partials");
+    FE_TRY(fe_dalloc((void**)&m->red, (size_t)RED_BLOCKS * RED_SLOTS * sizeof(double), m->st,
+                     "reduction partials"));
+    FE_CUDA(cudaStreamSynchronize(m->st), "reduction partials");
     m->red_len = RED_BLOCKS * RED_SLOTS;
   }
   return FE_OK;

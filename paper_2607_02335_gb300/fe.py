@@ -67,6 +67,13 @@ _SIGS = {
     "fe_pairing_noalloc": [_MESH, _i, _vp, _vp, _vp, _vp],
     "fe_cg_solve": [_MESH, _vp, _vp, ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_cg_result), _vp],
     "fe_rhs": [_MESH, _i, _vp, _vp],
+    "fe_serve_create": [ctypes.c_size_t, _i, _i, ctypes.POINTER(_vp)],
+    "fe_serve_submit": [_vp, ctypes.POINTER(fe_mesh_desc), _vp, ctypes.POINTER(fe_cg_opts),
+                        ctypes.POINTER(ctypes.c_longlong)],
+    "fe_serve_poll": [_vp, ctypes.c_longlong, ctypes.POINTER(fe_cg_result), _vp],
+    "fe_serve_stats": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_double)],
+    "fe_serve_destroy": [_vp],
     "fe_cg_solve_batched": [_i, ctypes.POINTER(_MESH), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                             ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_cg_result), _vp],
     "fe_l2_error": [_MESH, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp],
@@ -190,6 +197,46 @@ def fe_cg_solve_batched(meshes, b, x, opts: fe_cg_opts, stream=None):
     if st not in (FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN):
         raise FeError(st, "fe_cg_solve_batched")
     return list(res)
+
+
+def fe_serve_create(mem_budget: int, max_slots: int, device: int = 0) -> int:
+    h = _vp()
+    _check(_lib.fe_serve_create(int(mem_budget), max_slots, device, ctypes.byref(h)), "fe_serve_create")
+    return h.value
+
+
+def fe_serve_submit(server: int, desc: fe_mesh_desc, b_host, opts: fe_cg_opts) -> int:
+    import numpy as np
+    t = ctypes.c_longlong(0)
+    ptr = None
+    if b_host is not None:
+        b_host = np.ascontiguousarray(b_host, dtype=np.float64)
+        ptr = b_host.ctypes.data
+    _check(_lib.fe_serve_submit(server, ctypes.byref(desc), ptr, ctypes.byref(opts), ctypes.byref(t)),
+           "fe_serve_submit")
+    return t.value
+
+
+def fe_serve_poll(server: int, ticket: int, x_host=None):
+    """Returns None while the request is pending, else the fe_cg_result (x copied into the numpy
+    array x_host when given)."""
+    res = fe_cg_result()
+    ptr = None if x_host is None else x_host.ctypes.data
+    st = _lib.fe_serve_poll(server, ticket, ctypes.byref(res), ptr)
+    if st == FE_ERR_BUSY:
+        return None
+    _check(st, "fe_serve_poll")
+    return res
+
+
+def fe_serve_stats(server: int):
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.fe_serve_stats(server, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "fe_serve_stats")
+    return a.value, b.value, c.value
+
+
+def fe_serve_destroy(server: int) -> None:
+    _check(_lib.fe_serve_destroy(server), "fe_serve_destroy")
 
 
 # ---- convenience object ---------------------------------------------------------------------------
