@@ -44,6 +44,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="tiny sizes (plumbing check only)")
+    ap.add_argument("--batch-count", type=int, default=256, help="problems of the batched solve")
+    ap.add_argument("--serve-requests", type=int, default=300, help="requests per serving run")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate (1/s)")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-cap-s", type=float, default=45.0, help="wall-time cap per serving run")
+    ap.add_argument("--no-extras", action="store_true", help="operator sweep only")
     ap.add_argument("--profile-case", default=None,
                     help="p,m,op: only run K+W applies of one case (for profiler captures)")
     return ap.parse_args()
@@ -324,7 +331,22 @@ def run_ours(args, rank, world):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_value = units_per_step * world / e2e_s / 1e9
 
-    solve = None if args.small else mixed_vs_fp64_solve(fe, torch)
+    extras = {}
+    if not args.small and not args.no_extras:
+        for gm, *_ in meshes:
+            gm.close()
+        del cases, meshes
+        torch.cuda.empty_cache()
+        extras["solve_mixed_vs_fp64"] = mixed_vs_fp64_solve(fe, torch)
+        extras["batched"] = batched_solve(fe, torch, count=args.batch_count)
+        extras["serving"] = {
+            "workload": f"Poisson arrivals {args.serve_rate}/s, {args.serve_requests} requests, m "
+                        f"lognormal (median 16, sigma 0.5, max 64), p in {{2,3,7}}, amp {AMP}, sine "
+                        f"load, rtol 1e-10, budget {args.serve_budget_gb} GB, {args.serve_slots} slots",
+            "fp64": serving_run(fe, False, args.serve_requests, args.serve_rate, args.serve_budget_gb,
+                                args.serve_slots, args.serve_cap_s),
+            "mixed": serving_run(fe, True, args.serve_requests, args.serve_rate, args.serve_budget_gb,
+                                 args.serve_slots, args.serve_cap_s)}
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -343,7 +365,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
-        "solve_mixed_vs_fp64": solve,
+        **extras,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -389,6 +411,91 @@ def mixed_vs_fp64_solve(fe, torch, m=64, p=3, rtol=1e-10):
         out[name]["speedup_over_fp64"] = round(out["fp64"]["seconds"] / out[name]["seconds"], 3)
     gm.close()
     return out
+
+
+def batched_solve(fe, torch, count=256, seed=0, rtol=1e-10):
+    """256 independent Poisson problems (m ~ U{4..32}, p ~ U{2,3,5,7}, deformation amplitude
+    ~ U[0, 0.15], random dual right-hand side per cell-wise entry, seed 0), solved together by the
+    batched engine with the mixed scheme (FP32 operator inside FP64-refined FCG) to rtol 1e-10."""
+    from paper_2607_02335_gb300 import synth as S
+
+    probs = S.batched_problems(count, seed=seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    t0 = time.perf_counter()
+    meshes, bs = [], []
+    for pr in probs:
+        gm = fe.Mesh(pr["m"], pr["p"], deform_amp=pr["amp"], dirichlet=True)
+        meshes.append(gm)
+        bs.append(torch.rand(gm.cellwise_len, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    ncw = sum(g.cellwise_len for g in meshes)
+    opts = fe.fe_cg_opts(rtol, 20000, fe.FE_F32, 1, 1e-2, None)
+    xs = [torch.zeros_like(b) for b in bs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = fe.fe_cg_solve_batched([g.handle for g in meshes], bs, xs, opts)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    ok = sum(r.status == fe.FE_OK for r in res)
+    # a sample of problems solved alone through the same engine: the mix must not change them
+    sample = sorted(range(count), key=lambda i: meshes[i].cellwise_len)[: min(6, count)]
+    diffs = []
+    for i in sample:
+        xa = torch.zeros_like(bs[i])
+        fe.fe_cg_solve_batched([meshes[i].handle], [bs[i]], [xa], opts)
+        diffs.append(float((xa - xs[i]).abs().max()))
+    out = {"workload": f"{count} problems, m~U{{4..32}}, p~U{{2,3,5,7}}, amp~U[0,0.15], random dual "
+                       f"rhs, FP64 FCG + FP32 PCG preconditioner, rtol {rtol}, one persistent apply "
+                       f"launch per iteration",
+           "cellwise_dofs_total": ncw, "setup_seconds": round(t_setup, 3),
+           "solve_seconds": round(t_solve, 3), "solves_per_s": round(count / t_solve, 3),
+           "converged": ok, "max_rel_res": max(r.rel_res for r in res),
+           "inner_iters_max": max(r.iters for r in res), "outer_iters_max": max(r.outer_iters for r in res),
+           "alone_vs_mix_max_abs_diff": max(diffs) if diffs else None,
+           "alone_vs_mix_sample": len(sample)}
+    for g in meshes:
+        g.close()
+    del xs, bs
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_run(fe, mixed, n_req, rate, budget_gb, slots, cap_s, seed=0):
+    """Poisson arrivals at `rate`/s of Jacobi-CG solves (m lognormal, median 16, max 64; p in
+    {2,3,7}; manufactured sine load; rtol 1e-10) submitted to one server; returns its stats."""
+    from paper_2607_02335_gb300 import synth as S
+
+    arrivals = S.poisson_arrivals(rate, n_req, seed=seed)
+    reqs = S.serving_requests(n_req, seed=seed)
+    opts = fe.fe_cg_opts(1e-10, 20000, fe.FE_F32 if mixed else 0, 1 if mixed else 0, 1e-2, None)
+    srv = fe.fe_serve_create(int(budget_gb * 2 ** 30), slots, 0)
+    pending, done, submitted = {}, {}, 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while submitted < n_req and arrivals[submitted] <= now:
+            rq = reqs[submitted]
+            d = fe.fe_mesh_desc(rq["m"], rq["m"], rq["m"], rq["p"], AMP, fe.FE_GEOM_STORED, 1, 0)
+            pending[fe.fe_serve_submit(srv, d, None, opts)] = submitted
+            submitted += 1
+        for t in list(pending):
+            r = fe.fe_serve_poll(srv, t)
+            if r is not None:
+                done[pending.pop(t)] = r
+        if submitted == n_req and not pending:
+            break
+        if now > cap_s:
+            break
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    p50, p99, sps = fe.fe_serve_stats(srv)
+    fe.fe_serve_destroy(srv)
+    return {"submitted": submitted, "completed": len(done), "wall_s": round(wall, 3),
+            "solves_per_s": round(sps, 3), "p50_s": round(p50, 4), "p99_s": round(p99, 4),
+            "converged": sum(r.status == fe.FE_OK for r in done.values()),
+            "max_rel_res": max((r.rel_res for r in done.values()), default=None)}
 
 
 def run_profile_case(args):

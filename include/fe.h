@@ -211,7 +211,8 @@ fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes, const dou
  *    the solution (cellwise_len doubles) and forgets the ticket.  Non-blocking.
  *  fe_serve_stats: p50 and p99 of (completion - submission) over completed requests, in seconds,
  *    and completed solves per second since the first submission.
- *  fe_serve_destroy: finishes every admitted and queued request, then frees the server. */
+ *  fe_serve_destroy: drops requests still waiting for admission, finishes the admitted ones,
+ *    then frees the server. */
 fe_status fe_serve_create(size_t mem_budget, int max_slots, int device, fe_server** out);
 fe_status fe_serve_submit(fe_server* server, const fe_mesh_desc* desc, const double* b_host,
                           const fe_cg_opts* opts, long long* ticket);

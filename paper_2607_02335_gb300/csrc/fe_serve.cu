@@ -410,6 +410,11 @@ extern "C" fe_status fe_serve_destroy(fe_server* S) {
   if (!S) return FE_OK;
   {
     std::lock_guard<std::mutex> lock(S->mu);
+    for (Request* r : S->queue) {  // never admitted: dropped
+      S->reqs.erase(r->ticket);
+      delete r;
+    }
+    S->queue.clear();
     S->stop = true;
     S->cv.notify_all();
   }
