@@ -19,6 +19,8 @@ LIB = os.path.join(PKG, "libfe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# optional extra nvcc flags (e.g. -D switches for experiments); they get their own object folder
+EXTRA = os.environ.get("FE_NVCC_EXTRA", "").split()
 
 
 def _headers():
@@ -29,7 +31,7 @@ def _headers():
 def _compile(src: str, obj: str, hdr_mtime: float, verbose: bool) -> str:
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_mtime):
         return obj
-    cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+    cmd = [NVCC, *ARCH, *FLAGS, *EXTRA, "-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -39,20 +41,29 @@ def _compile(src: str, obj: str, hdr_mtime: float, verbose: bool) -> str:
 
 
 def build(verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD
+    if EXTRA:
+        import hashlib
+        build_dir = os.path.join(BUILD, hashlib.sha1(" ".join(EXTRA).encode()).hexdigest()[:10])
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdr = max(os.path.getmtime(h) for h in _headers())
-    objs = [os.path.join(BUILD, os.path.basename(s) + ".o") for s in srcs]
+    objs = [os.path.join(build_dir, os.path.basename(s) + ".o") for s in srcs]
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         list(ex.map(lambda so: _compile(so[0], so[1], hdr, verbose), zip(srcs, objs)))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+    stamp = os.path.join(build_dir, "flags")
+    same_flags = os.path.exists(stamp) and open(stamp).read() == " ".join(EXTRA)
+    if (not same_flags or not os.path.exists(LIB)
+            or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs)):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+        with open(os.path.join(BUILD, "flags"), "w") as f:
+            f.write(" ".join(EXTRA))
     return LIB
 
 

@@ -56,19 +56,15 @@ struct Sm<float> {
   static constexpr int BYTES = 4;
 };
 template <>
-struct Sm<dw> {
-  float* h;
-  float* l;
-  __device__ __forceinline__ Sm(unsigned char* base, int narr, int arr, int tile) {
-    float* f = reinterpret_cast<float*>(base);
-    h = f + (size_t)arr * tile;
-    l = f + (size_t)(narr + arr) * tile;
+struct Sm<dw> {  // hi and lo interleaved: one 64-bit shared-memory access per value
+  float2* p;
+  __device__ __forceinline__ Sm(unsigned char* base, int, int arr, int tile)
+      : p(reinterpret_cast<float2*>(base) + (size_t)arr * tile) {}
+  __device__ __forceinline__ dw get(int e) const {
+    const float2 v = p[e];
+    return {v.x, v.y};
   }
-  __device__ __forceinline__ dw get(int e) const { return {h[e], l[e]}; }
-  __device__ __forceinline__ void put(int e, dw v) const {
-    h[e] = v.h;
-    l[e] = v.l;
-  }
+  __device__ __forceinline__ void put(int e, dw v) const { p[e] = make_float2(v.h, v.l); }
   static constexpr int BYTES = 8;
 };
 
@@ -80,7 +76,7 @@ __device__ __forceinline__ void mv(const V (&M)[N][N], const V (&in)[N], V (&out
     V acc = NT<V>::zero();
 #pragma unroll
     for (int r = 0; r < N; ++r) acc = NT<V>::mac(acc, M[q][r], in[r]);
-    out[q] = NT<V>::fin(acc);
+    out[q] = NT<V>::keep(acc);
   }
 }
 // out[r] = sum_q M[q][r] in[q]
@@ -91,7 +87,7 @@ __device__ __forceinline__ void mtv(const V (&M)[N][N], const V (&in)[N], V (&ou
     V acc = NT<V>::zero();
 #pragma unroll
     for (int q = 0; q < N; ++q) acc = NT<V>::mac(acc, M[q][r], in[q]);
-    out[r] = NT<V>::fin(acc);
+    out[r] = NT<V>::keep(acc);
   }
 }
 
@@ -186,6 +182,19 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
     V v = active ? T::load_stream(a.x + gbase + k * N2 + lt) : T::zero();
     u[k] = masked(k) ? T::zero() : v;
   }
+  // low degrees: issue the metric loads now so that their latency hides behind the sweeps
+#ifndef FE_PREFETCH_MAXN
+#define FE_PREFETCH_MAXN 3
+#endif
+  constexpr bool PREF = (OP == FE_LAPLACE) && (GEOM == GEOM_STORED_K) && (N <= FE_PREFETCH_MAXN);
+  V gpre[PREF ? 6 * N : 1];
+  if constexpr (PREF) {
+    const typename NT<V>::GV* g0 = a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + lt;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) gpre[c * N + k] = active ? T::geo(g0 + c * N3 + k * N2) : T::zero();
+  }
   mv<N, V>(tab.V_, u, w);
 #pragma unroll
   for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
@@ -232,21 +241,30 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
         s2.put(e, gy);
         u[k] = gz;
       } else {
-        const typename NT<V>::GV* gp = a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + k * N2 + lt;
-        if (active) {
-          gxx = T::geo(gp + 0 * N3);
-          gyy = T::geo(gp + 1 * N3);
-          gzz = T::geo(gp + 2 * N3);
-          gxy = T::geo(gp + 3 * N3);
-          gxz = T::geo(gp + 4 * N3);
-          gyz = T::geo(gp + 5 * N3);
+        if constexpr (PREF) {
+          gxx = gpre[0 * N + k];
+          gyy = gpre[1 * N + k];
+          gzz = gpre[2 * N + k];
+          gxy = gpre[3 * N + k];
+          gxz = gpre[4 * N + k];
+          gyz = gpre[5 * N + k];
         } else {
-          gxx = gyy = gzz = gxy = gxz = gyz = T::zero();
+          const typename NT<V>::GV* gp = a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + k * N2 + lt;
+          if (active) {
+            gxx = T::geo(gp + 0 * N3);
+            gyy = T::geo(gp + 1 * N3);
+            gzz = T::geo(gp + 2 * N3);
+            gxy = T::geo(gp + 3 * N3);
+            gxz = T::geo(gp + 4 * N3);
+            gyz = T::geo(gp + 5 * N3);
+          } else {
+            gxx = gyy = gzz = gxy = gxz = gyz = T::zero();
+          }
         }
         V gx = T::zero(), gy = T::zero(), gz = T::zero();
-        gx = T::fin(T::mac(T::mac(T::mac(gx, gxx, dx), gxy, dy), gxz, dz));
-        gy = T::fin(T::mac(T::mac(T::mac(gy, gxy, dx), gyy, dy), gyz, dz));
-        gz = T::fin(T::mac(T::mac(T::mac(gz, gxz, dx), gyz, dy), gzz, dz));
+        gx = T::keep(T::mac(T::mac(T::mac(gx, gxx, dx), gxy, dy), gxz, dz));
+        gy = T::keep(T::mac(T::mac(T::mac(gy, gxy, dx), gyy, dy), gyz, dz));
+        gz = T::keep(T::mac(T::mac(T::mac(gz, gxz, dx), gyz, dy), gzz, dz));
         s1.put(e, gx);
         s2.put(e, gy);
         u[k] = gz;

@@ -1,5 +1,6 @@
 // fe_apply_launch.cuh -- host launchers of the apply kernels for one arithmetic V.
 #pragma once
+#include <cmath>
 #include <cstring>
 
 #include "fe_apply_kernel.cuh"

@@ -102,6 +102,7 @@ struct NT<double> {
   __device__ static __forceinline__ double zero() { return 0.0; }
   __device__ static __forceinline__ double mac(double a, double c, double v) { return fma(c, v, a); }
   __device__ static __forceinline__ double fin(double a) { return a; }
+  __device__ static __forceinline__ double keep(double a) { return a; }
   __device__ static __forceinline__ double mul(double a, double b) { return a * b; }
   __device__ static __forceinline__ double add(double a, double b) { return a + b; }
   __device__ static __forceinline__ double neg(double a) { return -a; }
@@ -118,6 +119,7 @@ struct NT<float> {
   __device__ static __forceinline__ float zero() { return 0.0f; }
   __device__ static __forceinline__ float mac(float a, float c, float v) { return fmaf(c, v, a); }
   __device__ static __forceinline__ float fin(float a) { return a; }
+  __device__ static __forceinline__ float keep(float a) { return a; }
   __device__ static __forceinline__ float mul(float a, float b) { return a * b; }
   __device__ static __forceinline__ float add(float a, float b) { return a + b; }
   __device__ static __forceinline__ float neg(float a) { return -a; }
@@ -134,6 +136,9 @@ struct NT<dw> {
   __device__ static __forceinline__ dw zero() { return {0.0f, 0.0f}; }
   __device__ static __forceinline__ dw mac(dw a, dw c, dw v) { return dw_mac(a, c, v); }
   __device__ static __forceinline__ dw fin(dw a) { return dw_norm(a); }
+  // intermediate results of the sweeps stay unnormalised: |lo| stays below a few ulp(hi), and the
+  // next products use lo only in FP32 cross terms (relative effect ~2^-45)
+  __device__ static __forceinline__ dw keep(dw a) { return a; }
   __device__ static __forceinline__ dw mul(dw a, dw b) { return dw_mul(a, b); }
   __device__ static __forceinline__ dw add(dw a, dw b) { return dw_add(a, b); }
   __device__ static __forceinline__ dw neg(dw a) { return {-a.h, -a.l}; }
