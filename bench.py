@@ -337,6 +337,8 @@ def run_ours(args, rank, world):
             gm.close()
         del cases, meshes
         torch.cuda.empty_cache()
+        extras["geometry_recompute"] = recompute_geometry(fe, torch, sweep, per_case, flush, stream,
+                                                          reps)
         extras["solve_mixed_vs_fp64"] = mixed_vs_fp64_solve(fe, torch)
         extras["batched"] = batched_solve(fe, torch, count=args.batch_count)
         extras["serving"] = {
@@ -380,6 +382,49 @@ def run_ours(args, rank, world):
                                 "kind": "oracle", "sample": smp.describe()}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def recompute_geometry(fe, torch, sweep, per_case, flush, stream, reps):
+    """The operator sweep with the metric recomputed from cell-wise nodal coordinates (double-word
+    coordinates, 24 B per cell-wise DoF, instead of the stored metric): volumetric and assembled
+    time per case, next to the stored-metric time of the same case."""
+    from paper_2607_02335_gb300 import synth as S
+
+    stored = {(c["degree"], c["op"]): c for c in per_case}
+    out = []
+    for p, m in sweep:
+        gm = fe.Mesh(m, p, deform_amp=AMP, geom_mode=fe.FE_GEOM_RECOMPUTE)
+        x = gm.gather(S.primal_unique(m, p, seed=0))
+        y = gm.empty(fe.FE_F64)
+        for op in (fe.FE_LAPLACE, fe.FE_MASS):
+            name = "laplace" if op == fe.FE_LAPLACE else "mass"
+            res = {}
+            for flags, key in ((fe.FE_ASSEMBLE, "assembled_ms"), (0, "volumetric_ms")):
+                fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, flags, stream)
+                tot = 0.0
+                for _ in range(reps):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, flags, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    tot += e0.elapsed_time(e1)
+                res[key] = tot / reps
+            ncw = gm.cellwise_len
+            st = stored[(p, name)]
+            out.append({
+                "op": name, "degree": p, "cells": f"{m}^3",
+                "assembled_ms": round(res["assembled_ms"], 4),
+                "volumetric_ms": round(res["volumetric_ms"], 4),
+                "gdofs_unique_assembled": round(gm.unique_dofs / (res["assembled_ms"] * 1e-3) / 1e9, 3),
+                "volumetric_hbm_bytes_per_cellwise_dof": 16 + 24,
+                "stored_volumetric_ms": st["volumetric_ms"],
+                "time_vs_stored": round(res["volumetric_ms"] / st["volumetric_ms"], 3)})
+        del x, y
+        gm.close()
+    return out
 
 
 def mixed_vs_fp64_solve(fe, torch, m=64, p=3, rtol=1e-10):

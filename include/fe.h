@@ -58,7 +58,11 @@ typedef enum { FE_F64 = 0, FE_F32 = 1, FE_BF16_F32ACC = 2, FE_F16_F32ACC = 3 } f
 /* Geometry representation (Sec. 2.3 and Sec. 5.3: "per-quadrature-point Jacobians"):
  *  STORED    -- w_q detJ J^{-1}J^{-T} (6 symmetric entries, Laplace) and w_q detJ (mass) per
  *               quadrature point, precomputed by fe_mesh_create;
- *  RECOMPUTE -- only the cell-wise nodal coordinates are stored; J is formed on the fly;
+ *  RECOMPUTE -- only the cell-wise nodal coordinates are stored (3 values per cell node, as
+ *               offsets from the cell's first node); each apply forms J and the metric from them,
+ *               chunk by chunk into an L2-sized library scratch of the mesh, so applies on one
+ *               RECOMPUTE mesh must not run concurrently on different streams.  Not accepted by
+ *               fe_cg_solve_batched and the request server;
  *  AFFINE    -- undeformed Cartesian mesh (deform_amp must be 0): one diagonal J for all cells,
  *               the paper's "scalar h" setting. */
 enum { FE_GEOM_STORED = 0, FE_GEOM_RECOMPUTE = 1, FE_GEOM_AFFINE = 2 };

@@ -120,8 +120,10 @@ template <int N, class V>
 struct CellArgs {
   const typename NT<V>::SV* x;
   typename NT<V>::SV* y;
-  const typename NT<V>::GV* geo;  // [cell][7][N3]: w detJ J^-1 J^-T (xx,yy,zz,xy,xz,yz), w detJ
-  long long ncells;
+  const typename NT<V>::GV* geo;  // [cell - geo_cell0][7][N3]: w detJ J^-1 J^-T (xx,..,yz), w detJ
+  long long ncells;               // cells at or above this index are not touched
+  long long cell_base;            // first cell of the launch (k_apply)
+  long long geo_cell0;            // cell whose metric is geo[0] (a chunk's scratch in recompute mode)
   int mx, my, mz;
   int dirichlet;
   V aff[4];  // affine mode: detJ/h_x^2, detJ/h_y^2, detJ/h_z^2, detJ
@@ -189,7 +191,7 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   constexpr bool PREF = (OP == FE_LAPLACE) && (GEOM == GEOM_STORED_K) && (N <= FE_PREFETCH_MAXN);
   V gpre[PREF ? 6 * N : 1];
   if constexpr (PREF) {
-    const typename NT<V>::GV* g0 = a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + lt;
+    const typename NT<V>::GV* g0 = a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + lt;
 #pragma unroll
     for (int k = 0; k < N; ++k)
 #pragma unroll
@@ -249,7 +251,8 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
           gxz = gpre[4 * N + k];
           gyz = gpre[5 * N + k];
         } else {
-          const typename NT<V>::GV* gp = a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + k * N2 + lt;
+          const typename NT<V>::GV* gp =
+              a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + k * N2 + lt;
           if (active) {
             gxx = T::geo(gp + 0 * N3);
             gyy = T::geo(gp + 1 * N3);
@@ -290,7 +293,8 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
       if constexpr (GEOM == GEOM_AFFINE_K) {
         jw = T::mul(T::mul(T::mul(tab.W_[la], tab.W_[lb]), tab.W_[k]), a.aff[3]);
       } else {
-        jw = active ? T::geo(a.geo + (size_t)cell * (FE_GEO_COMPS * N3) + 6 * N3 + k * N2 + lt)
+        jw = active ? T::geo(a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + 6 * N3 +
+                             k * N2 + lt)
                     : T::zero();
       }
       u[k] = T::mul(jw, uq);
@@ -321,7 +325,8 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
     k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.skip && *(volatile const int*)a.skip) return;  // uniform over the grid
-  apply_cells<N, V, OP, GEOM>(a.c, a.tab, (long long)blockIdx.x * Cfg<N>::CPB, smraw, Cfg<N>::TILE);
+  apply_cells<N, V, OP, GEOM>(a.c, a.tab, a.c.cell_base + (long long)blockIdx.x * Cfg<N>::CPB, smraw,
+                              Cfg<N>::TILE);
 }
 
 template <int N, class V>

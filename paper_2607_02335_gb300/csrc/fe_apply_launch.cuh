@@ -3,7 +3,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "fe_apply_kernel.cuh"
+#include "fe_recompute.cuh"
 
 template <class V>
 V fe_cast(double v);
@@ -41,13 +41,49 @@ static fe_status launch_one(const ApplyArgs<N, V>& a, cudaStream_t st) {
             "apply smem attribute");
     attr_done = true;
   }
-  const long long blocks = (a.c.ncells + C::CPB - 1) / C::CPB;
+  const long long blocks = (a.c.ncells - a.c.cell_base + C::CPB - 1) / C::CPB;
   if (blocks > 0) kern<<<(unsigned)blocks, C::THREADS, smem, st>>>(a);
   return fe_cuda_check(cudaGetLastError(), "apply kernel launch");
 }
 
+// Recompute mode: per chunk of cells, the metric into the L2-sized scratch, then the stored-metric
+// apply on the chunk.
+template <int N, class V, int OP>
+static fe_status launch_recompute(ApplyArgs<N, V> a, const ApplyLaunch& L,
+                                  const typename NT<V>::GV* xyz, typename NT<V>::GV* scratch) {
+  const fe_mesh* m = L.m;
+  if (!xyz || !scratch) {
+    fe_set_error("apply: recompute-mode buffers missing for this arithmetic");
+    return FE_ERR_INVALID;
+  }
+  using G = GeoCfg<N>;
+  const long long chunk = fe_rc_chunk_cells(N, m->ncells, sizeof(typename NT<V>::GV));
+  RecomputeArgs<N, V> r;
+  std::memset(&r, 0, sizeof(r));
+  r.xyz = xyz;
+  r.geo = scratch;
+  r.skip = L.skip;
+  r.tab = a.tab;
+  a.c.geo = scratch;
+  for (long long c0 = 0; c0 < m->ncells; c0 += chunk) {
+    const long long c1 = c0 + chunk < m->ncells ? c0 + chunk : m->ncells;
+    r.cell0 = c0;
+    r.cell_end = c1;
+    const long long gblocks = (c1 - c0 + G::CPB - 1) / G::CPB;
+    k_recompute<N, V, OP>
+        <<<(unsigned)gblocks, G::THREADS, recompute_smem_bytes<N, V>(), L.st>>>(r);
+    FE_CUDA(cudaGetLastError(), "recompute kernel launch");
+    a.c.cell_base = c0;
+    a.c.geo_cell0 = c0;
+    a.c.ncells = c1;
+    FE_TRY((launch_one<N, V, OP, GEOM_STORED_K>(a, L.st)));
+  }
+  return FE_OK;
+}
+
 template <int N, class V>
-static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* geo) {
+static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* geo,
+                                const typename NT<V>::GV* xyz, typename NT<V>::GV* scratch) {
   const fe_mesh* m = L.m;
   ApplyArgs<N, V> a;
   std::memset(&a, 0, sizeof(a));
@@ -66,6 +102,9 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
   a.c.aff[2] = fe_cast<V>(det / (hz * hz));
   a.c.aff[3] = fe_cast<V>(det);
   a.tab = make_tab<N, V>(m->tab);
+  if (m->d.geom_mode == FE_GEOM_RECOMPUTE)
+    return L.op == FE_LAPLACE ? launch_recompute<N, V, FE_LAPLACE>(a, L, xyz, scratch)
+                              : launch_recompute<N, V, FE_MASS>(a, L, xyz, scratch);
   const bool affine = m->d.geom_mode == FE_GEOM_AFFINE;
   if (L.op == FE_LAPLACE)
     return affine ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K>(a, L.st)
@@ -75,15 +114,16 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
 }
 
 template <class V>
-static fe_status launch_apply_v(const ApplyLaunch& L, const typename NT<V>::GV* geo) {
+static fe_status launch_apply_v(const ApplyLaunch& L, const typename NT<V>::GV* geo,
+                                const typename NT<V>::GV* xyz, typename NT<V>::GV* scratch) {
   switch (L.m->n) {
-    case 2: return launch_apply_n<2, V>(L, geo);
-    case 3: return launch_apply_n<3, V>(L, geo);
-    case 4: return launch_apply_n<4, V>(L, geo);
-    case 5: return launch_apply_n<5, V>(L, geo);
-    case 6: return launch_apply_n<6, V>(L, geo);
-    case 7: return launch_apply_n<7, V>(L, geo);
-    case 8: return launch_apply_n<8, V>(L, geo);
+    case 2: return launch_apply_n<2, V>(L, geo, xyz, scratch);
+    case 3: return launch_apply_n<3, V>(L, geo, xyz, scratch);
+    case 4: return launch_apply_n<4, V>(L, geo, xyz, scratch);
+    case 5: return launch_apply_n<5, V>(L, geo, xyz, scratch);
+    case 6: return launch_apply_n<6, V>(L, geo, xyz, scratch);
+    case 7: return launch_apply_n<7, V>(L, geo, xyz, scratch);
+    case 8: return launch_apply_n<8, V>(L, geo, xyz, scratch);
   }
   fe_set_error("apply: unsupported n = %d", L.m->n);
   return FE_ERR_INVALID;

@@ -121,6 +121,8 @@ __device__ __forceinline__ void apply_item(const BProb& P, int prec, int src, lo
     a.geo = reinterpret_cast<const typename NT<V>::GV*>(P.geo32);
   }
   a.ncells = P.ncells;
+  a.cell_base = 0;
+  a.geo_cell0 = 0;
   a.mx = P.mx;
   a.my = P.my;
   a.mz = P.mz;

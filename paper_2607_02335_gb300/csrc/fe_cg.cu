@@ -565,10 +565,6 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
                  opts->rtol, opts->mixed);
     return FE_ERR_INVALID;
   }
-  if (m->d.geom_mode == FE_GEOM_RECOMPUTE) {
-    fe_set_error("fe_cg_solve: needs stored or affine geometry");
-    return FE_ERR_INVALID;
-  }
   std::memset(res, 0, sizeof(*res));
   FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
   const bool mixed = opts->mixed == FE_F32;

@@ -105,6 +105,8 @@ struct NT<double> {
   __device__ static __forceinline__ double keep(double a) { return a; }
   __device__ static __forceinline__ double mul(double a, double b) { return a * b; }
   __device__ static __forceinline__ double add(double a, double b) { return a + b; }
+  __device__ static __forceinline__ double sub(double a, double b) { return a - b; }
+  __device__ static __forceinline__ double recip(double a) { return 1.0 / a; }
   __device__ static __forceinline__ double neg(double a) { return -a; }
   __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ double load_stream(const double* p) { return __ldcs(p); }
@@ -122,6 +124,8 @@ struct NT<float> {
   __device__ static __forceinline__ float keep(float a) { return a; }
   __device__ static __forceinline__ float mul(float a, float b) { return a * b; }
   __device__ static __forceinline__ float add(float a, float b) { return a + b; }
+  __device__ static __forceinline__ float sub(float a, float b) { return a - b; }
+  __device__ static __forceinline__ float recip(float a) { return 1.0f / a; }
   __device__ static __forceinline__ float neg(float a) { return -a; }
   __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float load_stream(const float* p) { return __ldcs(p); }
@@ -141,6 +145,13 @@ struct NT<dw> {
   __device__ static __forceinline__ dw keep(dw a) { return a; }
   __device__ static __forceinline__ dw mul(dw a, dw b) { return dw_mul(a, b); }
   __device__ static __forceinline__ dw add(dw a, dw b) { return dw_add(a, b); }
+  __device__ static __forceinline__ dw sub(dw a, dw b) { return dw_add(a, {-b.h, -b.l}); }
+  // one Newton step from the float reciprocal: r = r0 + r0 (1 - a r0)
+  __device__ static __forceinline__ dw recip(dw a) {
+    const float r0 = __frcp_rn(a.h);
+    const dw e = dw_add({1.0f, 0.0f}, dw_mul(a, {-r0, 0.0f}));
+    return dw_add({r0, 0.0f}, dw_mul({r0, 0.0f}, e));
+  }
   __device__ static __forceinline__ dw neg(dw a) { return {-a.h, -a.l}; }
   __device__ static __forceinline__ dw load(const double* p) { return dw_from_double(__ldg(p)); }
   __device__ static __forceinline__ dw load_stream(const double* p) { return dw_from_double(__ldcs(p)); }
@@ -182,6 +193,19 @@ Tab1D<N, V> make_tab(const HostTab& h);
 // ---------------------------------------------------------------------------------------------
 #define FE_GEO_COMPS 7  // xx, yy, zz, xy, xz, yz of w detJ J^{-1}J^{-T}, then w detJ
 
+// Recompute mode: cells per chunk of the metric scratch (about FE_RC_CHUNK_BYTES, a multiple of the
+// apply's cells per CTA), for a metric value of gv_bytes bytes.
+#ifndef FE_RC_CHUNK_BYTES
+#define FE_RC_CHUNK_BYTES (48LL << 20)
+#endif
+inline long long fe_rc_chunk_cells(int n, long long ncells, size_t gv_bytes) {
+  const long long per_cell = (long long)FE_GEO_COMPS * n * n * n * (long long)gv_bytes;
+  const long long cpb = 256 / (n * n);
+  long long c = FE_RC_CHUNK_BYTES / per_cell;
+  c = c >= cpb ? c / cpb * cpb : (c > 0 ? c : 1);
+  return c < ncells ? c : (ncells > 0 ? ncells : 1);
+}
+
 struct fe_mesh {
   fe_mesh_desc d;
   int p, n, n3;
@@ -191,10 +215,13 @@ struct fe_mesh {
   double* geo64 = nullptr;
   float2* geodw = nullptr;
   float* geo32 = nullptr;
-  // recompute mode: nodal coordinates [cell][3][n3]
+  // recompute mode: nodal coordinates [cell][3][n3], and an L2-sized scratch for the metric of one
+  // chunk of cells (per arithmetic: 0 double-word, 1 FP64, 2 FP32)
   double* xyz64 = nullptr;
   float2* xyzdw = nullptr;
   float* xyz32 = nullptr;
+  void* rc_scratch[3] = {nullptr, nullptr, nullptr};
+  long long rc_cells = 0;  // cells per chunk
   // Jacobi diagonal caches (cell-wise, continuous), per operator
   double* diag64[2] = {nullptr, nullptr};
   float* invdiag32[2] = {nullptr, nullptr};

@@ -123,11 +123,13 @@ __global__ void __launch_bounds__(N* N* N) k_geometry(const __grid_constant__ Ge
     sX[0 * N3 + t] = X0 + s;
     sX[1 * N3 + t] = X1 + s;
     sX[2 * N3 + t] = X2 + s;
-    if (a.xyz) {
+    if (a.xyz) {  // offsets from the cell's first node (the corner, GLL node 0 is 0)
+      const double C0 = (double)cx / a.mx, C1 = (double)cy / a.my, C2 = (double)cz / a.mz;
+      const double sc = a.amp * sinpi(C0) * sinpi(C1) * sinpi(C2);
       double* out = a.xyz + (size_t)cell * 3 * N3;
-      out[0 * N3 + t] = X0 + s;
-      out[1 * N3 + t] = X1 + s;
-      out[2 * N3 + t] = X2 + s;
+      out[0 * N3 + t] = (X0 + s) - (C0 + sc);
+      out[1 * N3 + t] = (X1 + s) - (C1 + sc);
+      out[2 * N3 + t] = (X2 + s) - (C2 + sc);
     }
   }
   if (!a.geo) return;
@@ -243,6 +245,28 @@ static unsigned grid_for(long long n, int threads) {
 
 fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
   fe_mesh* m = const_cast<fe_mesh*>(cm);
+  if (m->d.geom_mode == FE_GEOM_RECOMPUTE) {
+    // coordinate copy in the arithmetic of the call, and that arithmetic's metric scratch
+    const long long n = m->ncells * 3 * m->n3;
+    const int idx = prec == FE_F32 ? 2 : (native ? 1 : 0);
+    const size_t gv = idx == 2 ? sizeof(float) : (idx == 1 ? sizeof(double) : sizeof(float2));
+    if (idx == 0 && !m->xyzdw) {
+      FE_TRY(fe_dalloc((void**)&m->xyzdw, n * sizeof(float2), m->st, "coordinates (double-word)"));
+      k_split_dw<<<grid_for(n, 256), 256, 0, m->st>>>(m->xyz64, m->xyzdw, n);
+      FE_CUDA(cudaStreamSynchronize(m->st), "coordinates double-word split");
+    } else if (idx == 2 && !m->xyz32) {
+      FE_TRY(fe_dalloc((void**)&m->xyz32, n * sizeof(float), m->st, "coordinates (fp32)"));
+      k_to_f32<<<grid_for(n, 256), 256, 0, m->st>>>(m->xyz64, m->xyz32, n);
+      FE_CUDA(cudaStreamSynchronize(m->st), "coordinates fp32 copy");
+    }
+    if (!m->rc_scratch[idx]) {
+      const long long cells = fe_rc_chunk_cells(m->n, m->ncells, gv);
+      FE_TRY(fe_dalloc(&m->rc_scratch[idx], (size_t)cells * FE_GEO_COMPS * m->n3 * gv, m->st,
+                       "recompute metric scratch"));
+      FE_CUDA(cudaStreamSynchronize(m->st), "recompute metric scratch");
+    }
+    return FE_OK;
+  }
   if (m->d.geom_mode != FE_GEOM_STORED) return FE_OK;
   const long long n = m->ncells * FE_GEO_COMPS * m->n3;
   if ((prec == FE_F64 && !native && !m->geodw) || (prec == FE_F32 && !m->geo32) ||
@@ -274,7 +298,8 @@ fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
 static void free_mesh(fe_mesh* m, cudaStream_t st) {
   if (!m) return;
   if (m->cg_work && m->cg_free) m->cg_free(m->cg_work, st);
-  void* bufs[] = {m->geo64, m->geodw, m->geo32, m->xyz64, m->xyzdw, m->xyz32, m->diag64[0],
+  void* bufs[] = {m->geo64, m->geodw, m->geo32, m->xyz64, m->xyzdw, m->xyz32, m->rc_scratch[0],
+                  m->rc_scratch[1], m->rc_scratch[2], m->diag64[0],
                   m->diag64[1], m->invdiag32[0], m->invdiag32[1], m->invdiag64[0],
                   m->invdiag64[1], m->invmult64, m->red};
   for (void* b : bufs) fe_dfree(b, st);

@@ -1,6 +1,7 @@
 // fe_vec.cu -- structured DSS, Jacobi diagonal, duality pairings and cell-wise vector kernels.
 #include <cstring>
 
+#include "fe_recompute.cuh"
 #include "fe_vec.cuh"
 
 // ---------------------------------------------------------------------------------------------
@@ -90,9 +91,9 @@ struct DiagTab {
   double w[FE_MAXN];
 };
 struct DiagArgs {
-  const double* geo;
+  const double* geo;  // [cell - geo_cell0][7][N3]
   double* d;
-  long long ncells;
+  long long ncells, cell_base, geo_cell0;
   int op, affine;
   double aff[4];
   DiagTab tab;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS) k_diag(const __grid_constant_
   extern __shared__ double dsm[];
   const int t = threadIdx.x, cl = t / N2, lt = t - cl * N2, la = lt % N, lb = lt / N;
   const int cb = cl * C::CS;
-  const long long cell = (long long)blockIdx.x * C::CPB + cl;
+  const long long cell = a.cell_base + (long long)blockIdx.x * C::CPB + cl;
   const bool active = cell < a.ncells;
   // term t: (component, C1, C2, C3, factor)   matrices: 0 = V2, 1 = D2, 2 = DV
   const int nterms = (a.op == FE_LAPLACE) ? 6 : 1;
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS) k_diag(const __grid_constant_
           const double wq = a.tab.w[la] * a.tab.w[lb] * a.tab.w[q3];
           v = (c == 6) ? wq * a.aff[3] : (c < 3 ? wq * a.aff[c] : 0.0);
         } else {
-          v = a.geo[(size_t)cell * FE_GEO_COMPS * N3 + (size_t)c * N3 + q3 * N2 + lt];
+          v = a.geo[(size_t)(cell - a.geo_cell0) * FE_GEO_COMPS * N3 + (size_t)c * N3 + q3 * N2 + lt];
         }
       }
       g[q3] = v * fac[term];
@@ -182,14 +183,58 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS) k_diag(const __grid_constant_
 }
 
 template <int N>
-static fe_status launch_diag_n(const DiagArgs& a, cudaStream_t st) {
+static fe_status launch_diag_chunk(const DiagArgs& a, cudaStream_t st) {
   using C = Cfg<N>;
   const size_t smem = (size_t)C::TILE * sizeof(double);
   FE_CUDA(cudaFuncSetAttribute(k_diag<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
           "diag smem attribute");
-  const long long blocks = (a.ncells + C::CPB - 1) / C::CPB;
+  const long long blocks = (a.ncells - a.cell_base + C::CPB - 1) / C::CPB;
   if (blocks > 0) k_diag<N><<<(unsigned)blocks, C::THREADS, smem, st>>>(a);
   return fe_cuda_check(cudaGetLastError(), "diag launch");
+}
+
+// Recompute mode: the FP64 metric of one chunk of cells into the FP64 scratch, then the diagonal
+// of that chunk.
+template <int N>
+static fe_status launch_diag_n(const fe_mesh* m, DiagArgs a, cudaStream_t st) {
+  if (m->d.geom_mode != FE_GEOM_RECOMPUTE) return launch_diag_chunk<N>(a, st);
+  using G = GeoCfg<N>;
+  double* scratch = static_cast<double*>(m->rc_scratch[1]);
+  if (!scratch || !m->xyz64) {
+    fe_set_error("diag: recompute-mode buffers missing");
+    return FE_ERR_INVALID;
+  }
+  const long long chunk = fe_rc_chunk_cells(N, m->ncells, sizeof(double));
+  RecomputeArgs<N, double> r;
+  std::memset(&r, 0, sizeof(r));
+  r.xyz = m->xyz64;
+  r.geo = scratch;
+  for (int q = 0; q < N; ++q) {
+    r.tab.W_[q] = m->tab.w[q];
+    for (int i = 0; i < N; ++i) {
+      r.tab.V_[q][i] = m->tab.V[q][i];
+      r.tab.D_[q][i] = m->tab.D[q][i];
+    }
+  }
+  a.geo = scratch;
+  const long long total = m->ncells;
+  for (long long c0 = 0; c0 < total; c0 += chunk) {
+    const long long c1 = c0 + chunk < total ? c0 + chunk : total;
+    r.cell0 = c0;
+    r.cell_end = c1;
+    const unsigned gb = (unsigned)((c1 - c0 + G::CPB - 1) / G::CPB);
+    const size_t gs = recompute_smem_bytes<N, double>();
+    if (a.op == FE_LAPLACE)
+      k_recompute<N, double, FE_LAPLACE><<<gb, G::THREADS, gs, st>>>(r);
+    else
+      k_recompute<N, double, FE_MASS><<<gb, G::THREADS, gs, st>>>(r);
+    FE_CUDA(cudaGetLastError(), "recompute kernel launch");
+    a.cell_base = c0;
+    a.geo_cell0 = c0;
+    a.ncells = c1;
+    FE_TRY(launch_diag_chunk<N>(a, st));
+  }
+  return FE_OK;
 }
 
 // Dirichlet nodes -> 1 (one warp per cell, lanes over the cell's nodes)
@@ -232,19 +277,20 @@ fe_status fe_launch_diag(const fe_mesh* m, int op, double* d, cudaStream_t st) {
       a.tab.DV[q][i] = m->tab.Dh[q][i] * m->tab.V[q][i];
     }
   }
-  if (!a.affine && !a.geo) {
-    fe_set_error("diag: needs stored or affine geometry");
+  if (m->d.geom_mode == FE_GEOM_RECOMPUTE) FE_TRY(fe_ensure_geometry(m, FE_F64, true));
+  if (!a.affine && !a.geo && m->d.geom_mode != FE_GEOM_RECOMPUTE) {
+    fe_set_error("diag: the stored metric has been released");
     return FE_ERR_INVALID;
   }
   fe_status s;
   switch (m->n) {
-    case 2: s = launch_diag_n<2>(a, st); break;
-    case 3: s = launch_diag_n<3>(a, st); break;
-    case 4: s = launch_diag_n<4>(a, st); break;
-    case 5: s = launch_diag_n<5>(a, st); break;
-    case 6: s = launch_diag_n<6>(a, st); break;
-    case 7: s = launch_diag_n<7>(a, st); break;
-    case 8: s = launch_diag_n<8>(a, st); break;
+    case 2: s = launch_diag_n<2>(m, a, st); break;
+    case 3: s = launch_diag_n<3>(m, a, st); break;
+    case 4: s = launch_diag_n<4>(m, a, st); break;
+    case 5: s = launch_diag_n<5>(m, a, st); break;
+    case 6: s = launch_diag_n<6>(m, a, st); break;
+    case 7: s = launch_diag_n<7>(m, a, st); break;
+    case 8: s = launch_diag_n<8>(m, a, st); break;
     default: fe_set_error("diag: bad n"); return FE_ERR_INVALID;
   }
   if (s != FE_OK) return s;
