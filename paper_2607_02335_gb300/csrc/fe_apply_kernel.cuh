@@ -14,11 +14,17 @@
 // owns one 1D line of the cell's n^3 tensor per phase: the z-line (i,j) = (t % n, t / n) while
 // data sits in registers (global load/store, pointwise geometry, z sweeps), the x-line
 // (j,k) = (t % n, t / n) and the y-line (i,k) = (t % n, t / n) for the x and y sweeps, which
-// read and write the cell's tile in shared memory.  Every contraction loop is unrolled with
-// compile-time indices, so the 1D matrices (kernel parameters) are read from the constant bank
-// as instruction operands.  Rows of the shared-memory tile are padded to n+1 entries, which makes
-// the x- and y-line accesses of a warp bank-conflict free for 4-byte planes (double-word values
-// are kept as separate hi and lo float planes).
+// read and write the cell's tile in shared memory.  Rows of the tile are padded to n+1 entries,
+// which keeps the line accesses of a warp free of bank conflicts (double-word values are stored
+// as interleaved hi/lo pairs, one 64-bit access each).
+//
+// Every 1D contraction uses the even-odd form of the matrix (the reflection symmetry of the GLL
+// nodes and Gauss points; the even-odd decomposition named in Sec. 2.3 "Initial performance
+// measurements"), which halves the multiply-adds.
+// Up to n = FE_ROLL_MINN - 1 all loops unroll with compile-time indices, so the 1D tables (kernel
+// parameters) are read from the constant bank as instruction operands; from n = FE_ROLL_MINN on
+// the output loop of each contraction stays a run-time loop (apply_cells_rolled), because the
+// fully unrolled double-word kernel no longer fits the instruction cache.
 #pragma once
 #include "fe_internal.h"
 
@@ -68,27 +74,56 @@ struct Sm<dw> {  // hi and lo interleaved: one 64-bit shared-memory access per v
   static constexpr int BYTES = 8;
 };
 
-// out[q] = sum_r M[q][r] in[r]
-template <int N, class V>
-__device__ __forceinline__ void mv(const V (&M)[N][N], const V (&in)[N], V (&out)[N]) {
+// One 1D contraction of a line in even-odd form (the EO comment in fe_internal.h):
+// put(q, value) receives output q.  ROLLED: the output pairs are a run-time loop (outputs must
+// go to shared memory); otherwise everything unrolls and put may write a register array.
+template <int N, class V, int SIG, bool ROLLED, class Put>
+__device__ __forceinline__ void eo_line(const EO<N, V>& t, const V (&in)[N], Put put) {
+  using T = NT<V>;
+  constexpr int H = N / 2, MID = N / 2;
+  V e[H], o[H];
 #pragma unroll
-  for (int q = 0; q < N; ++q) {
-    V acc = NT<V>::zero();
+  for (int r = 0; r < H; ++r) {
+    e[r] = T::addk(in[r], in[N - 1 - r]);
+    o[r] = T::subk(in[r], in[N - 1 - r]);
+  }
+  if constexpr (N & 1) {
+    V acc;
+    if constexpr (SIG > 0) {
+      acc = T::prod(t.mm, in[MID]);
 #pragma unroll
-    for (int r = 0; r < N; ++r) acc = NT<V>::mac(acc, M[q][r], in[r]);
-    out[q] = NT<V>::keep(acc);
+      for (int r = 0; r < H; ++r) acc = T::mac(acc, t.cr[r], e[r]);
+    } else {
+      acc = T::prod(t.cr[0], o[0]);
+#pragma unroll
+      for (int r = 1; r < H; ++r) acc = T::mac(acc, t.cr[r], o[r]);
+    }
+    put(MID, T::keep(acc));
+  }
+  auto pair = [&](int q) {
+    V a = T::prod(t.A[q][0], e[0]);
+#pragma unroll
+    for (int r = 1; r < H; ++r) a = T::mac(a, t.A[q][r], e[r]);
+    if constexpr (N & 1) a = T::mac(a, t.cm[q], in[MID]);
+    V b = T::prod(t.B[q][0], o[0]);
+#pragma unroll
+    for (int r = 1; r < H; ++r) b = T::mac(b, t.B[q][r], o[r]);
+    put(q, T::addk(a, b));
+    put(N - 1 - q, SIG > 0 ? T::subk(a, b) : T::subk(b, a));
+  };
+  if constexpr (ROLLED) {
+#pragma unroll 1
+    for (int q = 0; q < H; ++q) pair(q);
+  } else {
+#pragma unroll
+    for (int q = 0; q < H; ++q) pair(q);
   }
 }
-// out[r] = sum_q M[q][r] in[q]
-template <int N, class V>
-__device__ __forceinline__ void mtv(const V (&M)[N][N], const V (&in)[N], V (&out)[N]) {
-#pragma unroll
-  for (int r = 0; r < N; ++r) {
-    V acc = NT<V>::zero();
-#pragma unroll
-    for (int q = 0; q < N; ++q) acc = NT<V>::mac(acc, M[q][r], in[q]);
-    out[r] = NT<V>::keep(acc);
-  }
+
+// register line -> register line
+template <int N, class V, int SIG>
+__device__ __forceinline__ void eo_regs(const EO<N, V>& t, const V (&in)[N], V (&out)[N]) {
+  eo_line<N, V, SIG, false>(t, in, [&](int q, V v) { out[q] = v; });
 }
 
 // line access in the padded tile: x-line (a=j, b=k), y-line (a=i, b=k), z-line (a=i, b=j)
@@ -100,19 +135,16 @@ template <int N>
 __device__ __forceinline__ int zl(int a, int b, int r) { return r * Cfg<N>::PS + b * Cfg<N>::RS + a; }
 
 // in-place 1D sweep of every line along one axis of the tile, by the line-owning thread
-template <int N, class V, int AX, bool TR>
+template <int N, class V, int AX, int SIG>
 __device__ __forceinline__ void tile_sweep(const Sm<V>& s, int cbase, int a, int b,
-                                           const V (&M)[N][N]) {
-  V in[N], out[N];
+                                           const EO<N, V>& M) {
+  V in[N];
 #pragma unroll
   for (int r = 0; r < N; ++r)
     in[r] = s.get(cbase + (AX == 0 ? xl<N>(a, b, r) : yl<N>(a, b, r)));
-  if (TR)
-    mtv<N, V>(M, in, out);
-  else
-    mv<N, V>(M, in, out);
-#pragma unroll
-  for (int r = 0; r < N; ++r) s.put(cbase + (AX == 0 ? xl<N>(a, b, r) : yl<N>(a, b, r)), out[r]);
+  eo_line<N, V, SIG, false>(M, in, [&](int q, V v) {
+    s.put(cbase + (AX == 0 ? xl<N>(a, b, q) : yl<N>(a, b, q)), v);
+  });
 }
 
 // Everything an apply needs except the 1D tables.
@@ -138,6 +170,180 @@ struct ApplyArgs {
 
 enum { GEOM_STORED_K = 0, GEOM_AFFINE_K = 2 };
 
+// ---------------------------------------------------------------------------------------------
+// High degrees: the same sweeps with the output index of every 1D contraction as a run-time loop.
+// Fully unrolled n x n contractions in double-word arithmetic outgrow the instruction cache from
+// n ~ 6 on (the unrolled kernel then waits on instruction fetch); here each sweep is one unrolled
+// n-term dot product per output, the coefficients come from the constant bank with a
+// warp-uniform index, and every output goes straight to the shared-memory tile.
+// ---------------------------------------------------------------------------------------------
+#ifndef FE_PREFETCH_MASS_MAXN  // mass: fetch w detJ of the z-line at the start up to this n
+#define FE_PREFETCH_MASS_MAXN 6
+#endif
+#ifndef FE_ROLL_MINN
+#define FE_ROLL_MINN 5
+#endif
+
+// s[base + q * stride] = (M in)_q
+template <int N, class V, int SIG>
+__device__ __forceinline__ void sweep_rolled(const EO<N, V>& M, const V (&in)[N], const Sm<V>& s,
+                                             int base, int stride) {
+  eo_line<N, V, SIG, true>(M, in, [&](int q, V v) { s.put(base + q * stride, v); });
+}
+
+template <int N, class V, int OP, int GEOM>
+__device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
+                                                   long long cell0, unsigned char* smraw,
+                                                   int tile_stride) {
+  using T = NT<V>;
+  using C = Cfg<N>;
+  constexpr int N2 = C::N2, N3 = C::N3, RS = C::RS, PS = C::PS;
+  constexpr int NARR = (OP == FE_LAPLACE) ? 3 : 1;
+  const Sm<V> s0(smraw, NARR, 0, tile_stride);
+  const Sm<V> s1(smraw, NARR, NARR > 1 ? 1 : 0, tile_stride);
+  const Sm<V> s2(smraw, NARR, NARR > 2 ? 2 : 0, tile_stride);
+
+  const int t = threadIdx.x;
+  const int cl = t / N2;
+  const int lt = t - cl * N2;
+  const int la = lt % N, lb = lt / N;
+  const int cb = cl * C::CS;
+  const long long cell = cell0 + cl;
+  const bool active = cl < C::CPB && cell < a.ncells;
+  const long long gbase = cell * N3;
+  // line starts in the tile: x-line (j=la, k=lb), y-line (i=la, k=lb), z-line (i=la, j=lb)
+  const int bx = cb + lb * PS + la * RS, by = cb + lb * PS + la, bz = cb + lb * RS + la;
+
+  bool bnd_line = false, bnd_k0 = false, bnd_k1 = false;
+  if (a.dirichlet && active) {
+    const int cx = (int)(cell % a.mx);
+    const int cy = (int)((cell / a.mx) % a.my);
+    const int cz = (int)(cell / ((long long)a.mx * a.my));
+    bnd_line = (cx == 0 && la == 0) || (cx == a.mx - 1 && la == N - 1) || (cy == 0 && lb == 0) ||
+               (cy == a.my - 1 && lb == N - 1);
+    bnd_k0 = (cz == 0);
+    bnd_k1 = (cz == a.mz - 1);
+  }
+  auto masked = [&](int k) { return bnd_line || (k == 0 && bnd_k0) || (k == N - 1 && bnd_k1); };
+  auto load_line = [&](const Sm<V>& s, int base, int stride, V (&v)[N]) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) v[r] = s.get(base + r * stride);
+  };
+
+  V in[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    V v = active ? T::load_stream(a.x + gbase + k * N2 + lt) : T::zero();
+    in[k] = masked(k) ? T::zero() : v;
+  }
+  constexpr bool PREF_M = (OP == FE_MASS) && (GEOM == GEOM_STORED_K) && (N <= FE_PREFETCH_MASS_MAXN);
+  V jpre[PREF_M ? N : 1];
+  if constexpr (PREF_M) {
+    const typename NT<V>::GV* g6 =
+        a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + 6 * N3 + lt;
+#pragma unroll
+    for (int k = 0; k < N; ++k) jpre[k] = active ? T::geo(g6 + k * N2) : T::zero();
+  }
+  sweep_rolled<N, V, 1>(tab.eV, in, s0, bz, PS);  // z
+  __syncthreads();
+  load_line(s0, bx, 1, in);
+  sweep_rolled<N, V, 1>(tab.eV, in, s0, bx, 1);  // x
+  __syncthreads();
+  load_line(s0, by, RS, in);
+  sweep_rolled<N, V, 1>(tab.eV, in, s0, by, RS);  // y
+  __syncthreads();
+
+  if constexpr (OP == FE_LAPLACE) {
+    V inz[N];
+    load_line(s0, bz, PS, inz);
+    load_line(s0, bx, 1, in);
+    sweep_rolled<N, V, -1>(tab.eD, in, s1, bx, 1);  // d/dx -> s1
+    load_line(s0, by, RS, in);
+    sweep_rolled<N, V, -1>(tab.eD, in, s2, by, RS);  // d/dy -> s2
+    __syncthreads();
+    sweep_rolled<N, V, -1>(tab.eD, inz, s0, bz, PS);  // d/dz -> s0 (own z-line)
+    // pointwise metric on the own z-line: g = G grad u
+    const typename NT<V>::GV* gp = a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + lt;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int e = bz + k * PS;
+      const V dx = s1.get(e), dy = s2.get(e), dz = s0.get(e);
+      V gxx, gyy, gzz, gxy, gxz, gyz;
+      if constexpr (GEOM == GEOM_AFFINE_K) {
+        const V wq = T::mul(T::mul(tab.W_[la], tab.W_[lb]), tab.W_[k]);
+        s1.put(e, T::mul(T::mul(wq, a.aff[0]), dx));
+        s2.put(e, T::mul(T::mul(wq, a.aff[1]), dy));
+        s0.put(e, T::mul(T::mul(wq, a.aff[2]), dz));
+      } else {
+        if (active) {
+          gxx = T::geo(gp + 0 * N3 + k * N2);
+          gyy = T::geo(gp + 1 * N3 + k * N2);
+          gzz = T::geo(gp + 2 * N3 + k * N2);
+          gxy = T::geo(gp + 3 * N3 + k * N2);
+          gxz = T::geo(gp + 4 * N3 + k * N2);
+          gyz = T::geo(gp + 5 * N3 + k * N2);
+        } else {
+          gxx = gyy = gzz = gxy = gxz = gyz = T::zero();
+        }
+        const V gx = T::keep(T::mac(T::mac(T::prod(gxx, dx), gxy, dy), gxz, dz));
+        const V gy = T::keep(T::mac(T::mac(T::prod(gxy, dx), gyy, dy), gyz, dz));
+        const V gz = T::keep(T::mac(T::mac(T::prod(gxz, dx), gyz, dy), gzz, dz));
+        s1.put(e, gx);
+        s2.put(e, gy);
+        s0.put(e, gz);
+      }
+    }
+    __syncthreads();
+    // transposed derivatives, each in place on its own array
+    load_line(s1, bx, 1, in);
+    sweep_rolled<N, V, -1>(tab.eDT, in, s1, bx, 1);
+    load_line(s2, by, RS, in);
+    sweep_rolled<N, V, -1>(tab.eDT, in, s2, by, RS);
+    load_line(s0, bz, PS, in);
+    sweep_rolled<N, V, -1>(tab.eDT, in, s0, bz, PS);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int e = bz + k * PS;
+      in[k] = T::add(T::add(s0.get(e), s1.get(e)), s2.get(e));
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const V uq = s0.get(bz + k * PS);
+      V jw;
+      if constexpr (GEOM == GEOM_AFFINE_K) {
+        jw = T::mul(T::mul(T::mul(tab.W_[la], tab.W_[lb]), tab.W_[k]), a.aff[3]);
+      } else if constexpr (PREF_M) {
+        jw = jpre[k];
+      } else {
+        jw = active ? T::geo(a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + 6 * N3 +
+                             k * N2 + lt)
+                    : T::zero();
+      }
+      in[k] = T::mul(jw, uq);
+    }
+  }
+
+  // transposed interpolation: z from registers, then x and y in place
+  sweep_rolled<N, V, 1>(tab.eVT, in, s0, bz, PS);
+  __syncthreads();
+  load_line(s0, bx, 1, in);
+  sweep_rolled<N, V, 1>(tab.eVT, in, s0, bx, 1);
+  __syncthreads();
+  load_line(s0, by, RS, in);
+  sweep_rolled<N, V, 1>(tab.eVT, in, s0, by, RS);
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      V v = s0.get(bz + k * PS);
+      if (masked(k)) v = T::zero();
+      T::store(a.y + gbase + k * N2 + lt, v);
+    }
+  }
+}
+
 // The cells cell0 .. cell0 + CPB - 1 (those below ncells), applied by the CTA's first CPB*n^2
 // threads.  Threads beyond that (a CTA wider than the tile, as in the batched persistent kernel)
 // work on a spare slot of the tile that nobody reads and still reach every barrier; the caller
@@ -146,6 +352,10 @@ template <int N, class V, int OP, int GEOM>
 __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
                                             long long cell0, unsigned char* smraw,
                                             int tile_stride) {
+  if constexpr (N >= FE_ROLL_MINN) {
+    apply_cells_rolled<N, V, OP, GEOM>(a, tab, cell0, smraw, tile_stride);
+    return;
+  }
   using T = NT<V>;
   using C = Cfg<N>;
   constexpr int N2 = C::N2, N3 = C::N3;
@@ -186,10 +396,19 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   }
   // low degrees: issue the metric loads now so that their latency hides behind the sweeps
 #ifndef FE_PREFETCH_MAXN
-#define FE_PREFETCH_MAXN 3
+#define FE_PREFETCH_MAXN 4
 #endif
   constexpr bool PREF = (OP == FE_LAPLACE) && (GEOM == GEOM_STORED_K) && (N <= FE_PREFETCH_MAXN);
   V gpre[PREF ? 6 * N : 1];
+  // mass: the N values of w detJ on the z-line are always fetched up front
+  constexpr bool PREF_M = (OP == FE_MASS) && (GEOM == GEOM_STORED_K) && (N <= FE_PREFETCH_MASS_MAXN);
+  V jpre[PREF_M ? N : 1];
+  if constexpr (PREF_M) {
+    const typename NT<V>::GV* g6 =
+        a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + 6 * N3 + lt;
+#pragma unroll
+    for (int k = 0; k < N; ++k) jpre[k] = active ? T::geo(g6 + k * N2) : T::zero();
+  }
   if constexpr (PREF) {
     const typename NT<V>::GV* g0 = a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + lt;
 #pragma unroll
@@ -197,13 +416,13 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 #pragma unroll
       for (int c = 0; c < 6; ++c) gpre[c * N + k] = active ? T::geo(g0 + c * N3 + k * N2) : T::zero();
   }
-  mv<N, V>(tab.V_, u, w);
+  eo_regs<N, V, 1>(tab.eV, u, w);
 #pragma unroll
   for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
   __syncthreads();
-  tile_sweep<N, V, 0, false>(s0, cb, la, lb, tab.V_);  // x
+  tile_sweep<N, V, 0, 1>(s0, cb, la, lb, tab.eV);  // x
   __syncthreads();
-  tile_sweep<N, V, 1, false>(s0, cb, la, lb, tab.V_);  // y
+  tile_sweep<N, V, 1, 1>(s0, cb, la, lb, tab.eV);  // y
   __syncthreads();
   // s0 now holds u at the Gauss points
 
@@ -213,17 +432,17 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
       V in[N], out[N];
 #pragma unroll
       for (int r = 0; r < N; ++r) in[r] = s0.get(cb + xl<N>(la, lb, r));
-      mv<N, V>(tab.D_, in, out);
+      eo_regs<N, V, -1>(tab.eD, in, out);
 #pragma unroll
       for (int r = 0; r < N; ++r) s1.put(cb + xl<N>(la, lb, r), out[r]);
 #pragma unroll
       for (int r = 0; r < N; ++r) in[r] = s0.get(cb + yl<N>(la, lb, r));
-      mv<N, V>(tab.D_, in, out);
+      eo_regs<N, V, -1>(tab.eD, in, out);
 #pragma unroll
       for (int r = 0; r < N; ++r) s2.put(cb + yl<N>(la, lb, r), out[r]);
 #pragma unroll
       for (int r = 0; r < N; ++r) in[r] = s0.get(cb + zl<N>(la, lb, r));
-      mv<N, V>(tab.D_, in, u);  // u := d/dz along the z-line
+      eo_regs<N, V, -1>(tab.eD, in, u);  // u := d/dz along the z-line
     }
     __syncthreads();
     // ---- pointwise metric: g = G grad u (z-line owner)
@@ -264,10 +483,9 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
             gxx = gyy = gzz = gxy = gxz = gyz = T::zero();
           }
         }
-        V gx = T::zero(), gy = T::zero(), gz = T::zero();
-        gx = T::keep(T::mac(T::mac(T::mac(gx, gxx, dx), gxy, dy), gxz, dz));
-        gy = T::keep(T::mac(T::mac(T::mac(gy, gxy, dx), gyy, dy), gyz, dz));
-        gz = T::keep(T::mac(T::mac(T::mac(gz, gxz, dx), gyz, dy), gzz, dz));
+        const V gx = T::keep(T::mac(T::mac(T::prod(gxx, dx), gxy, dy), gxz, dz));
+        const V gy = T::keep(T::mac(T::mac(T::prod(gxy, dx), gyy, dy), gyz, dz));
+        const V gz = T::keep(T::mac(T::mac(T::prod(gxz, dx), gyz, dy), gzz, dz));
         s1.put(e, gx);
         s2.put(e, gy);
         u[k] = gz;
@@ -275,9 +493,9 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
     }
     __syncthreads();
     // ---- transposed derivative: t = D^T gx (x) + D^T gy (y) + D^T gz (z)
-    tile_sweep<N, V, 0, true>(s1, cb, la, lb, tab.D_);
-    tile_sweep<N, V, 1, true>(s2, cb, la, lb, tab.D_);
-    mtv<N, V>(tab.D_, u, w);
+    tile_sweep<N, V, 0, -1>(s1, cb, la, lb, tab.eDT);
+    tile_sweep<N, V, 1, -1>(s2, cb, la, lb, tab.eDT);
+    eo_regs<N, V, -1>(tab.eDT, u, w);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -292,6 +510,8 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
       V jw;
       if constexpr (GEOM == GEOM_AFFINE_K) {
         jw = T::mul(T::mul(T::mul(tab.W_[la], tab.W_[lb]), tab.W_[k]), a.aff[3]);
+      } else if constexpr (PREF_M) {
+        jw = jpre[k];
       } else {
         jw = active ? T::geo(a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + 6 * N3 +
                              k * N2 + lt)
@@ -302,13 +522,13 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   }
 
   // ---- transposed interpolation: z in registers, then x and y in the tile
-  mtv<N, V>(tab.V_, u, w);
+  eo_regs<N, V, 1>(tab.eVT, u, w);
 #pragma unroll
   for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
   __syncthreads();
-  tile_sweep<N, V, 0, true>(s0, cb, la, lb, tab.V_);
+  tile_sweep<N, V, 0, 1>(s0, cb, la, lb, tab.eVT);
   __syncthreads();
-  tile_sweep<N, V, 1, true>(s0, cb, la, lb, tab.V_);
+  tile_sweep<N, V, 1, 1>(s0, cb, la, lb, tab.eVT);
   __syncthreads();
   if (active) {
 #pragma unroll

@@ -17,6 +17,25 @@ inline dw fe_cast<dw>(double v) {
   return {h, (float)(v - (double)h)};
 }
 
+// even-odd form of M (tr: of M^T), from the FP64 tables
+template <int N, class V>
+void fill_eo(EO<N, V>& e, const double (&M0)[FE_MAXN][FE_MAXN], bool tr) {
+  auto M = [&](int q, int r) { return tr ? M0[r][q] : M0[q][r]; };
+  constexpr int H = N / 2, mid = N / 2;
+  std::memset(&e, 0, sizeof(e));
+  for (int q = 0; q < H; ++q) {
+    for (int r = 0; r < H; ++r) {
+      e.A[q][r] = fe_cast<V>(0.5 * (M(q, r) + M(q, N - 1 - r)));
+      e.B[q][r] = fe_cast<V>(0.5 * (M(q, r) - M(q, N - 1 - r)));
+    }
+    if (N & 1) {
+      e.cm[q] = fe_cast<V>(M(q, mid));
+      e.cr[q] = fe_cast<V>(M(mid, q));
+    }
+  }
+  if (N & 1) e.mm = fe_cast<V>(M(mid, mid));
+}
+
 template <int N, class V>
 Tab1D<N, V> make_tab(const HostTab& h) {
   Tab1D<N, V> t;
@@ -27,6 +46,10 @@ Tab1D<N, V> make_tab(const HostTab& h) {
       t.D_[a][b] = fe_cast<V>(h.D[a][b]);
     }
   }
+  fill_eo<N, V>(t.eV, h.V, false);
+  fill_eo<N, V>(t.eVT, h.V, true);
+  fill_eo<N, V>(t.eD, h.D, false);
+  fill_eo<N, V>(t.eDT, h.D, true);
   return t;
 }
 

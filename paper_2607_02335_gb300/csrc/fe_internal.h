@@ -44,6 +44,18 @@ __device__ __forceinline__ dw dw_mac(dw acc, dw c, dw v) {
   dw s = dw_two_sum(acc.h, p);
   return {s.h, __fadd_rn(acc.l, __fadd_rn(s.l, e))};
 }
+// c*v as an unnormalised pair (the first term of a dot product: no TwoSum with a zero accumulator)
+__device__ __forceinline__ dw dw_prod(dw c, dw v) {
+  float p = __fmul_rn(c.h, v.h);
+  float e = __fmaf_rn(c.h, v.h, -p);
+  e = __fmaf_rn(c.h, v.l, e);
+  e = __fmaf_rn(c.l, v.h, e);
+  return {p, e};
+}
+__device__ __forceinline__ dw dw_add_keep(dw a, dw b) {
+  dw s = dw_two_sum(a.h, b.h);
+  return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
+}
 __device__ __forceinline__ dw dw_norm(dw a) { return dw_fast_two_sum(a.h, a.l); }
 __device__ __forceinline__ dw dw_add(dw a, dw b) {
   dw s = dw_two_sum(a.h, b.h);
@@ -66,7 +78,13 @@ __device__ __forceinline__ dw dw_from_double(double x) {
   if (e - 949u <= 201u) {
     unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
     float hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
-    float lo = __fmul_rn(__uint2float_rn((unsigned)b & 0x1FFFFFFFu), __uint_as_float((e - 948u) << 23));
+    // float of the 29-bit integer m without an int->float conversion (those issue on the slow FP64
+    // pipe): low 23 and high 6 bits are exact floats through the 2^23 bias, and the fma rounds
+    // m once, as a conversion would
+    const unsigned m = (unsigned)b & 0x1FFFFFFFu;
+    const float flo = __fsub_rn(__uint_as_float(0x4B000000u | (m & 0x7FFFFFu)), 8388608.0f);
+    const float fhi = __fsub_rn(__uint_as_float(0x4B000000u | (m >> 23)), 8388608.0f);
+    float lo = __fmul_rn(__fmaf_rn(fhi, 8388608.0f, flo), __uint_as_float((e - 948u) << 23));
     lo = __uint_as_float(__float_as_uint(lo) | sign);
     return {hi, lo};
   }
@@ -89,6 +107,33 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }
 __device__ __forceinline__ double dw_to_double(dw a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 
+// binary64 of h + l on the integer and FP32 pipes (no FP64 add): after a TwoSum |l| <= ulp(h)/2,
+// so l is at most 2^28 units of 2^(e-52), e the exponent of h; those units, truncated to an
+// integer, are added to (or, for opposite signs, subtracted from) the bit pattern of h, whose
+// low 29 mantissa bits are zero.  Subtracting from a power of two crosses into the binade below,
+// where the unit is half as large.  Result within 2^(e-52) of h + l (about one double ulp).
+// Zero and the exponent range outside 2^-75 .. 2^127 take the FP64 path.
+__device__ __forceinline__ double dw_to_double_int(dw a) {
+  const dw s = dw_two_sum(a.h, a.l);
+  const unsigned hb = __float_as_uint(s.h);
+  const unsigned e8 = (hb >> 23) & 0xFFu;
+  if (e8 - 52u > 202u) return s.h == 0.0f ? 0.0 : dw_to_double(s);
+  const unsigned long long dh = ((unsigned long long)(hb & 0x80000000u) << 32) |
+                                ((unsigned long long)(e8 + 896u) << 52) |
+                                ((unsigned long long)(hb & 0x7FFFFFu) << 29);
+  const float v = __fmul_rn(fabsf(s.l), __uint_as_float((306u - e8) << 23));
+  const unsigned vb = __float_as_uint(v);
+  const int ev = (int)(vb >> 23) - 127;
+  const unsigned mv = (vb & 0x7FFFFFu) | 0x800000u;
+  const unsigned li = ev >= 23 ? (mv << (ev - 23)) : (ev >= 0 ? (mv >> (23 - ev)) : 0u);
+  unsigned long long out;
+  if (((hb ^ __float_as_uint(s.l)) & 0x80000000u) == 0u)
+    out = dh + li;
+  else
+    out = dh - ((hb & 0x7FFFFFu) == 0u ? 2ull * li : (unsigned long long)li);
+  return __longlong_as_double((long long)out);
+}
+
 // ---------------------------------------------------------------------------------------------
 // number traits: value type V, storage type of vectors (SV) and of geometry (GV)
 // ---------------------------------------------------------------------------------------------
@@ -101,6 +146,9 @@ struct NT<double> {
   using GV = double;
   __device__ static __forceinline__ double zero() { return 0.0; }
   __device__ static __forceinline__ double mac(double a, double c, double v) { return fma(c, v, a); }
+  __device__ static __forceinline__ double prod(double c, double v) { return c * v; }
+  __device__ static __forceinline__ double addk(double a, double b) { return a + b; }
+  __device__ static __forceinline__ double subk(double a, double b) { return a - b; }
   __device__ static __forceinline__ double fin(double a) { return a; }
   __device__ static __forceinline__ double keep(double a) { return a; }
   __device__ static __forceinline__ double mul(double a, double b) { return a * b; }
@@ -120,6 +168,9 @@ struct NT<float> {
   using GV = float;
   __device__ static __forceinline__ float zero() { return 0.0f; }
   __device__ static __forceinline__ float mac(float a, float c, float v) { return fmaf(c, v, a); }
+  __device__ static __forceinline__ float prod(float c, float v) { return c * v; }
+  __device__ static __forceinline__ float addk(float a, float b) { return a + b; }
+  __device__ static __forceinline__ float subk(float a, float b) { return a - b; }
   __device__ static __forceinline__ float fin(float a) { return a; }
   __device__ static __forceinline__ float keep(float a) { return a; }
   __device__ static __forceinline__ float mul(float a, float b) { return a * b; }
@@ -139,6 +190,11 @@ struct NT<dw> {
   using GV = float2;
   __device__ static __forceinline__ dw zero() { return {0.0f, 0.0f}; }
   __device__ static __forceinline__ dw mac(dw a, dw c, dw v) { return dw_mac(a, c, v); }
+  __device__ static __forceinline__ dw prod(dw c, dw v) { return dw_prod(c, v); }
+  // unnormalised sums (TwoSum of the high parts, low parts added in float): the error stays at
+  // the double-word level of the operands, which is all the following products need
+  __device__ static __forceinline__ dw addk(dw a, dw b) { return dw_add_keep(a, b); }
+  __device__ static __forceinline__ dw subk(dw a, dw b) { return dw_add_keep(a, {-b.h, -b.l}); }
   __device__ static __forceinline__ dw fin(dw a) { return dw_norm(a); }
   // intermediate results of the sweeps stay unnormalised: |lo| stays below a few ulp(hi), and the
   // next products use lo only in FP32 cross terms (relative effect ~2^-45)
@@ -155,7 +211,7 @@ struct NT<dw> {
   __device__ static __forceinline__ dw neg(dw a) { return {-a.h, -a.l}; }
   __device__ static __forceinline__ dw load(const double* p) { return dw_from_double(__ldg(p)); }
   __device__ static __forceinline__ dw load_stream(const double* p) { return dw_from_double(__ldcs(p)); }
-  __device__ static __forceinline__ void store(double* p, dw v) { __stcs(p, dw_to_double(v)); }
+  __device__ static __forceinline__ void store(double* p, dw v) { __stcs(p, dw_to_double_int(v)); }
   __device__ static __forceinline__ dw geo(const float2* p) {
     float2 g = __ldcs(p);
     return {g.x, g.y};
@@ -166,11 +222,28 @@ struct NT<dw> {
 // 1D tables passed by value as kernel parameters (they land in the constant bank and are read
 // with compile-time offsets).  Index convention: A[q][i] maps node/point i to point q.
 // ---------------------------------------------------------------------------------------------
+// Even-odd form of an n x n matrix M with the reflection symmetry M[n-1-q][n-1-r] = sig M[q][r]
+// (sig = +1 for V, -1 for D: node and point sets are symmetric about 1/2).  With
+// e_r = x_r + x_{n-1-r} and o_r = x_r - x_{n-1-r} (r < n/2), a = sum_r A[q][r] e_r (+ cm[q] x_mid),
+// b = sum_r B[q][r] o_r:  (M x)_q = a + b and (M x)_{n-1-q} = sig (a - b); for odd n the middle
+// output is sum_r cr[r] e_r + mm x_mid (sig = +1) or sum_r cr[r] o_r (sig = -1).  About half the
+// multiply-adds of the plain product.
+template <int N, class V>
+struct EO {
+  static constexpr int H = N / 2;
+  V A[H][H];  // (M[q][r] + M[q][n-1-r]) / 2
+  V B[H][H];  // (M[q][r] - M[q][n-1-r]) / 2
+  V cm[H];    // M[q][mid]   (odd n)
+  V cr[H];    // M[mid][r]   (odd n)
+  V mm;       // M[mid][mid] (odd n, sig = +1)
+};
+
 template <int N, class V>
 struct Tab1D {
   V V_[N][N];  // V[q][i]  = l_i(s_q): GLL-node Lagrange basis at Gauss point q      (Sec. 2.3 "V")
   V D_[N][N];  // D[q][r]  = derivative of the Gauss-point Lagrange basis r at s_q (collocation)
   V W_[N];     // Gauss weights on [0,1]
+  EO<N, V> eV, eVT, eD, eDT;  // even-odd forms of V, V^T, D, D^T
 };
 
 // host-side 1D rules in double precision for one degree
