@@ -544,20 +544,22 @@ def serving_run(fe, mixed, n_req, rate, budget_gb, slots, cap_s, seed=0):
 
 
 def run_profile_case(args):
-    """One (degree, cells, operator) case applied W+K times with FE_ASSEMBLE; no timing."""
+    """One (degree, cells, operator[, vol]) case applied W+K times with FE_ASSEMBLE (vol: the
+    volumetric apply alone); no timing."""
     import torch
 
     from paper_2607_02335_gb300 import fe
     from paper_2607_02335_gb300 import synth as S
 
-    p, m, opname = args.profile_case.split(",")
-    p, m = int(p), int(m)
+    parts = args.profile_case.split(",")
+    p, m, opname = int(parts[0]), int(parts[1]), parts[2]
+    flags = 0 if len(parts) > 3 and parts[3] == "vol" else fe.FE_ASSEMBLE
     op = fe.FE_LAPLACE if opname == "laplace" else fe.FE_MASS
     gm = fe.Mesh(m, p, deform_amp=AMP)
     x = gm.gather(S.primal_unique(m, p, seed=0))
     y = gm.empty()
     for _ in range(args.warmup + args.steps):
-        fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, fe.FE_ASSEMBLE)
+        fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, flags)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile_case, "launches": args.warmup + args.steps}))
 

@@ -45,12 +45,11 @@ extern "C" fe_status fe_apply(const fe_mesh* m, fe_op op, fe_prec prec, const vo
   FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
   const bool native = (flags & FE_NATIVE_F64) && prec == FE_F64;
   FE_TRY(fe_ensure_geometry(m, prec, native));
-  ApplyLaunch L{m, (int)op, x, y, (cudaStream_t)stream, nullptr};
+  ApplyLaunch L{m, (int)op, x, y, (cudaStream_t)stream, nullptr, (flags & FE_ASSEMBLE) != 0};
   if (prec == FE_F64)
     FE_TRY(native ? fe_launch_apply_f64native(L) : fe_launch_apply_f64dw(L));
   else
     FE_TRY(fe_launch_apply_f32(L));
-  if (flags & FE_ASSEMBLE) FE_TRY(fe_launch_dss(m, prec, y, (cudaStream_t)stream));
   return FE_OK;
 }
 

@@ -171,6 +171,86 @@ struct ApplyArgs {
 enum { GEOM_STORED_K = 0, GEOM_AFFINE_K = 2 };
 
 // ---------------------------------------------------------------------------------------------
+// Assembled applies (FE_ASSEMBLE): a CTA owns a BX x BY brick of cells in one z-layer and sums the
+// copies on the x- and y-interfaces inside the brick in shared memory before it stores y (the
+// fused part of the structured DSS of Sec. 4.1); the DSS passes that follow only visit the
+// interfaces between bricks (and all z-interfaces).  Every node has at most one copy pair per
+// axis, and the per-axis pair sums commute, so the order of the intra- and inter-brick sums does
+// not change the assembled value.
+// ---------------------------------------------------------------------------------------------
+template <int N>
+struct Brick;
+template <> struct Brick<2> { static constexpr int BX = 8, BY = 8; };
+template <> struct Brick<3> { static constexpr int BX = 7, BY = 4; };
+template <> struct Brick<4> { static constexpr int BX = 4, BY = 4; };
+template <> struct Brick<5> { static constexpr int BX = 5, BY = 2; };
+template <> struct Brick<6> { static constexpr int BX = 3, BY = 2; };
+template <> struct Brick<7> { static constexpr int BX = 2, BY = 2; };
+template <> struct Brick<8> { static constexpr int BX = 2, BY = 2; };
+
+struct CellPos {
+  long long cell;
+  int cx, cy, cz;
+  bool active;
+};
+
+// Cell of tile slot cl.  Unfused: cells cell0 + cl (below ncells).  Fused: cell0 is the brick
+// index over (bricks along x, bricks along y, z-layers).
+template <int N, bool FUSE, class A>
+__device__ __forceinline__ CellPos cell_pos(const A& a, long long cell0, int cl) {
+  CellPos c;
+  if constexpr (FUSE) {  // brick index < 2^31: 32-bit index arithmetic
+    constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
+    const unsigned nbx = (unsigned)(a.mx + BX - 1) / BX, nby = (unsigned)(a.my + BY - 1) / BY;
+    const unsigned b = (unsigned)cell0, rb = b / nbx;
+    c.cx = (int)(b - rb * nbx) * BX + cl % BX;
+    c.cy = (int)(rb % nby) * BY + cl / BX;
+    c.cz = (int)(rb / nby);
+    c.active = cl < BX * BY && c.cx < a.mx && c.cy < a.my;
+    c.cell = ((long long)c.cz * a.my + c.cy) * a.mx + c.cx;
+  } else {  // cell coordinates only where the Dirichlet masks need them (64-bit divisions)
+    c.cell = cell0 + cl;
+    c.active = cl < Cfg<N>::CPB && c.cell < a.ncells;
+    c.cx = c.cy = c.cz = 0;
+    if (a.dirichlet && c.active) {
+      c.cx = (int)(c.cell % a.mx);
+      c.cy = (int)((c.cell / a.mx) % a.my);
+      c.cz = (int)(c.cell / ((long long)a.mx * a.my));
+    }
+  }
+  return c;
+}
+
+// Intra-brick interface sums on the output tile s (all threads of the CTA call it).  x-faces:
+// (slot, i = n-1) + (slot+1, i = 0) at (j, k) = (la, lb); y-faces: (slot, j = n-1) +
+// (slot+BX, j = 0) at (i, k) = (la, lb).
+template <int N, class V, class A>
+__device__ __forceinline__ void brick_sums(const Sm<V>& s, int cb, int cl, int la, int lb,
+                                           const A& a, long long cell0) {
+  using C = Cfg<N>;
+  constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
+  const int dx = cl % BX, dy = cl / BX;
+  const int mx = a.mx, my = a.my;
+  const CellPos c = cell_pos<N, true>(a, cell0, cl);  // recomputed: nothing held across sweeps
+  if (c.active && dx < BX - 1 && c.cx + 1 < mx) {
+    const int eL = cb + lb * C::PS + la * C::RS + (N - 1);
+    const int eR = cb + C::CS + lb * C::PS + la * C::RS;
+    const V v = NT<V>::add(s.get(eL), s.get(eR));
+    s.put(eL, v);
+    s.put(eR, v);
+  }
+  __syncthreads();
+  if (c.active && dy < BY - 1 && c.cy + 1 < my) {
+    const int eL = cb + lb * C::PS + (N - 1) * C::RS + la;
+    const int eR = cb + BX * C::CS + lb * C::PS + la;
+    const V v = NT<V>::add(s.get(eL), s.get(eR));
+    s.put(eL, v);
+    s.put(eR, v);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
 // High degrees: the same sweeps with the output index of every 1D contraction as a run-time loop.
 // Fully unrolled n x n contractions in double-word arithmetic outgrow the instruction cache from
 // n ~ 6 on (the unrolled kernel then waits on instruction fetch); here each sweep is one unrolled
@@ -191,7 +271,7 @@ __device__ __forceinline__ void sweep_rolled(const EO<N, V>& M, const V (&in)[N]
   eo_line<N, V, SIG, true>(M, in, [&](int q, V v) { s.put(base + q * stride, v); });
 }
 
-template <int N, class V, int OP, int GEOM>
+template <int N, class V, int OP, int GEOM, bool FUSE>
 __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
                                                    long long cell0, unsigned char* smraw,
                                                    int tile_stride) {
@@ -208,17 +288,16 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
   const int lt = t - cl * N2;
   const int la = lt % N, lb = lt / N;
   const int cb = cl * C::CS;
-  const long long cell = cell0 + cl;
-  const bool active = cl < C::CPB && cell < a.ncells;
+  const CellPos pos = cell_pos<N, FUSE>(a, cell0, cl);
+  const long long cell = pos.cell;
+  const bool active = pos.active;
   const long long gbase = cell * N3;
   // line starts in the tile: x-line (j=la, k=lb), y-line (i=la, k=lb), z-line (i=la, j=lb)
   const int bx = cb + lb * PS + la * RS, by = cb + lb * PS + la, bz = cb + lb * RS + la;
 
   bool bnd_line = false, bnd_k0 = false, bnd_k1 = false;
   if (a.dirichlet && active) {
-    const int cx = (int)(cell % a.mx);
-    const int cy = (int)((cell / a.mx) % a.my);
-    const int cz = (int)(cell / ((long long)a.mx * a.my));
+    const int cx = pos.cx, cy = pos.cy, cz = pos.cz;
     bnd_line = (cx == 0 && la == 0) || (cx == a.mx - 1 && la == N - 1) || (cy == 0 && lb == 0) ||
                (cy == a.my - 1 && lb == N - 1);
     bnd_k0 = (cz == 0);
@@ -334,6 +413,7 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
   load_line(s0, by, RS, in);
   sweep_rolled<N, V, 1>(tab.eVT, in, s0, by, RS);
   __syncthreads();
+  if constexpr (FUSE) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
   if (active) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -348,12 +428,12 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
 // threads.  Threads beyond that (a CTA wider than the tile, as in the batched persistent kernel)
 // work on a spare slot of the tile that nobody reads and still reach every barrier; the caller
 // then sizes each array tile_stride = TILE + CS.
-template <int N, class V, int OP, int GEOM>
+template <int N, class V, int OP, int GEOM, bool FUSE = false>
 __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
                                             long long cell0, unsigned char* smraw,
                                             int tile_stride) {
   if constexpr (N >= FE_ROLL_MINN) {
-    apply_cells_rolled<N, V, OP, GEOM>(a, tab, cell0, smraw, tile_stride);
+    apply_cells_rolled<N, V, OP, GEOM, FUSE>(a, tab, cell0, smraw, tile_stride);
     return;
   }
   using T = NT<V>;
@@ -369,17 +449,16 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   const int lt = t - cl * N2;
   const int la = lt % N, lb = lt / N;  // line coordinates (a, b) of this thread
   const int cb = cl * C::CS;           // this cell's offset in the tile
-  const long long cell = cell0 + cl;
-  const bool active = cl < C::CPB && cell < a.ncells;
+  const CellPos pos = cell_pos<N, FUSE>(a, cell0, cl);
+  const long long cell = pos.cell;
+  const bool active = pos.active;
   const long long gbase = cell * N3;
 
   // Dirichlet masks of this thread's z-line (i = la, j = lb)
   bool bnd_line = false;  // the whole z-line lies on the x- or y-boundary
   bool bnd_k0 = false, bnd_k1 = false;
   if (a.dirichlet && active) {
-    const int cx = (int)(cell % a.mx);
-    const int cy = (int)((cell / a.mx) % a.my);
-    const int cz = (int)(cell / ((long long)a.mx * a.my));
+    const int cx = pos.cx, cy = pos.cy, cz = pos.cz;
     bnd_line = (cx == 0 && la == 0) || (cx == a.mx - 1 && la == N - 1) || (cy == 0 && lb == 0) ||
                (cy == a.my - 1 && lb == N - 1);
     bnd_k0 = (cz == 0);
@@ -530,6 +609,7 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   __syncthreads();
   tile_sweep<N, V, 1, 1>(s0, cb, la, lb, tab.eVT);
   __syncthreads();
+  if constexpr (FUSE) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
   if (active) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -540,13 +620,14 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   }
 }
 
-template <int N, class V, int OP, int GEOM>
+template <int N, class V, int OP, int GEOM, bool FUSE>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
     k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.skip && *(volatile const int*)a.skip) return;  // uniform over the grid
-  apply_cells<N, V, OP, GEOM>(a.c, a.tab, a.c.cell_base + (long long)blockIdx.x * Cfg<N>::CPB, smraw,
-                              Cfg<N>::TILE);
+  const long long cell0 =
+      FUSE ? (long long)blockIdx.x : a.c.cell_base + (long long)blockIdx.x * Cfg<N>::CPB;
+  apply_cells<N, V, OP, GEOM, FUSE>(a.c, a.tab, cell0, smraw, Cfg<N>::TILE);
 }
 
 template <int N, class V>

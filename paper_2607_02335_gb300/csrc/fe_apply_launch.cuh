@@ -53,19 +53,29 @@ Tab1D<N, V> make_tab(const HostTab& h) {
   return t;
 }
 
-template <int N, class V, int OP, int GEOM>
+template <int N, class V, int OP, int GEOM, bool FUSE = false>
 static fe_status launch_one(const ApplyArgs<N, V>& a, cudaStream_t st) {
   using C = Cfg<N>;
   const size_t smem = apply_smem_bytes<N, V>(OP);
-  auto kern = k_apply<N, V, OP, GEOM>;
-  static bool attr_done = false;  // one attribute call per instantiation (and device)
-  if (!attr_done) {
+  auto kern = k_apply<N, V, OP, GEOM, FUSE>;
+  static bool attr_done[64] = {};  // one attribute call per instantiation and device
+  int dev = 0;
+  FE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 64 || !attr_done[dev]) {
     FE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
             "apply smem attribute");
-    attr_done = true;
+    if (dev >= 0 && dev < 64) attr_done[dev] = true;
   }
-  const long long blocks = (a.c.ncells - a.c.cell_base + C::CPB - 1) / C::CPB;
-  if (blocks > 0) kern<<<(unsigned)blocks, C::THREADS, smem, st>>>(a);
+  long long blocks;
+  int threads = C::THREADS;
+  if constexpr (FUSE) {
+    constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
+    blocks = (long long)((a.c.mx + BX - 1) / BX) * ((a.c.my + BY - 1) / BY) * a.c.mz;
+    threads = BX * BY * C::N2;
+  } else {
+    blocks = (a.c.ncells - a.c.cell_base + C::CPB - 1) / C::CPB;
+  }
+  if (blocks > 0) kern<<<(unsigned)blocks, threads, smem, st>>>(a);
   return fe_cuda_check(cudaGetLastError(), "apply kernel launch");
 }
 
@@ -125,10 +135,35 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
   a.c.aff[2] = fe_cast<V>(det / (hz * hz));
   a.c.aff[3] = fe_cast<V>(det);
   a.tab = make_tab<N, V>(m->tab);
-  if (m->d.geom_mode == FE_GEOM_RECOMPUTE)
-    return L.op == FE_LAPLACE ? launch_recompute<N, V, FE_LAPLACE>(a, L, xyz, scratch)
-                              : launch_recompute<N, V, FE_MASS>(a, L, xyz, scratch);
+  constexpr int PREC = sizeof(typename NT<V>::SV) == 8 ? FE_F64 : FE_F32;
+  if (m->d.geom_mode == FE_GEOM_RECOMPUTE) {
+    FE_TRY((L.op == FE_LAPLACE ? launch_recompute<N, V, FE_LAPLACE>(a, L, xyz, scratch)
+                               : launch_recompute<N, V, FE_MASS>(a, L, xyz, scratch)));
+    return L.assemble ? fe_launch_dss(m, PREC, L.y, L.st) : FE_OK;
+  }
   const bool affine = m->d.geom_mode == FE_GEOM_AFFINE;
+// Assembled applies sum the intra-brick interfaces in the kernel up to n = FE_FUSE_MAXN.  Above it
+// the bricks hold fewer cells than the unfused tile (n = 6, 7) or the kernel needs more
+// registers, and the measured assembled time was no better than apply + full DSS.
+#ifndef FE_FUSE_MAXN
+#define FE_FUSE_MAXN 4
+#endif
+  if (L.assemble && N > FE_FUSE_MAXN) {
+    FE_TRY((L.op == FE_LAPLACE ? (affine ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K>(a, L.st)
+                                         : launch_one<N, V, FE_LAPLACE, GEOM_STORED_K>(a, L.st))
+                               : (affine ? launch_one<N, V, FE_MASS, GEOM_AFFINE_K>(a, L.st)
+                                         : launch_one<N, V, FE_MASS, GEOM_STORED_K>(a, L.st))));
+    return fe_launch_dss(m, PREC, L.y, L.st);
+  }
+  if (L.assemble) {  // brick-fused x/y sums, then the DSS passes between bricks
+    if (L.op == FE_LAPLACE)
+      FE_TRY(affine ? (launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K, true>(a, L.st))
+                    : (launch_one<N, V, FE_LAPLACE, GEOM_STORED_K, true>(a, L.st)));
+    else
+      FE_TRY(affine ? (launch_one<N, V, FE_MASS, GEOM_AFFINE_K, true>(a, L.st))
+                    : (launch_one<N, V, FE_MASS, GEOM_STORED_K, true>(a, L.st)));
+    return fe_launch_dss_strided(m, PREC, L.y, Brick<N>::BX, Brick<N>::BY, L.st);
+  }
   if (L.op == FE_LAPLACE)
     return affine ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K>(a, L.st)
                   : launch_one<N, V, FE_LAPLACE, GEOM_STORED_K>(a, L.st);

@@ -344,6 +344,7 @@ struct ApplyLaunch {
   void* y;
   cudaStream_t st;
   const int* skip = nullptr;  // optional device flag that turns the launch into a no-op
+  bool assemble = false;      // FE_ASSEMBLE: the launcher also runs the DSS on y
 };
 fe_status fe_launch_apply_f64dw(const ApplyLaunch& a);
 fe_status fe_launch_apply_f64native(const ApplyLaunch& a);
@@ -351,6 +352,10 @@ fe_status fe_launch_apply_f32(const ApplyLaunch& a);
 
 // dss / vectors (fe_dss.cu)
 fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st);
+// DSS passes of an apply whose kernel already summed the x- and y-interfaces inside bricks of
+// bx x by cells: all z-interfaces, then the y- and x-interfaces between bricks
+fe_status fe_launch_dss_strided(const fe_mesh* m, int prec, void* v, int bx, int by,
+                                cudaStream_t st);
 fe_status fe_launch_diag(const fe_mesh* m, int op, double* d, cudaStream_t st);
 fe_status fe_launch_pairing(const fe_mesh* m, int prec, const void* a, const void* b,
                             double* out, cudaStream_t st);

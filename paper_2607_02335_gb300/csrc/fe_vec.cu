@@ -12,10 +12,13 @@
 // because each pass sees the partial sums of the previous one, edge and vertex copies are
 // assembled as a by-product.
 // ---------------------------------------------------------------------------------------------
+// stride s > 1 (x and y only): just the interfaces whose left cell index is s-1 mod s, the
+// boundaries between bricks of s cells along that axis (nb = (m-1)/s of them per line)
 template <class S>
-__global__ void k_dss_pass(S* __restrict__ v, int axis, int n, int mx, int my, int mz,
+__global__ void k_dss_pass(S* __restrict__ v, int axis, int n, int mx, int my, int mz, int stride,
                            long long nwork) {
   const int p = n - 1, n2 = n * n, n3 = n2 * n;
+  const int nbx = (mx - 1) / stride, nby = (my - 1) / stride;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nwork;
        e += (long long)gridDim.x * blockDim.x) {
     const int f = (int)(e % n2);
@@ -24,13 +27,14 @@ __global__ void k_dss_pass(S* __restrict__ v, int axis, int n, int mx, int my, i
     long long L, R;
     int locL, locR;
     if (axis == 0) {  // faces normal to x
-      const long long cxL = q % (mx - 1), r = q / (mx - 1);
-      L = r * mx + cxL;  // r = cz*my + cy
+      const long long u = q % nbx, r = q / nbx;
+      L = r * mx + (u * stride + stride - 1);  // r = cz*my + cy
       R = L + 1;
       locL = (fb * n + fa) * n + p;
       locR = (fb * n + fa) * n + 0;
     } else if (axis == 1) {  // faces normal to y
-      const long long cx = q % mx, r = q / mx, cyL = r % (my - 1), cz = r / (my - 1);
+      const long long cx = q % mx, r = q / mx, u = r % nby, cz = r / nby;
+      const long long cyL = u * stride + stride - 1;
       L = (cz * my + cyL) * mx + cx;
       R = L + mx;
       locL = (fb * n + p) * n + fa;
@@ -57,23 +61,35 @@ static unsigned grid_cap(long long n, int threads) {
 }
 
 template <class S>
-static fe_status dss_t(const fe_mesh* m, S* v, cudaStream_t st) {
+static fe_status dss_t(const fe_mesh* m, S* v, int sx, int sy, cudaStream_t st) {
   const int n = m->n, n2 = n * n;
   const int mx = m->d.mx, my = m->d.my, mz = m->d.mz;
-  const long long work[3] = {(long long)(mx - 1) * my * mz * n2, (long long)mx * (my - 1) * mz * n2,
+  const int stride[3] = {sx, sy, 1};
+  const long long work[3] = {(long long)((mx - 1) / sx) * my * mz * n2,
+                             (long long)mx * ((my - 1) / sy) * mz * n2,
                              (long long)mx * my * (mz - 1) * n2};
   for (int axis = 2; axis >= 0; --axis) {  // z, y, x
     if (work[axis] <= 0) continue;
-    k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, mz, work[axis]);
+    k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, mz, stride[axis],
+                                                             work[axis]);
   }
   return fe_cuda_check(cudaGetLastError(), "dss launch");
 }
 
-fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st) {
-  if (prec == FE_F64) return dss_t<double>(m, (double*)v, st);
-  if (prec == FE_F32) return dss_t<float>(m, (float*)v, st);
+fe_status fe_launch_dss_strided(const fe_mesh* m, int prec, void* v, int bx, int by,
+                                cudaStream_t st) {
+  if (bx < 1 || by < 1) {
+    fe_set_error("dss: bad brick %d x %d", bx, by);
+    return FE_ERR_INVALID;
+  }
+  if (prec == FE_F64) return dss_t<double>(m, (double*)v, bx, by, st);
+  if (prec == FE_F32) return dss_t<float>(m, (float*)v, bx, by, st);
   fe_set_error("dss: unsupported precision %d", prec);
   return FE_ERR_INVALID;
+}
+
+fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st) {
+  return fe_launch_dss_strided(m, prec, v, 1, 1, st);
 }
 
 // ---------------------------------------------------------------------------------------------

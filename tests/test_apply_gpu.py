@@ -90,6 +90,37 @@ def test_assembled_deformed_dirichlet_vs_csr(fe, p, m):
         assert np.array_equal(hi, lo)
 
 
+# (degree, mesh): several bricks along x and y with a ragged last brick, for every degree
+FUSED = [(1, (17, 10, 3)), (2, (15, 9, 2)), (3, (9, 10, 3)), (4, (11, 5, 2)), (5, (7, 5, 2)),
+         (6, (5, 5, 2)), (7, (5, 3, 2))]
+
+
+@pytest.mark.parametrize("p,m", FUSED)
+def test_fused_assembly_equals_apply_then_dss(fe, p, m):
+    """FE_ASSEMBLE sums the x/y interfaces inside each CTA's brick of cells and leaves the rest to
+    the DSS passes between bricks; the result must equal the unassembled apply followed by the
+    full structured DSS (same sums in another order: rounding-level differences only)."""
+    for dirichlet in (False, True):
+        gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=dirichlet)
+        x = gm.gather(S.primal_unique(m, p, seed=6, dirichlet=dirichlet))
+        for op in (fe.FE_LAPLACE, fe.FE_MASS):
+            yf = to_host(gm.apply(x, op=op, flags=fe.FE_ASSEMBLE))
+            yr = to_host(gm.dss(gm.apply(x, op=op)))
+            assert rel_max_err(yf, yr) <= 1e-14, (p, op, dirichlet)
+            yf32 = to_host(gm.apply(x.float(), op=op, prec=fe.FE_F32, flags=fe.FE_ASSEMBLE))
+            yr32 = to_host(gm.dss(gm.apply(x.float(), op=op, prec=fe.FE_F32), prec=fe.FE_F32))
+            assert rel_max_err(yf32, yr32) <= 1e-6, (p, op, dirichlet, "fp32")
+            yn = to_host(gm.apply(x, op=op, flags=fe.FE_ASSEMBLE | fe.FE_NATIVE_F64))
+            assert rel_max_err(yn, yr) <= 1e-12, (p, op, dirichlet, "native")
+    # against the oracle on the Dirichlet mesh
+    om = oracle_mesh(m, p, amp=0.1, dirichlet=True)
+    xg = S.primal_unique(m, p, seed=6, dirichlet=True)
+    yref = O.gather(om, O.apply_dirichlet_csr(om, O.assemble_csr(om, O.LAPLACE), xg))
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=True)
+    y = to_host(gm.apply(gm.gather(xg), flags=fe.FE_ASSEMBLE))
+    assert rel_max_err(y, yref) <= TOL64
+
+
 def test_dss_multiplicity_and_random(fe):
     m, p = (3, 4, 2), 3
     om = oracle_mesh(m, p)
