@@ -206,14 +206,20 @@ def kernel_source_sha():
 
 
 def committed_traffic():
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """dram read + write bytes per launch of the roofline kernel from the committed ncu summary,
+    or None when the kernel sources changed after the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
+    d = {}
     with open(path) as f:
-        d = json.load(f)
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                d[k.strip()] = v.strip()
     if d.get("source_sha") != kernel_source_sha():
         return None
-    return d.get("bytes_per_launch")
+    return int(d["bytes_per_launch"]) if "bytes_per_launch" in d else None
 
 
 def run_ours(args, rank, world):

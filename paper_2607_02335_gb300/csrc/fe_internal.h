@@ -35,8 +35,12 @@ __device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {  // requires |
   float e = __fsub_rn(b, __fsub_rn(s, a));
   return {s, e};
 }
-// unnormalised accumulator acc + c*v (hi part exact through TwoSum, low parts summed in float)
-__device__ __forceinline__ dw dw_mac(dw acc, dw c, dw v) {
+// unnormalised accumulator acc + c*v, 10 FP32 operations.  s = acc.h + p with p = fl(c.h v.h); of
+// the TwoSum error, acc.h's share t1 = acc.h - (s - bb) is exact (bb = s - acc.h), and p's share
+// p - bb plus the product error c.h v.h - p is c.h v.h - bb, one fma (a small value rounded once,
+// an error of order 2^-24 ulp(s)).  The low parts and cross products go in float.
+// The 12-operation form: exact product error and a full TwoSum, low parts summed in float.
+__device__ __forceinline__ dw dw_mac12(dw acc, dw c, dw v) {
   float p = __fmul_rn(c.h, v.h);
   float e = __fmaf_rn(c.h, v.h, -p);
   e = __fmaf_rn(c.h, v.l, e);
@@ -44,6 +48,19 @@ __device__ __forceinline__ dw dw_mac(dw acc, dw c, dw v) {
   dw s = dw_two_sum(acc.h, p);
   return {s.h, __fadd_rn(acc.l, __fadd_rn(s.l, e))};
 }
+#ifndef FE_MAC_V1
+__device__ __forceinline__ dw dw_mac(dw acc, dw c, dw v) {
+  const float p = __fmul_rn(c.h, v.h);
+  const float s = __fadd_rn(acc.h, p);
+  const float bb = __fsub_rn(s, acc.h);
+  const float t1 = __fsub_rn(acc.h, __fsub_rn(s, bb));
+  const float t2 = __fmaf_rn(c.h, v.h, -bb);
+  const float x = __fmaf_rn(c.l, v.h, __fmaf_rn(c.h, v.l, acc.l));
+  return {s, __fadd_rn(__fadd_rn(t1, t2), x)};
+}
+#else
+__device__ __forceinline__ dw dw_mac(dw acc, dw c, dw v) { return dw_mac12(acc, c, v); }
+#endif
 // c*v as an unnormalised pair (the first term of a dot product: no TwoSum with a zero accumulator)
 __device__ __forceinline__ dw dw_prod(dw c, dw v) {
   float p = __fmul_rn(c.h, v.h);
@@ -69,6 +86,14 @@ __device__ __forceinline__ dw dw_mul(dw a, dw b) {
   return dw_fast_two_sum(p, e);
 }
 
+// Out-of-range paths of the conversions below, kept out of line: inlined, the compiler
+// predicates them into every call, and their conversions and FP64 adds then occupy the slow FP64
+// pipe even though they never take effect.
+static __device__ __noinline__ dw dw_from_double_slow(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+
 // binary64 -> double-word by bit manipulation on the integer pipe (FP64<->FP32 conversions run
 // at the FP64 rate on GB300).  hi = x truncated to 24 significant bits, lo = the remaining 29
 // bits rounded to float.  Exact range 2^-74 <= |x| < 2^128; other values take the FP64 path.
@@ -88,9 +113,7 @@ __device__ __forceinline__ dw dw_from_double(double x) {
     lo = __uint_as_float(__float_as_uint(lo) | sign);
     return {hi, lo};
   }
-  float hi = __double2float_rn(x);
-  float lo = __double2float_rn(x - (double)hi);
-  return {hi, lo};
+  return dw_from_double_slow(x);
 }
 // float -> binary64 exactly for normal floats by bit manipulation; zero and subnormal -> 0.
 __device__ __forceinline__ double f2d_bits(float f) {
@@ -106,6 +129,7 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return (double)f;  // inf / nan
 }
 __device__ __forceinline__ double dw_to_double(dw a) { return f2d_bits(a.h) + f2d_bits(a.l); }
+static __device__ __noinline__ double dw_to_double_slow(dw a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 
 // binary64 of h + l on the integer and FP32 pipes (no FP64 add): after a TwoSum |l| <= ulp(h)/2,
 // so l is at most 2^28 units of 2^(e-52), e the exponent of h; those units, truncated to an
@@ -117,7 +141,8 @@ __device__ __forceinline__ double dw_to_double_int(dw a) {
   const dw s = dw_two_sum(a.h, a.l);
   const unsigned hb = __float_as_uint(s.h);
   const unsigned e8 = (hb >> 23) & 0xFFu;
-  if (e8 - 52u > 202u) return s.h == 0.0f ? 0.0 : dw_to_double(s);
+  if (s.h == 0.0f) return 0.0;
+  if (e8 - 52u > 202u) return dw_to_double_slow(s);
   const unsigned long long dh = ((unsigned long long)(hb & 0x80000000u) << 32) |
                                 ((unsigned long long)(e8 + 896u) << 52) |
                                 ((unsigned long long)(hb & 0x7FFFFFu) << 29);
@@ -146,6 +171,7 @@ struct NT<double> {
   using GV = double;
   __device__ static __forceinline__ double zero() { return 0.0; }
   __device__ static __forceinline__ double mac(double a, double c, double v) { return fma(c, v, a); }
+  __device__ static __forceinline__ double mac12(double a, double c, double v) { return fma(c, v, a); }
   __device__ static __forceinline__ double prod(double c, double v) { return c * v; }
   __device__ static __forceinline__ double addk(double a, double b) { return a + b; }
   __device__ static __forceinline__ double subk(double a, double b) { return a - b; }
@@ -168,6 +194,7 @@ struct NT<float> {
   using GV = float;
   __device__ static __forceinline__ float zero() { return 0.0f; }
   __device__ static __forceinline__ float mac(float a, float c, float v) { return fmaf(c, v, a); }
+  __device__ static __forceinline__ float mac12(float a, float c, float v) { return fmaf(c, v, a); }
   __device__ static __forceinline__ float prod(float c, float v) { return c * v; }
   __device__ static __forceinline__ float addk(float a, float b) { return a + b; }
   __device__ static __forceinline__ float subk(float a, float b) { return a - b; }
@@ -190,6 +217,8 @@ struct NT<dw> {
   using GV = float2;
   __device__ static __forceinline__ dw zero() { return {0.0f, 0.0f}; }
   __device__ static __forceinline__ dw mac(dw a, dw c, dw v) { return dw_mac(a, c, v); }
+  // the 12-operation form, for the geometry terms (their error reaches every output)
+  __device__ static __forceinline__ dw mac12(dw a, dw c, dw v) { return dw_mac12(a, c, v); }
   __device__ static __forceinline__ dw prod(dw c, dw v) { return dw_prod(c, v); }
   // unnormalised sums (TwoSum of the high parts, low parts added in float): the error stays at
   // the double-word level of the operands, which is all the following products need

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(GeoCfg<N>::THREADS)
   for (int c = 0; c < 3; ++c) {
     V acc = T::zero();
 #pragma unroll
-    for (int r = 0; r < N; ++r) acc = T::mac(acc, a.tab.V_[i][r], s0[c * N3 + (k * N + j) * N + r]);
+    for (int r = 0; r < N; ++r)
+      acc = T::mac12(acc, a.tab.V_[i][r], s0[c * N3 + (k * N + j) * N + r]);
     s1[c * N3 + t] = T::keep(acc);
   }
   __syncthreads();
@@ -72,7 +73,8 @@ __global__ void __launch_bounds__(GeoCfg<N>::THREADS)
   for (int c = 0; c < 3; ++c) {
     V acc = T::zero();
 #pragma unroll
-    for (int r = 0; r < N; ++r) acc = T::mac(acc, a.tab.V_[j][r], s1[c * N3 + (k * N + r) * N + i]);
+    for (int r = 0; r < N; ++r)
+      acc = T::mac12(acc, a.tab.V_[j][r], s1[c * N3 + (k * N + r) * N + i]);
     s0[c * N3 + t] = T::keep(acc);
   }
   __syncthreads();
@@ -80,7 +82,8 @@ __global__ void __launch_bounds__(GeoCfg<N>::THREADS)
   for (int c = 0; c < 3; ++c) {
     V acc = T::zero();
 #pragma unroll
-    for (int r = 0; r < N; ++r) acc = T::mac(acc, a.tab.V_[k][r], s0[c * N3 + (r * N + j) * N + i]);
+    for (int r = 0; r < N; ++r)
+      acc = T::mac12(acc, a.tab.V_[k][r], s0[c * N3 + (r * N + j) * N + i]);
     s1[c * N3 + t] = T::fin(acc);
   }
   __syncthreads();
@@ -91,9 +94,9 @@ __global__ void __launch_bounds__(GeoCfg<N>::THREADS)
     V d0 = T::zero(), d1 = T::zero(), d2 = T::zero();
 #pragma unroll
     for (int r = 0; r < N; ++r) {
-      d0 = T::mac(d0, a.tab.D_[i][r], s1[c * N3 + (k * N + j) * N + r]);
-      d1 = T::mac(d1, a.tab.D_[j][r], s1[c * N3 + (k * N + r) * N + i]);
-      d2 = T::mac(d2, a.tab.D_[k][r], s1[c * N3 + (r * N + j) * N + i]);
+      d0 = T::mac12(d0, a.tab.D_[i][r], s1[c * N3 + (k * N + j) * N + r]);
+      d1 = T::mac12(d1, a.tab.D_[j][r], s1[c * N3 + (k * N + r) * N + i]);
+      d2 = T::mac12(d2, a.tab.D_[k][r], s1[c * N3 + (r * N + j) * N + i]);
     }
     J[c][0] = T::fin(d0);
     J[c][1] = T::fin(d1);
