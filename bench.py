@@ -34,6 +34,7 @@ AMP = 0.1
 METRIC = "Operator-apply GDoF/s (unique DoFs, FP64, FE_ASSEMBLE) over the Q2/Q3/Q7 sweep"
 UNIT = "GDoF/s"
 GEO_BYTES = {0: 48, 1: 8}  # stored geometry bytes per cell-wise DoF: Laplace 6 doubles, mass 1
+FP64_PIPE_TFLOPS = 0.98   # FP64 FMA rate probed on a pool GB300 (0.49 T FMA/s), for context
 
 
 def parse():
@@ -279,34 +280,52 @@ def run_ours(args, rank, world):
     ms_per_step = total_ms / args.steps
     value = units_per_step * world * args.steps / (total_ms * 1e-3) / 1e9
 
-    # per-case breakdown: assembled apply and the volumetric kernel alone (flushed, averaged)
+    # per-case breakdown: assembled apply and the volumetric kernel alone; 5 warm-ups, then the
+    # median of 20 reps with L2 flushed before each, and of 20 reps without the flush
     peak, peak_kind = load_peaks()
-    reps = max(5, min(args.steps, 20))
+    reps = 20
     per_case = []
+
+    def rep_median(gm, x, y, op, flags, flushed):
+        for _ in range(5):
+            fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, flags, stream)
+        ts = []
+        for _ in range(reps):
+            if flushed:
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, flags, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
     for gm, x, y, op, p, m in cases:
         res = {}
         for flags, key in ((fe.FE_ASSEMBLE, "assembled_ms"), (0, "volumetric_ms")):
-            tot = 0.0
-            for _ in range(reps):
-                flush.fill_(1.0)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, flags, stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                tot += e0.elapsed_time(e1)
-            res[key] = tot / reps
-        ncw = gm.cellwise_len
+            res[key] = rep_median(gm, x, y, op, flags, True)
+            res[key + "_unflushed"] = rep_median(gm, x, y, op, flags, False)
+        ncw, n = gm.cellwise_len, p + 1
         alg_bytes = ncw * (16 + GEO_BYTES[op])
         vol_gbs = alg_bytes / (res["volumetric_ms"] * 1e-3) / 1e9
+        # FP64 flops per cell-wise DoF of the plain formulation (no even-odd): Laplace 24n+17,
+        # mass 12n+1; the FP64-equivalent rate against the FP64 pipe's measured FMA rate
+        flops = ncw * ((24 * n + 17) if op == fe.FE_LAPLACE else (12 * n + 1))
+        fp64_tf = flops / (res["volumetric_ms"] * 1e-3) / 1e12
         per_case.append({
             "op": "laplace" if op == fe.FE_LAPLACE else "mass", "degree": p, "cells": f"{m}^3",
             "cellwise_dofs": ncw, "unique_dofs": gm.unique_dofs,
             "assembled_ms": round(res["assembled_ms"], 4), "volumetric_ms": round(res["volumetric_ms"], 4),
+            "assembled_ms_unflushed": round(res["assembled_ms_unflushed"], 4),
+            "volumetric_ms_unflushed": round(res["volumetric_ms_unflushed"], 4),
             "gdofs_unique_assembled": round(gm.unique_dofs / (res["assembled_ms"] * 1e-3) / 1e9, 3),
+            "gdofs_cellwise_assembled": round(ncw / (res["assembled_ms"] * 1e-3) / 1e9, 3),
             "gdofs_cellwise_volumetric": round(ncw / (res["volumetric_ms"] * 1e-3) / 1e9, 3),
             "volumetric_alg_bytes": alg_bytes, "volumetric_gbs": round(vol_gbs, 1),
             "volumetric_hbm_frac": round(vol_gbs / peak, 4),
+            "fp64_equiv_tflops": round(fp64_tf, 3),
+            "vs_fp64_pipe_peak": round(fp64_tf / FP64_PIPE_TFLOPS, 2),
         })
     dom = max(per_case, key=lambda c: c["volumetric_ms"])
     achieved = dom["volumetric_gbs"]
@@ -345,6 +364,7 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
         extras["geometry_recompute"] = recompute_geometry(fe, torch, sweep, per_case, flush, stream,
                                                           reps)
+        extras["reduced_precision_apply"] = reduced_precision_apply(fe, torch, flush, stream)
         extras["solve_mixed_vs_fp64"] = mixed_vs_fp64_solve(fe, torch)
         extras["batched"] = batched_solve(fe, torch, count=args.batch_count)
         extras["serving"] = {
@@ -386,6 +406,11 @@ def run_ours(args, rank, world):
         t_cpu, nu = smp.full_step_estimate()
         line["cpu_baseline"] = {"value": round(nu / t_cpu / 1e9, 6), "unit": UNIT, "cores": threads,
                                 "kind": "oracle", "sample": smp.describe()}
+        smp.threads = 1  # the same sample on one core, one pass
+        smp.reset()
+        smp.time_once()
+        t1, _ = smp.full_step_estimate()
+        line["cpu_baseline"]["value_1core"] = round(nu / t1 / 1e9, 6)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -433,6 +458,40 @@ def recompute_geometry(fe, torch, sweep, per_case, flush, stream, reps):
     return out
 
 
+def reduced_precision_apply(fe, torch, flush, stream, m=96, p=3, reps=10):
+    """Volumetric apply of the Q3 96^3 deformed mesh in the reduced-precision arithmetics of the
+    inner solves: FP32, and 16-bit operands with FP32 accumulation (16-bit metric)."""
+    from paper_2607_02335_gb300 import synth as S
+
+    peak, _ = load_peaks()
+    gm = fe.Mesh(m, p, deform_amp=AMP)
+    x = gm.gather(S.primal_unique(m, p, seed=0)).float()
+    y = gm.empty(fe.FE_F32)
+    out = []
+    for name, prec, gbytes in (("fp32", fe.FE_F32, 4), ("bf16_f32acc", fe.FE_BF16_F32ACC, 2),
+                               ("fp16_f32acc", fe.FE_F16_F32ACC, 2)):
+        for op in (fe.FE_LAPLACE, fe.FE_MASS):
+            fe.fe_apply(gm.handle, op, prec, x, y, 0, stream)
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fe.fe_apply(gm.handle, op, prec, x, y, 0, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = float(np.median(ts))
+            alg = gm.cellwise_len * (8 + (6 if op == fe.FE_LAPLACE else 1) * gbytes)
+            out.append({"arith": name, "op": "laplace" if op == fe.FE_LAPLACE else "mass",
+                        "case": f"Q{p} {m}^3", "volumetric_ms": round(ms, 4),
+                        "alg_bytes_per_cellwise_dof": alg // gm.cellwise_len,
+                        "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)})
+    del x, y
+    gm.close()
+    return out
+
+
 def mixed_vs_fp64_solve(fe, torch, m=64, p=3, rtol=1e-10):
     """Poisson -Laplace u = f, u = sin sin sin, Q3 on the deformed 64^3 mesh: Jacobi-PCG in FP64
     vs FP32 PCG under FP64 iterative refinement, both to a relative FP64 residual of 1e-10.
@@ -444,7 +503,9 @@ def mixed_vs_fp64_solve(fe, torch, m=64, p=3, rtol=1e-10):
            "cellwise_dofs": gm.cellwise_len}
     sols = {}
     variants = (("fp64", 0, False), ("mixed_fp32_in_fp64_ir", fe.FE_F32, False),
-                ("mixed_fp64_fcg_fp32_pcg_precond", fe.FE_F32, True))
+                ("mixed_fp64_fcg_fp32_pcg_precond", fe.FE_F32, True),
+                ("mixed_fp64_fcg_bf16_pcg_precond", fe.FE_BF16_F32ACC, True),
+                ("mixed_fp64_fcg_fp16_pcg_precond", fe.FE_F16_F32ACC, True))
     for name, mixed, flex in variants:
         for rep in range(2):
             x = torch.zeros_like(b)

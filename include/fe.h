@@ -52,7 +52,11 @@ typedef enum {
 typedef enum { FE_LAPLACE = 0, FE_MASS = 1 } fe_op;
 
 /* Arithmetic of a call.  FE_F64: double storage, FP64-accurate arithmetic (see FE_NATIVE_F64).
- * FE_F32: float storage and float arithmetic. */
+ * FE_F32: float storage and float arithmetic.  FE_BF16_F32ACC / FE_F16_F32ACC: float vectors, but
+ * every operand of a product in the contractions (the input, intermediate sweep values, the 1D
+ * matrices and the stored metric, kept in the 16-bit format scaled by a power of two) is rounded
+ * to bf16 / fp16 and the products accumulate in FP32 (Sec. 3.2's reduced-precision
+ * preconditioner; stored geometry only). */
 typedef enum { FE_F64 = 0, FE_F32 = 1, FE_BF16_F32ACC = 2, FE_F16_F32ACC = 3 } fe_prec;
 
 /* Geometry representation (Sec. 2.3 and Sec. 5.3: "per-quadrature-point Jacobians"):
@@ -109,7 +113,9 @@ fe_status fe_gather(const fe_mesh* mesh, const double* x_unique_host, double* x_
 /* Local operator apply (Sec. 3.1 "local operator"; Eq. (mass_operator) / (laplace_operator)
  * with per-quadrature-point geometry): y_K = A_K x_K for every cell K (dual, unassembled).
  * With FE_ASSEMBLE the structured DSS follows (Sec. 4.1): y = S(A x), continuous.  x and y must
- * not overlap.  prec FE_BF16_F32ACC / FE_F16_F32ACC return FE_ERR_INVALID (not provided). */
+ * not overlap.  x and y are float arrays for every prec but FE_F64.  FE_BF16_F32ACC /
+ * FE_F16_F32ACC need FE_GEOM_STORED (else FE_ERR_INVALID); their first call on a mesh builds the
+ * 16-bit metric from the FP64 one. */
 fe_status fe_apply(const fe_mesh* mesh, fe_op op, fe_prec prec, const void* x, void* y,
                    unsigned flags, void* stream);
 
@@ -162,13 +168,16 @@ fe_status fe_l2_error(const fe_mesh* mesh, int kind, const double* u, double* er
  * mixed = FE_F32, flexible = 0: FP64 iterative refinement (r = b - A x in FP64, x += d in FP64)
  * around an FP32 inner PCG solved to inner_rtol.  mixed = FE_F32, flexible = 1: FP64 FCG whose
  * (variable) preconditioner is the FP32 inner PCG solve, the reduced-precision preconditioner
- * that motivates FCG in Sec. 3.2.  The FP32 inner solve receives the residual assembled in FP64
+ * that motivates FCG in Sec. 3.2.  mixed = FE_BF16_F32ACC or FE_F16_F32ACC: the same schemes with
+ * the inner operator in 16-bit operands and FP32 accumulation (stored geometry only; inner
+ * vectors stay FP32).  The FP32 inner solve receives the residual assembled in FP64
  * and split evenly over the copies of each node.  b (dual) and x (primal, in/out) are device
  * arrays of cellwise_len doubles.  Synchronous: returns after the solve. */
 typedef struct {
   double rtol;       /* relative residual target */
   int maxit;         /* iteration cap (inner iterations in total for mixed) */
-  int mixed;         /* 0 = FP64, FE_F32 = FP32 inner solve under FP64 refinement */
+  int mixed;         /* 0 = FP64; FE_F32, FE_BF16_F32ACC, FE_F16_F32ACC = inner solve in that
+                        arithmetic under FP64 refinement */
   int flexible;      /* 1 = FCG beta */
   double inner_rtol; /* mixed only: relative reduction per inner solve (<= 0: 1e-2); an inner
                         solve also stops after 20 iterations without a 10% residual drop */

@@ -14,6 +14,8 @@ static fe_status check_vec(const fe_mesh* m, const void* p, const char* what) {
   return FE_OK;
 }
 
+// element size of the vectors of a call: double for FE_F64, float otherwise (the 16-bit operand
+// formats keep float vectors)
 static size_t elem_size(int prec) { return prec == FE_F64 ? sizeof(double) : sizeof(float); }
 
 extern "C" fe_status fe_apply(const fe_mesh* m, fe_op op, fe_prec prec, const void* x, void* y,
@@ -28,8 +30,13 @@ extern "C" fe_status fe_apply(const fe_mesh* m, fe_op op, fe_prec prec, const vo
     fe_set_error("fe_apply: unknown operator %d", (int)op);
     return FE_ERR_INVALID;
   }
-  if (prec != FE_F64 && prec != FE_F32) {
-    fe_set_error("fe_apply: precision %d not provided (FE_F64 and FE_F32 are)", (int)prec);
+  if (prec != FE_F64 && prec != FE_F32 && prec != FE_BF16_F32ACC && prec != FE_F16_F32ACC) {
+    fe_set_error("fe_apply: unknown precision %d", (int)prec);
+    return FE_ERR_INVALID;
+  }
+  const bool lowp = prec == FE_BF16_F32ACC || prec == FE_F16_F32ACC;
+  if (lowp && m->d.geom_mode != FE_GEOM_STORED) {
+    fe_set_error("fe_apply: 16-bit contractions need FE_GEOM_STORED geometry");
     return FE_ERR_INVALID;
   }
   if (flags & ~(FE_ASSEMBLE | FE_NATIVE_F64)) {
@@ -48,6 +55,8 @@ extern "C" fe_status fe_apply(const fe_mesh* m, fe_op op, fe_prec prec, const vo
   ApplyLaunch L{m, (int)op, x, y, (cudaStream_t)stream, nullptr, (flags & FE_ASSEMBLE) != 0};
   if (prec == FE_F64)
     FE_TRY(native ? fe_launch_apply_f64native(L) : fe_launch_apply_f64dw(L));
+  else if (lowp)
+    FE_TRY(fe_launch_apply_lowp(L, (int)prec));
   else
     FE_TRY(fe_launch_apply_f32(L));
   return FE_OK;

@@ -61,6 +61,23 @@ struct Sm<float> {
   __device__ __forceinline__ void put(int e, float v) const { p[e] = v; }
   static constexpr int BYTES = 4;
 };
+template <class W>
+struct Sm16 {  // 16-bit-operand values kept as floats
+  float* p;
+  __device__ __forceinline__ Sm16(unsigned char* base, int, int arr, int tile)
+      : p(reinterpret_cast<float*>(base) + (size_t)arr * tile) {}
+  __device__ __forceinline__ W get(int e) const { return {p[e]}; }
+  __device__ __forceinline__ void put(int e, W v) const { p[e] = v.v; }
+  static constexpr int BYTES = 4;
+};
+template <>
+struct Sm<bfv> : Sm16<bfv> {
+  using Sm16<bfv>::Sm16;
+};
+template <>
+struct Sm<hfv> : Sm16<hfv> {
+  using Sm16<hfv>::Sm16;
+};
 template <>
 struct Sm<dw> {  // hi and lo interleaved: one 64-bit shared-memory access per value
   float2* p;
@@ -158,7 +175,8 @@ struct CellArgs {
   long long geo_cell0;            // cell whose metric is geo[0] (a chunk's scratch in recompute mode)
   int mx, my, mz;
   int dirichlet;
-  V aff[4];  // affine mode: detJ/h_x^2, detJ/h_y^2, detJ/h_z^2, detJ
+  V aff[4];      // affine mode: detJ/h_x^2, detJ/h_y^2, detJ/h_z^2, detJ
+  float oscale;  // 16-bit operand types: 1 / (power-of-two scale of the stored metric)
 };
 
 template <int N, class V>
@@ -419,6 +437,7 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
     for (int k = 0; k < N; ++k) {
       V v = s0.get(bz + k * PS);
       if (masked(k)) v = T::zero();
+      if constexpr (T::LOWP) v.v *= a.oscale;
       T::store(a.y + gbase + k * N2 + lt, v);
     }
   }
@@ -615,6 +634,7 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
     for (int k = 0; k < N; ++k) {
       V v = s0.get(cb + zl<N>(la, lb, k));
       if (masked(k)) v = T::zero();
+      if constexpr (T::LOWP) v.v *= a.oscale;
       T::store(a.y + gbase + k * N2 + lt, v);
     }
   }

@@ -16,6 +16,14 @@ inline dw fe_cast<dw>(double v) {
   const float h = (float)v;
   return {h, (float)(v - (double)h)};
 }
+template <>
+inline bfv fe_cast<bfv>(double v) {  // round to nearest even bf16
+  return {__bfloat162float(__float2bfloat16_rn((float)v))};
+}
+template <>
+inline hfv fe_cast<hfv>(double v) {
+  return {__half2float(__float2half_rn((float)v))};
+}
 
 // even-odd form of M (tr: of M^T), from the FP64 tables
 template <int N, class V>
@@ -114,6 +122,18 @@ static fe_status launch_recompute(ApplyArgs<N, V> a, const ApplyLaunch& L,
   return FE_OK;
 }
 
+// the kernel of (operator, geometry mode); 16-bit operand types have stored geometry only
+template <int N, class V, bool FUSE>
+static fe_status launch_geom(const ApplyArgs<N, V>& a, int op, bool affine, cudaStream_t st) {
+  if constexpr (!NT<V>::LOWP) {
+    if (affine)
+      return op == FE_LAPLACE ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K, FUSE>(a, st)
+                              : launch_one<N, V, FE_MASS, GEOM_AFFINE_K, FUSE>(a, st);
+  }
+  return op == FE_LAPLACE ? launch_one<N, V, FE_LAPLACE, GEOM_STORED_K, FUSE>(a, st)
+                          : launch_one<N, V, FE_MASS, GEOM_STORED_K, FUSE>(a, st);
+}
+
 template <int N, class V>
 static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* geo,
                                 const typename NT<V>::GV* xyz, typename NT<V>::GV* scratch) {
@@ -135,11 +155,21 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
   a.c.aff[2] = fe_cast<V>(det / (hz * hz));
   a.c.aff[3] = fe_cast<V>(det);
   a.tab = make_tab<N, V>(m->tab);
+  a.c.oscale = 1.0f;
+  if constexpr (NT<V>::LOWP) {
+    if (m->d.geom_mode != FE_GEOM_STORED || !geo) {
+      fe_set_error("apply: 16-bit contractions need stored geometry");
+      return FE_ERR_INVALID;
+    }
+    a.c.oscale = 1.0f / m->gscale[L.op == FE_LAPLACE ? 0 : 1];
+  }
   constexpr int PREC = sizeof(typename NT<V>::SV) == 8 ? FE_F64 : FE_F32;
-  if (m->d.geom_mode == FE_GEOM_RECOMPUTE) {
-    FE_TRY((L.op == FE_LAPLACE ? launch_recompute<N, V, FE_LAPLACE>(a, L, xyz, scratch)
-                               : launch_recompute<N, V, FE_MASS>(a, L, xyz, scratch)));
-    return L.assemble ? fe_launch_dss(m, PREC, L.y, L.st) : FE_OK;
+  if constexpr (!NT<V>::LOWP) {
+    if (m->d.geom_mode == FE_GEOM_RECOMPUTE) {
+      FE_TRY((L.op == FE_LAPLACE ? launch_recompute<N, V, FE_LAPLACE>(a, L, xyz, scratch)
+                                 : launch_recompute<N, V, FE_MASS>(a, L, xyz, scratch)));
+      return L.assemble ? fe_launch_dss(m, PREC, L.y, L.st) : FE_OK;
+    }
   }
   const bool affine = m->d.geom_mode == FE_GEOM_AFFINE;
 // Assembled applies sum the intra-brick interfaces in the kernel up to n = FE_FUSE_MAXN.  Above it
@@ -148,27 +178,14 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
 #ifndef FE_FUSE_MAXN
 #define FE_FUSE_MAXN 4
 #endif
-  if (L.assemble && N > FE_FUSE_MAXN) {
-    FE_TRY((L.op == FE_LAPLACE ? (affine ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K>(a, L.st)
-                                         : launch_one<N, V, FE_LAPLACE, GEOM_STORED_K>(a, L.st))
-                               : (affine ? launch_one<N, V, FE_MASS, GEOM_AFFINE_K>(a, L.st)
-                                         : launch_one<N, V, FE_MASS, GEOM_STORED_K>(a, L.st))));
-    return fe_launch_dss(m, PREC, L.y, L.st);
-  }
-  if (L.assemble) {  // brick-fused x/y sums, then the DSS passes between bricks
-    if (L.op == FE_LAPLACE)
-      FE_TRY(affine ? (launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K, true>(a, L.st))
-                    : (launch_one<N, V, FE_LAPLACE, GEOM_STORED_K, true>(a, L.st)));
-    else
-      FE_TRY(affine ? (launch_one<N, V, FE_MASS, GEOM_AFFINE_K, true>(a, L.st))
-                    : (launch_one<N, V, FE_MASS, GEOM_STORED_K, true>(a, L.st)));
-    return fe_launch_dss_strided(m, PREC, L.y, Brick<N>::BX, Brick<N>::BY, L.st);
-  }
-  if (L.op == FE_LAPLACE)
-    return affine ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K>(a, L.st)
-                  : launch_one<N, V, FE_LAPLACE, GEOM_STORED_K>(a, L.st);
-  return affine ? launch_one<N, V, FE_MASS, GEOM_AFFINE_K>(a, L.st)
-                : launch_one<N, V, FE_MASS, GEOM_STORED_K>(a, L.st);
+  const bool fuse = L.assemble && N <= FE_FUSE_MAXN;
+  if (fuse)
+    FE_TRY((launch_geom<N, V, true>(a, L.op, affine, L.st)));
+  else
+    FE_TRY((launch_geom<N, V, false>(a, L.op, affine, L.st)));
+  if (!L.assemble) return FE_OK;
+  return fuse ? fe_launch_dss_strided(m, PREC, L.y, Brick<N>::BX, Brick<N>::BY, L.st)
+              : fe_launch_dss(m, PREC, L.y, L.st);
 }
 
 template <class V>

@@ -351,6 +351,11 @@ fe_status fe_cg_ensure_diag(const fe_mesh* m, CgWork* w, int op) {
 
 namespace {
 
+// the operator of the FP32 inner solve: FP32, or 16-bit operands with FP32 accumulation
+fe_status launch_inner_apply(const ApplyLaunch& L, const CgWork* w) {
+  return w->inner_prec == FE_F32 ? fe_launch_apply_f32(L) : fe_launch_apply_lowp(L, w->inner_prec);
+}
+
 // one PCG iteration on vectors of type S, solution of type U, scalars sc
 template <class S, class U>
 fe_status enqueue_iteration(const fe_mesh* m, CgWork* w, int op, bool flexible, double rtol,
@@ -361,7 +366,7 @@ fe_status enqueue_iteration(const fe_mesh* m, CgWork* w, int op, bool flexible, 
   if (sizeof(S) == 8)
     FE_TRY(fe_launch_apply_f64dw(L));
   else
-    FE_TRY(fe_launch_apply_f32(L));
+    FE_TRY(launch_inner_apply(L, w));
   k_qp<S><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(q, p, w->partials, sc, n);
   k_fin_alpha<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, hist);
   k_update_ur<S, U><<<grid_for(n), 256, 0, w->st>>>(u, r, p, q, sc, n);
@@ -382,7 +387,7 @@ fe_status build_graph(const fe_mesh* m, CgWork* w, int op, bool flexible, double
   cudaGraph_t g = nullptr;
   {  // one uncaptured apply first, so that per-kernel attributes are set outside the capture
     ApplyLaunch L{m, op, p, q, w->st, &sc->done};
-    FE_TRY(sizeof(S) == 8 ? fe_launch_apply_f64dw(L) : fe_launch_apply_f32(L));
+    FE_TRY(sizeof(S) == 8 ? fe_launch_apply_f64dw(L) : launch_inner_apply(L, w));
   }
   FE_CUDA(cudaStreamBeginCapture(w->st, cudaStreamCaptureModeThreadLocal), "begin capture");
   fe_status s = enqueue_iteration<S, U>(m, w, op, flexible, rtol, u, r, z, p, q, wv, invdiag, sc, hist);
@@ -560,20 +565,38 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
     fe_set_error("fe_cg_solve: vectors must be 16-byte aligned");
     return FE_ERR_INVALID;
   }
-  if (opts->maxit < 1 || !(opts->rtol >= 0.0) || (opts->mixed != 0 && opts->mixed != FE_F32)) {
+  const bool lowp = opts->mixed == FE_BF16_F32ACC || opts->mixed == FE_F16_F32ACC;
+  if (opts->maxit < 1 || !(opts->rtol >= 0.0) ||
+      (opts->mixed != 0 && opts->mixed != FE_F32 && !lowp)) {
     fe_set_error("fe_cg_solve: invalid options (maxit %d, rtol %g, mixed %d)", opts->maxit,
                  opts->rtol, opts->mixed);
     return FE_ERR_INVALID;
   }
+  if (lowp && m->d.geom_mode != FE_GEOM_STORED) {
+    fe_set_error("fe_cg_solve: a 16-bit inner operator needs FE_GEOM_STORED geometry");
+    return FE_ERR_INVALID;
+  }
   std::memset(res, 0, sizeof(*res));
   FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
-  const bool mixed = opts->mixed == FE_F32;
+  const bool mixed = opts->mixed != 0;
   const int op = FE_LAPLACE;
   CgWork* w = nullptr;
   FE_TRY(fe_cg_get_work(m, mixed, &w));
   FE_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cg: caller stream");
   FE_TRY(fe_ensure_geometry(m, FE_F64, false));
-  if (mixed) FE_TRY(fe_ensure_geometry(m, FE_F32, false));
+  if (mixed) {
+    FE_TRY(fe_ensure_geometry(m, FE_F32, false));
+    if (lowp) FE_TRY(fe_ensure_geometry(m, opts->mixed, false));
+    w->inner_prec = opts->mixed;
+    if (w->g32_prec != w->inner_prec) {  // the inner graphs bake the operator in
+      for (int f = 0; f < 2; ++f)
+        if (w->g32[f]) {
+          cudaGraphExecDestroy(w->g32[f]);
+          w->g32[f] = nullptr;
+        }
+      w->g32_prec = w->inner_prec;
+    }
+  }
   FE_TRY(fe_cg_ensure_diag(m, w, op));
   const long long n = w->n;
   const int flex = opts->flexible ? 1 : 0;

@@ -98,6 +98,8 @@ struct CgWork {
   cudaStream_t st = nullptr;
   cudaGraphExec_t g64[2] = {nullptr, nullptr};  // [flexible]
   cudaGraphExec_t g32[2] = {nullptr, nullptr};
+  int inner_prec = FE_F32;  // arithmetic of the inner solve's operator (FP32 or 16-bit operands)
+  int g32_prec = FE_F32;    // the one the g32 graphs were captured with
   double* g64_hist = nullptr;
 };
 

@@ -8,6 +8,8 @@
 // near the memory roofline.  The same sweep code is instantiated for `double` (the FP64 pipe,
 // kept as a cross-check variant) and for `float` (the FP32 path of mixed precision).
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -169,6 +171,7 @@ template <>
 struct NT<double> {
   using SV = double;
   using GV = double;
+  static constexpr bool LOWP = false;
   __device__ static __forceinline__ double zero() { return 0.0; }
   __device__ static __forceinline__ double mac(double a, double c, double v) { return fma(c, v, a); }
   __device__ static __forceinline__ double mac12(double a, double c, double v) { return fma(c, v, a); }
@@ -192,6 +195,7 @@ template <>
 struct NT<float> {
   using SV = float;
   using GV = float;
+  static constexpr bool LOWP = false;
   __device__ static __forceinline__ float zero() { return 0.0f; }
   __device__ static __forceinline__ float mac(float a, float c, float v) { return fmaf(c, v, a); }
   __device__ static __forceinline__ float mac12(float a, float c, float v) { return fmaf(c, v, a); }
@@ -211,10 +215,59 @@ struct NT<float> {
   __device__ static __forceinline__ float geo(const float* p) { return __ldcs(p); }
 };
 
+// 16-bit contractions with FP32 accumulation (FE_BF16_F32ACC, FE_F16_F32ACC): a value is a float,
+// but every operand of a product (inputs, intermediate sweep values, 1D coefficients, metric) is
+// rounded to the 16-bit format, so each product is exact in FP32 and only the accumulation is
+// FP32.  Vectors are FP32 arrays; the metric is stored in the 16-bit format.
+struct bfv {
+  float v;
+  static constexpr bool BF = true;
+};
+struct hfv {
+  float v;
+  static constexpr bool BF = false;
+};
+template <class W>
+struct NT16 {
+  using SV = float;
+  using GV = unsigned short;  // bits of the 16-bit metric value
+  static constexpr bool LOWP = true;
+  __device__ static __forceinline__ float rnd(float x) {
+    if constexpr (W::BF)
+      return __bfloat162float(__float2bfloat16_rn(x));
+    else
+      return __half2float(__float2half_rn(x));
+  }
+  __device__ static __forceinline__ W zero() { return {0.0f}; }
+  __device__ static __forceinline__ W mac(W a, W c, W x) { return {fmaf(c.v, x.v, a.v)}; }
+  __device__ static __forceinline__ W mac12(W a, W c, W x) { return {fmaf(c.v, x.v, a.v)}; }
+  __device__ static __forceinline__ W prod(W c, W x) { return {c.v * x.v}; }
+  __device__ static __forceinline__ W addk(W a, W b) { return {rnd(a.v + b.v)}; }
+  __device__ static __forceinline__ W subk(W a, W b) { return {rnd(a.v - b.v)}; }
+  __device__ static __forceinline__ W fin(W a) { return a; }
+  __device__ static __forceinline__ W keep(W a) { return {rnd(a.v)}; }
+  __device__ static __forceinline__ W mul(W a, W b) { return {a.v * b.v}; }
+  __device__ static __forceinline__ W add(W a, W b) { return {a.v + b.v}; }
+  __device__ static __forceinline__ W sub(W a, W b) { return {a.v - b.v}; }
+  __device__ static __forceinline__ W recip(W a) { return {1.0f / a.v}; }
+  __device__ static __forceinline__ W neg(W a) { return {-a.v}; }
+  __device__ static __forceinline__ W load(const float* p) { return {rnd(__ldg(p))}; }
+  __device__ static __forceinline__ W load_stream(const float* p) { return {rnd(__ldcs(p))}; }
+  __device__ static __forceinline__ void store(float* p, W x) { __stcs(p, x.v); }
+  __device__ static __forceinline__ W geo(const unsigned short* p) {
+    const unsigned short b = __ldcs(p);
+    if constexpr (W::BF)
+      return {__uint_as_float((unsigned)b << 16)};
+    else
+      return {__half2float(__ushort_as_half(b))};
+  }
+};
+
 template <>
 struct NT<dw> {
   using SV = double;
   using GV = float2;
+  static constexpr bool LOWP = false;
   __device__ static __forceinline__ dw zero() { return {0.0f, 0.0f}; }
   __device__ static __forceinline__ dw mac(dw a, dw c, dw v) { return dw_mac(a, c, v); }
   // the 12-operation form, for the geometry terms (their error reaches every output)
@@ -246,6 +299,10 @@ struct NT<dw> {
     return {g.x, g.y};
   }
 };
+template <>
+struct NT<bfv> : NT16<bfv> {};
+template <>
+struct NT<hfv> : NT16<hfv> {};
 
 // ---------------------------------------------------------------------------------------------
 // 1D tables passed by value as kernel parameters (they land in the constant bank and are read
@@ -317,6 +374,8 @@ struct fe_mesh {
   double* geo64 = nullptr;
   float2* geodw = nullptr;
   float* geo32 = nullptr;
+  unsigned short* geo16[2] = {nullptr, nullptr};  // bf16 / fp16 metric, scaled by gscale[op]
+  float gscale[2] = {1.0f, 1.0f};                 // powers of two: Laplace terms, w detJ
   // recompute mode: nodal coordinates [cell][3][n3], and an L2-sized scratch for the metric of one
   // chunk of cells (per arithmetic: 0 double-word, 1 FP64, 2 FP32)
   double* xyz64 = nullptr;
@@ -378,6 +437,8 @@ struct ApplyLaunch {
 fe_status fe_launch_apply_f64dw(const ApplyLaunch& a);
 fe_status fe_launch_apply_f64native(const ApplyLaunch& a);
 fe_status fe_launch_apply_f32(const ApplyLaunch& a);
+// FE_BF16_F32ACC / FE_F16_F32ACC: float vectors, 16-bit operands, stored geometry only
+fe_status fe_launch_apply_lowp(const ApplyLaunch& a, int prec);
 
 // dss / vectors (fe_dss.cu)
 fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st);

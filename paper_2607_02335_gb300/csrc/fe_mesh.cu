@@ -236,6 +236,35 @@ __global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out,
     out[e] = __double2float_rn(in[e]);
 }
 
+// 16-bit metric copies: max |value| of the Laplace terms (components 0-5) and of w detJ
+// (component 6), as ordered bit patterns of non-negative doubles
+__global__ void k_geo_absmax(const double* __restrict__ g, long long n, int n3,
+                             unsigned long long* __restrict__ out) {
+  unsigned long long m0 = 0, m1 = 0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(g[e]));
+    if ((e / n3) % FE_GEO_COMPS == 6)
+      m1 = b > m1 ? b : m1;
+    else
+      m0 = b > m0 ? b : m0;
+  }
+  atomicMax(out + 0, m0);
+  atomicMax(out + 1, m1);
+}
+template <bool BF>
+__global__ void k_to_h16(const double* __restrict__ g, unsigned short* __restrict__ out, long long n,
+                         int n3, float s0, float s1) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float v = (float)g[e] * ((e / n3) % FE_GEO_COMPS == 6 ? s1 : s0);
+    if constexpr (BF)
+      out[e] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    else
+      out[e] = __half_as_ushort(__float2half_rn(v));
+  }
+}
+
 static unsigned grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152LL * 64) b = 152LL * 64;
@@ -269,6 +298,38 @@ fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
   }
   if (m->d.geom_mode != FE_GEOM_STORED) return FE_OK;
   const long long n = m->ncells * FE_GEO_COMPS * m->n3;
+  if (prec == FE_BF16_F32ACC || prec == FE_F16_F32ACC) {
+    const int k = prec == FE_BF16_F32ACC ? 0 : 1;
+    if (m->geo16[k]) return FE_OK;
+    if (!m->geo64) {
+      fe_set_error("16-bit metric: the FP64 metric of this mesh has been released");
+      return FE_ERR_INVALID;
+    }
+    // scale each metric family by a power of two that brings its largest value into [1/2, 1],
+    // which keeps w detJ (about h^3) inside the fp16 range
+    unsigned long long* dmax = nullptr;
+    FE_TRY(fe_dalloc((void**)&dmax, 2 * sizeof(unsigned long long), m->st, "metric max"));
+    FE_CUDA(cudaMemsetAsync(dmax, 0, 2 * sizeof(unsigned long long), m->st), "metric max");
+    k_geo_absmax<<<grid_for(n, 256), 256, 0, m->st>>>(m->geo64, n, (int)m->n3, dmax);
+    unsigned long long hmax[2] = {0, 0};
+    FE_CUDA(cudaMemcpyAsync(hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, m->st), "metric max");
+    FE_CUDA(cudaStreamSynchronize(m->st), "metric max");
+    fe_dfree(dmax, m->st);
+    for (int c = 0; c < 2; ++c) {
+      double gm;
+      std::memcpy(&gm, &hmax[c], sizeof(gm));
+      m->gscale[c] = gm > 0.0 ? (float)std::ldexp(1.0, -std::ilogb(gm) - 1) : 1.0f;
+    }
+    FE_TRY(fe_dalloc((void**)&m->geo16[k], n * sizeof(unsigned short), m->st, "metric (16-bit)"));
+    if (k == 0)
+      k_to_h16<true><<<grid_for(n, 256), 256, 0, m->st>>>(m->geo64, m->geo16[k], n, (int)m->n3,
+                                                          m->gscale[0], m->gscale[1]);
+    else
+      k_to_h16<false><<<grid_for(n, 256), 256, 0, m->st>>>(m->geo64, m->geo16[k], n, (int)m->n3,
+                                                           m->gscale[0], m->gscale[1]);
+    FE_CUDA(cudaStreamSynchronize(m->st), "metric (16-bit) copy");
+    return FE_OK;
+  }
   if ((prec == FE_F64 && !native && !m->geodw) || (prec == FE_F32 && !m->geo32) ||
       (prec == FE_F64 && native && !m->geo64)) {
     if (!m->geo64) {
@@ -298,7 +359,8 @@ fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
 static void free_mesh(fe_mesh* m, cudaStream_t st) {
   if (!m) return;
   if (m->cg_work && m->cg_free) m->cg_free(m->cg_work, st);
-  void* bufs[] = {m->geo64, m->geodw, m->geo32, m->xyz64, m->xyzdw, m->xyz32, m->rc_scratch[0],
+  void* bufs[] = {m->geo64, m->geodw, m->geo32, m->geo16[0], m->geo16[1], m->xyz64, m->xyzdw,
+                  m->xyz32, m->rc_scratch[0],
                   m->rc_scratch[1], m->rc_scratch[2], m->diag64[0],
                   m->diag64[1], m->invdiag32[0], m->invdiag32[1], m->invdiag64[0],
                   m->invdiag64[1], m->invmult64, m->red};

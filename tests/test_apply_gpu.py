@@ -199,7 +199,7 @@ def test_invalid_arguments(fe):
     with pytest.raises(fe.FeError):
         fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_F64, x, x)  # overlap
     with pytest.raises(fe.FeError):
-        fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_BF16_F32ACC, x, gm.empty())
+        fe.fe_apply(gm.handle, fe.FE_LAPLACE, 7, x, gm.empty())  # unknown precision
     with pytest.raises(fe.FeError):
         fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_F64, 0, gm.empty())
     with pytest.raises(fe.FeError):
@@ -250,3 +250,36 @@ def test_smooth_input_accuracy(fe, p):
     yref = O.apply_local(om, O.LAPLACE, xc)
     assert rel_max_err(to_host(gm.apply(x, flags=fe.FE_NATIVE_F64)), yref) <= 1e-12
     assert rel_max_err(to_host(gm.apply(x)), yref) <= 1e-11
+
+
+# 16-bit operands with FP32 accumulation: every stage output (interpolated values, gradients,
+# metric products, even-odd sums) is rounded to the 16-bit format, about a dozen roundings of unit
+# roundoff u on the way from x to y (bf16 u = 2^-9, fp16 u = 2^-12), amplified by the
+# cancellation of the Laplacian of a random field; the bounds allow ~12 u x a factor of 2.5.
+TOL_LOWP = {"bf16": 6e-2, "fp16": 8e-3}
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7])
+def test_lowp_apply_vs_oracle(fe, p):
+    m = SHAPES[p]
+    om = oracle_mesh(m, p, amp=0.1)
+    gm = fe.Mesh(m, p, deform_amp=0.1)
+    xc = O.gather(om, S.primal_unique(m, p, seed=0))
+    x32 = torch.from_numpy(xc).float().cuda()
+    for name, prec in (("bf16", fe.FE_BF16_F32ACC), ("fp16", fe.FE_F16_F32ACC)):
+        for op in (fe.FE_LAPLACE, fe.FE_MASS):
+            yref = O.apply_local(om, op, xc)
+            y = to_host(gm.apply(x32, op=op, prec=prec))
+            assert rel_max_err(y, yref) <= TOL_LOWP[name], (p, op, name, rel_max_err(y, yref))
+            ya = to_host(gm.apply(x32, op=op, prec=prec, flags=fe.FE_ASSEMBLE))
+            yd = to_host(gm.dss(gm.apply(x32, op=op, prec=prec), prec=fe.FE_F32))
+            assert rel_max_err(ya, yd) <= 1e-6, (p, op, name)
+
+
+def test_lowp_requires_stored_geometry(fe):
+    for mode in (fe.FE_GEOM_AFFINE, fe.FE_GEOM_RECOMPUTE):
+        gm = fe.Mesh(3, 2, geom_mode=mode)
+        x = gm.empty(fe.FE_F32)
+        with pytest.raises(fe.FeError) as e:
+            fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_BF16_F32ACC, x, gm.empty(fe.FE_F32))
+        assert e.value.status == fe.FE_ERR_INVALID

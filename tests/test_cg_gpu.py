@@ -103,6 +103,30 @@ def test_mixed_precision_reaches_fp64_residual(fe, p, m):
     assert abs(e64 - e32) <= 1e-6 * e64
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_mixed_16bit_inner_operator(fe, prec):
+    """FP64 FCG preconditioned by an inner PCG whose operator has 16-bit operands and FP32
+    accumulation, and FP64 iterative refinement around it: both reach an FP64 residual of 1e-10,
+    checked by the oracle from the returned x."""
+    m, p = (5, 4, 3), 3
+    om = oracle_mesh(m, p, amp=0.1, dirichlet=True)
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=True)
+    bc = O.rhs(om, O.RHS_SINE)
+    b = torch.from_numpy(bc).cuda()
+    code = fe.FE_BF16_F32ACC if prec == "bf16" else fe.FE_F16_F32ACC
+    xf = torch.zeros_like(b)
+    rf = gm.cg_solve(b, xf, rtol=1e-10, maxit=6000, mixed=code, flexible=True)
+    assert rf.status == fe.FE_OK and rf.rel_res <= 1e-10
+    assert oracle_relres(om, bc, xf.cpu().numpy()) <= 1.2e-10
+    xi = torch.zeros_like(b)
+    ri = gm.cg_solve(b, xi, rtol=1e-10, maxit=6000, mixed=code)
+    assert ri.status == fe.FE_OK and oracle_relres(om, bc, xi.cpu().numpy()) <= 1.2e-10
+    # the FP32 inner operator still works on the same mesh afterwards (inner graphs rebuilt)
+    x32 = torch.zeros_like(b)
+    r32 = gm.cg_solve(b, x32, rtol=1e-10, maxit=6000, mixed=fe.FE_F32, flexible=True)
+    assert r32.status == fe.FE_OK and oracle_relres(om, bc, x32.cpu().numpy()) <= 1.2e-10
+
+
 def test_cg_statuses(fe):
     m, p = (3, 3, 3), 2
     gm = fe.Mesh(m, p, deform_amp=0.05, dirichlet=True)
