@@ -640,9 +640,13 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   }
 }
 
+#ifdef FE_MINB
+#define FE_APPLY_BOUNDS __launch_bounds__(Cfg<N>::THREADS, FE_MINB)
+#else
+#define FE_APPLY_BOUNDS __launch_bounds__(Cfg<N>::THREADS)
+#endif
 template <int N, class V, int OP, int GEOM, bool FUSE>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
-    k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
+__global__ void FE_APPLY_BOUNDS k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.skip && *(volatile const int*)a.skip) return;  // uniform over the grid
   const long long cell0 =
