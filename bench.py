@@ -223,6 +223,22 @@ def committed_traffic():
     return int(d["bytes_per_launch"]) if "bytes_per_launch" in d else None
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks of the job (the slowest replica sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step, steps, world, seconds):
+    """Whole-job GDoF/s: every rank processes units_per_rank_step per step (weak scaling)."""
+    return units_per_rank_step * world * steps / seconds / 1e9
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -272,13 +288,9 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = units_per_step * world * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_rate(units_per_step, args.steps, world, total_ms * 1e-3)
 
     # per-case breakdown: assembled apply and the volumetric kernel alone; 5 warm-ups, then the
     # median of 20 reps with L2 flushed before each, and of 20 reps without the flush
@@ -353,8 +365,8 @@ def run_ours(args, rank, world):
             fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, fe.FE_ASSEMBLE, stream)
             hyk.copy_(y, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value = units_per_step * world / e2e_s / 1e9
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    e2e_value = job_rate(units_per_step, 1, world, e2e_s)
 
     extras = {}
     if not args.small and not args.no_extras:
