@@ -48,6 +48,13 @@ class _Mesh(ctypes.Structure):
                 ("p", ctypes.c_int), ("amp", ctypes.c_double), ("dirichlet", ctypes.c_int)]
 
 
+class _MB(ctypes.Structure):
+    _fields_ = [("nblocks", ctypes.c_int), ("p", ctypes.c_int),
+                ("dims", ctypes.POINTER(ctypes.c_int)),
+                ("block_verts", ctypes.POINTER(ctypes.c_int)),
+                ("vxyz", ctypes.POINTER(ctypes.c_double))]
+
+
 class _CGOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("flexible", ctypes.c_int)]
 
@@ -92,6 +99,12 @@ def _L():
             "or_l2_error": (i32, [M, i32, _D, _D]),
             "or_cg": (i32, [M, i32, _D, _D, ctypes.POINTER(_CGOpts), ctypes.POINTER(i32),
                             _D, _D, _D, i32]),
+            "or_mb_n_cellwise": (ll, [ctypes.POINTER(_MB)]),
+            "or_mb_cell_offset": (ll, [ctypes.POINTER(_MB), i32]),
+            "or_mb_cell_nodes": (None, [ctypes.POINTER(_MB), i32, i32, i32, i32, _D]),
+            "or_mb_element_matrix": (i32, [ctypes.POINTER(_MB), i32, ll, _D]),
+            "or_mb_apply_local": (i32, [ctypes.POINTER(_MB), i32, _D, _D, i32]),
+            "or_mb_numbering": (ll, [ctypes.POINTER(_MB), ctypes.c_double, ctypes.POINTER(ll)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -346,3 +359,85 @@ def cg(mesh: Mesh, op: int, bg: np.ndarray, x0=None, rtol: float = 1e-10, maxit:
     k = it.value
     return {"x": x, "status": st, "iters": k, "alpha": alpha[:k], "beta": beta[:max(k - 1, 0)],
             "relres": relres[:k + 1]}
+
+
+class MBMesh:
+    """Block-structured mesh (Sec. 4.2): macro-blocks given by eight corner vertices each
+    (local corner c = i + 2j + 4k), a structured grid of dims[b] cells per block, trilinear
+    geometry.  Cell-wise layout: blocks one after the other, each block's cells lexicographic,
+    the canonical node order inside a cell.  The global numbering comes from the nodes'
+    coordinates (``or_mb_numbering``); gather, scatter and DSS are then the plain definitions
+    G, G^T and S = G G^T of Sec. 2.1 and Eq. (dss_operator)."""
+
+    def __init__(self, vxyz, block_verts, dims, p: int, tol: float = 1e-9):
+        self.vxyz = np.ascontiguousarray(np.asarray(vxyz, dtype=np.float64).reshape(-1, 3))
+        self.block_verts = np.ascontiguousarray(np.asarray(block_verts, dtype=np.int32).reshape(-1, 8))
+        self.dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+        self.p, self.n = int(p), int(p) + 1
+        self.nblocks = len(self.block_verts)
+        self._c = _MB(self.nblocks, self.p, self.dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      self.block_verts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      self.vxyz.ctypes.data_as(_D))
+        self.n_cellwise = int(_L().or_mb_n_cellwise(ctypes.byref(self._c)))
+        self.gid = np.zeros(self.n_cellwise, dtype=np.int64)
+        nu = _L().or_mb_numbering(ctypes.byref(self._c), tol,
+                                  self.gid.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+        if nu < 0:
+            raise MemoryError("or_mb_numbering")
+        self.n_unique = int(nu)
+
+    def cell_offset(self, block: int) -> int:
+        return int(_L().or_mb_cell_offset(ctypes.byref(self._c), block))
+
+    def cell_nodes(self, block, cx, cy, cz):
+        xn = np.zeros(3 * self.n ** 3)
+        _L().or_mb_cell_nodes(ctypes.byref(self._c), block, cx, cy, cz, _dp(xn))
+        return xn.reshape(-1, 3)
+
+    def node_coords(self):
+        """Physical coordinates of every global node (from its first copy)."""
+        xyz = np.zeros((self.n_unique, 3))
+        n3 = self.n ** 3
+        e = 0
+        for b in range(self.nblocks):
+            mx, my, mz = (int(v) for v in self.dims[b])
+            for cz in range(mz):
+                for cy in range(my):
+                    for cx in range(mx):
+                        xyz[self.gid[e:e + n3]] = self.cell_nodes(b, cx, cy, cz)
+                        e += n3
+        return xyz
+
+    def gather(self, xg):
+        return np.asarray(xg, dtype=np.float64)[self.gid]
+
+    def scatter(self, yc):
+        yg = np.zeros(self.n_unique)
+        np.add.at(yg, self.gid, np.asarray(yc, dtype=np.float64))
+        return yg
+
+    def dss(self, yc):
+        return self.gather(self.scatter(yc))
+
+    def multiplicity(self):
+        return self.gather(np.bincount(self.gid, minlength=self.n_unique).astype(np.float64))
+
+    def element_matrix(self, op: int, cell: int):
+        nn = self.n ** 3
+        A = np.zeros(nn * nn)
+        st = _L().or_mb_element_matrix(ctypes.byref(self._c), op, cell, _dp(A))
+        if st:
+            raise RuntimeError(f"or_mb_element_matrix: status {st}")
+        return A.reshape(nn, nn)
+
+    def apply_local(self, op: int, xc, nthreads: int = 0):
+        xc = np.ascontiguousarray(xc, dtype=np.float64)
+        yc = np.zeros(self.n_cellwise)
+        st = _L().or_mb_apply_local(ctypes.byref(self._c), op, _dp(xc), _dp(yc), nthreads)
+        if st:
+            raise RuntimeError(f"or_mb_apply_local: status {st}")
+        return yc
+
+    def apply_assembled(self, op: int, xg, nthreads: int = 0):
+        """A_CG x_glob = G^T (blockdiag A_K) G x_glob (Sec. 3.1)."""
+        return self.scatter(self.apply_local(op, self.gather(xg), nthreads))

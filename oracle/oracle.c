@@ -231,22 +231,23 @@ typedef struct {
   double* grad;
 } qdata;
 
-static int qdata_build(const or_mesh* m, long long cell, qdata* d) {
-  int n = m->p + 1, nn = n * n * n, nq = nn;
-  int cx, cy, cz;
-  cell_coords(m, cell, &cx, &cy, &cz);
+/* quadrature data of a cell of degree p from its nodal coordinates xn (n^3 x 3) */
+static int qdata_build_nodes(int p, const double* xn, qdata* d) {
+  int n = p + 1, nn = n * n * n, nq = nn;
+  or_mesh m1;
+  memset(&m1, 0, sizeof(m1));
+  m1.p = p;
+  const or_mesh* m = &m1;
   double t[OR_MAXN], s[OR_MAXN], w[OR_MAXN];
-  ref_nodes01(m->p, t);
+  ref_nodes01(p, t);
   gauss01(n, s, w);
-  double* xn = (double*)malloc(sizeof(double) * 3 * nn);
   d->n = n;
   d->nn = nn;
   d->nq = nq;
   d->wdet = (double*)malloc(sizeof(double) * nq);
   d->phi = (double*)malloc(sizeof(double) * (size_t)nq * nn);
   d->grad = (double*)malloc(sizeof(double) * (size_t)nq * nn * 3);
-  if (!xn || !d->wdet || !d->phi || !d->grad) return 2;
-  or_cell_nodes(m, cx, cy, cz, xn);
+  if (!d->wdet || !d->phi || !d->grad) return 2;
   int status = 0;
   for (int q3 = 0; q3 < n; ++q3)
     for (int q2 = 0; q2 < n; ++q2)
@@ -272,8 +273,19 @@ static int qdata_build(const or_mesh* m, long long cell, qdata* d) {
                     g[0] * Ji[0 * 3 + c] + g[1] * Ji[1 * 3 + c] + g[2] * Ji[2 * 3 + c];
             }
       }
-  free(xn);
   return status;
+}
+
+static int qdata_build(const or_mesh* m, long long cell, qdata* d) {
+  int n = m->p + 1, nn = n * n * n;
+  int cx, cy, cz;
+  cell_coords(m, cell, &cx, &cy, &cz);
+  double* xn = (double*)malloc(sizeof(double) * 3 * nn);
+  if (!xn) return 2;
+  or_cell_nodes(m, cx, cy, cz, xn);
+  int st = qdata_build_nodes(m->p, xn, d);
+  free(xn);
+  return st;
 }
 
 static void qdata_free(qdata* d) {
@@ -286,10 +298,19 @@ static void qdata_free(qdata* d) {
  *   Laplace  K_ij = sum_q w_q detJ_q (J^{-T} grad phi_i).(J^{-T} grad phi_j)
  *   mass     M_ij = sum_q w_q detJ_q phi_i phi_j
  * (Eq. (laplace_operator) and Eq. (mass_operator) with general per-quadrature-point geometry). */
+static void element_matrix_from_qdata(const qdata* dp, int op, double* A);
+
 int or_element_matrix(const or_mesh* m, int op, long long cell, double* A) {
   qdata d;
   int st = qdata_build(m, cell, &d);
   if (st == 2) return 2;
+  element_matrix_from_qdata(&d, op, A);
+  qdata_free(&d);
+  return st;
+}
+
+static void element_matrix_from_qdata(const qdata* dp, int op, double* A) {
+  const qdata d = *dp;
   int nn = d.nn;
   for (long long e = 0; e < (long long)nn * nn; ++e) A[e] = 0.0;
   for (int q = 0; q < d.nq; ++q) {
@@ -307,8 +328,6 @@ int or_element_matrix(const or_mesh* m, int op, long long cell, double* A) {
         A[(size_t)i * nn + j] += wd * v;
       }
   }
-  qdata_free(&d);
-  return st;
 }
 
 int or_element_row(const or_mesh* m, int op, long long cell, int row, double* out) {
@@ -828,4 +847,168 @@ int or_cg(const or_mesh* m, int op, const double* bg, double* xg, const or_cg_op
   free(t);
   free(bnd);
   return status;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Block-structured meshes (Sec. 4.2 "Generalization to Block-Structured Grids"): macro-blocks,
+ * each a structured grid of cells whose geometry is the trilinear map of its eight corner
+ * vertices.  The global (unique) numbering is found from the nodes' physical coordinates --
+ * conforming blocks place shared nodes at the same points -- so it knows nothing of faces,
+ * orientations or sharing lists.
+ * ---------------------------------------------------------------------------------------- */
+long long or_mb_n_cellwise(const or_mb* mb) {
+  long long n3 = (long long)(mb->p + 1) * (mb->p + 1) * (mb->p + 1), c = 0;
+  for (int b = 0; b < mb->nblocks; ++b)
+    c += (long long)mb->dims[3 * b] * mb->dims[3 * b + 1] * mb->dims[3 * b + 2];
+  return c * n3;
+}
+
+long long or_mb_cell_offset(const or_mb* mb, int block) {
+  long long c = 0;
+  for (int b = 0; b < block; ++b)
+    c += (long long)mb->dims[3 * b] * mb->dims[3 * b + 1] * mb->dims[3 * b + 2];
+  return c;
+}
+
+/* x(xi) = sum_c N_c(xi) X_c over the corners c = i + 2j + 4k at xi = (i, j, k) */
+static void trilinear(const or_mb* mb, int block, const double xi[3], double x[3]) {
+  for (int a = 0; a < 3; ++a) x[a] = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    double w = ((c & 1) ? xi[0] : 1.0 - xi[0]) * ((c & 2) ? xi[1] : 1.0 - xi[1]) *
+               ((c & 4) ? xi[2] : 1.0 - xi[2]);
+    const double* X = mb->vxyz + 3 * mb->block_verts[8 * block + c];
+    for (int a = 0; a < 3; ++a) x[a] += w * X[a];
+  }
+}
+
+void or_mb_cell_nodes(const or_mb* mb, int block, int cx, int cy, int cz, double* xn) {
+  int n = mb->p + 1;
+  const int* d = mb->dims + 3 * block;
+  double t[OR_MAXN];
+  ref_nodes01(mb->p, t);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        double xi[3] = {(cx + t[i]) / d[0], (cy + t[j]) / d[1], (cz + t[k]) / d[2]};
+        trilinear(mb, block, xi, xn + 3 * ((k * n + j) * n + i));
+      }
+}
+
+/* block and cell coordinates of a cell numbered over all blocks */
+static void mb_cell(const or_mb* mb, long long cell, int* block, int* cx, int* cy, int* cz) {
+  int b = 0;
+  long long c = cell;
+  for (;;) {
+    long long nb = (long long)mb->dims[3 * b] * mb->dims[3 * b + 1] * mb->dims[3 * b + 2];
+    if (c < nb || b == mb->nblocks - 1) break;
+    c -= nb;
+    ++b;
+  }
+  const int* d = mb->dims + 3 * b;
+  *block = b;
+  *cx = (int)(c % d[0]);
+  *cy = (int)((c / d[0]) % d[1]);
+  *cz = (int)(c / ((long long)d[0] * d[1]));
+}
+
+int or_mb_element_matrix(const or_mb* mb, int op, long long cell, double* A) {
+  int n = mb->p + 1, nn = n * n * n, b, cx, cy, cz;
+  mb_cell(mb, cell, &b, &cx, &cy, &cz);
+  double* xn = (double*)malloc(sizeof(double) * 3 * nn);
+  if (!xn) return 2;
+  or_mb_cell_nodes(mb, b, cx, cy, cz, xn);
+  qdata d;
+  int st = qdata_build_nodes(mb->p, xn, &d);
+  free(xn);
+  if (st == 2) return 2;
+  element_matrix_from_qdata(&d, op, A);
+  qdata_free(&d);
+  return st;
+}
+
+int or_mb_apply_local(const or_mb* mb, int op, const double* xc, double* yc, int nthreads) {
+  int n = mb->p + 1, nn = n * n * n;
+  long long nc = or_mb_n_cellwise(mb) / nn;
+  int status = 0;
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long long c = 0; c < nc; ++c) {
+    double* A = (double*)malloc(sizeof(double) * (size_t)nn * nn);
+    int st = or_mb_element_matrix(mb, op, c, A);
+    if (st) status = st;
+    for (int a = 0; a < nn; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < nn; ++b) s += A[(size_t)a * nn + b] * xc[c * nn + b];
+      yc[c * nn + a] = s;
+    }
+    free(A);
+  }
+  return status;
+}
+
+typedef struct {
+  double x[3];
+  long long idx;
+} mb_pt;
+
+static int cmp_pt(const void* a, const void* b) {
+  const mb_pt* p = (const mb_pt*)a;
+  const mb_pt* q = (const mb_pt*)b;
+  for (int d = 0; d < 3; ++d) {
+    if (p->x[d] < q->x[d]) return -1;
+    if (p->x[d] > q->x[d]) return 1;
+  }
+  return (p->idx > q->idx) - (p->idx < q->idx);
+}
+
+static long long uf_find(long long* par, long long i) {
+  while (par[i] != i) {
+    par[i] = par[par[i]];
+    i = par[i];
+  }
+  return i;
+}
+
+/* gid[e] for every cell-wise entry e: nodes closer than tol get the same number; numbers follow
+ * the ascending (x, y, z) order of the nodes.  Returns the unique count (< 0 on failure). */
+long long or_mb_numbering(const or_mb* mb, double tol, long long* gid) {
+  int n = mb->p + 1, nn = n * n * n;
+  long long ncw = or_mb_n_cellwise(mb), nc = ncw / nn;
+  mb_pt* pts = (mb_pt*)malloc(sizeof(mb_pt) * ncw);
+  long long* par = (long long*)malloc(sizeof(long long) * ncw);
+  double* xn = (double*)malloc(sizeof(double) * 3 * nn);
+  if (!pts || !par || !xn) return -1;
+  for (long long c = 0; c < nc; ++c) {
+    int b, cx, cy, cz;
+    mb_cell(mb, c, &b, &cx, &cy, &cz);
+    or_mb_cell_nodes(mb, b, cx, cy, cz, xn);
+    for (int a = 0; a < nn; ++a) {
+      long long e = c * nn + a;
+      for (int d = 0; d < 3; ++d) pts[e].x[d] = xn[3 * a + d];
+      pts[e].idx = e;
+    }
+  }
+  qsort(pts, (size_t)ncw, sizeof(mb_pt), cmp_pt);
+  for (long long e = 0; e < ncw; ++e) par[e] = e;
+  /* nodes within tol of each other are neighbours in the x-sorted order up to an x-window */
+  for (long long i = 0; i < ncw; ++i)
+    for (long long j = i + 1; j < ncw && pts[j].x[0] - pts[i].x[0] <= tol; ++j)
+      if (fabs(pts[j].x[1] - pts[i].x[1]) <= tol && fabs(pts[j].x[2] - pts[i].x[2]) <= tol) {
+        long long ri = uf_find(par, i), rj = uf_find(par, j);
+        if (ri != rj) par[rj < ri ? ri : rj] = rj < ri ? rj : ri;
+      }
+  long long nu = 0;
+  long long* rootid = (long long*)malloc(sizeof(long long) * ncw);
+  if (!rootid) return -1;
+  for (long long i = 0; i < ncw; ++i) rootid[i] = -1;
+  for (long long i = 0; i < ncw; ++i) {
+    long long r = uf_find(par, i);
+    if (rootid[r] < 0) rootid[r] = nu++;
+    gid[pts[i].idx] = rootid[r];
+  }
+  free(rootid);
+  free(pts);
+  free(par);
+  free(xn);
+  return nu;
 }

@@ -99,6 +99,20 @@ typedef struct {
 int or_cg(const or_mesh* m, int op, const double* bg, double* xg, const or_cg_opts* o, int* iters,
           double* alpha, double* beta, double* relres, int nthreads);
 
+/* ---- block-structured meshes (Sec. 4.2): trilinear macro-blocks, numbering by coordinates ---- */
+typedef struct {
+  int nblocks, p;
+  const int* dims;        /* 3 per block: cells along the block's local x, y, z */
+  const int* block_verts; /* 8 per block: macro-vertex of local corner c = i + 2j + 4k */
+  const double* vxyz;     /* 3 per macro-vertex */
+} or_mb;
+long long or_mb_n_cellwise(const or_mb* mb);
+long long or_mb_cell_offset(const or_mb* mb, int block);
+void or_mb_cell_nodes(const or_mb* mb, int block, int cx, int cy, int cz, double* xn);
+int or_mb_element_matrix(const or_mb* mb, int op, long long cell, double* A);
+int or_mb_apply_local(const or_mb* mb, int op, const double* xc, double* yc, int nthreads);
+long long or_mb_numbering(const or_mb* mb, double tol, long long* gid);
+
 #ifdef __cplusplus
 }
 #endif
