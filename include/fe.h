@@ -233,6 +233,42 @@ fe_status fe_serve_poll(fe_server* server, long long ticket, fe_cg_result* res, 
 fe_status fe_serve_stats(fe_server* server, double* p50_s, double* p99_s, double* solves_per_s);
 fe_status fe_serve_destroy(fe_server* server);
 
+/* Block-structured meshes (Sec. 4.2 "Generalization to Block-Structured Grids").  A macro-mesh
+ * of nblocks hexahedral blocks: block b has the macro-vertices block_verts[8b + c] at its local
+ * corners c = i + 2j + 4k (i, j, k in {0,1} along its local x, y, z), trilinear geometry from the
+ * vertex coordinates vxyz (3 per vertex; every block must be right-handed) and a structured grid
+ * of dims[3b..3b+2] cells of the given degree.  Blocks that share a face must agree on its cell
+ * counts (conforming); shared faces may meet with any relative rotation or reflection.
+ * Cell-wise layout: the blocks one after the other, each block in layout 0.  No Dirichlet
+ * masking.  fe_mb_create derives the interface structure on the host from the vertex numbers:
+ * face pairs with a 3-bit relative orientation (swap, flip s, flip t), and sharing lists of the
+ * macro-edge and macro-vertex nodes with one representative copy per block.  Synchronous.
+ * FE_ERR_INVALID for non-conforming faces, left-handed blocks, or bad sizes. */
+typedef struct {
+  int nblocks, nverts, degree;
+  const int* dims;        /* 3 per block (host) */
+  const int* block_verts; /* 8 per block (host) */
+  const double* vxyz;     /* 3 per vertex (host) */
+  int device;
+} fe_mb_desc;
+typedef struct fe_mbmesh fe_mbmesh;
+fe_status fe_mb_create(const fe_mb_desc* desc, void* stream, fe_mbmesh** out);
+fe_status fe_mb_destroy(fe_mbmesh* mesh);
+/* n_cells and cellwise_len over all blocks; unique_dofs counted from the macro-topology */
+fe_status fe_mb_layout(const fe_mbmesh* mesh, fe_layout* out);
+/* counts of the inter-block structure: face pairs, macro-edge node entities, macro-vertex
+ * entities, and the largest number of blocks sharing an entity (any pointer may be NULL) */
+fe_status fe_mb_info(const fe_mbmesh* mesh, int* face_pairs, long long* edge_entities,
+                     int* vertex_entities, int* max_valence);
+/* Local apply of every block (fe_apply per block; prec FE_F64 / FE_F32, flag FE_NATIVE_F64).
+ * With FE_ASSEMBLE: the structured DSS inside every block, then the inter-block summation of
+ * Algorithm "Unstructured Inter-Block Summation" (faces, lines, vertices). */
+fe_status fe_mb_apply(const fe_mbmesh* mesh, fe_op op, fe_prec prec, const void* x, void* y,
+                      unsigned flags, void* stream);
+/* DSS of the block-structured mesh: structured passes inside every block (Algorithm
+ * "Dimensionally-Split Structured Summation"), then the inter-block summation.  r == z allowed. */
+fe_status fe_mb_dss(const fe_mbmesh* mesh, fe_prec prec, const void* r, void* z, void* stream);
+
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char* fe_last_error(void);
 

@@ -376,6 +376,7 @@ struct fe_mesh {
   float* geo32 = nullptr;
   unsigned short* geo16[2] = {nullptr, nullptr};  // bf16 / fp16 metric, scaled by gscale[op]
   float gscale[2] = {1.0f, 1.0f};                 // powers of two: Laplace terms, w detJ
+  bool tri = false;  // a block of a block-structured mesh (trilinear map of its corners)
   // recompute mode: nodal coordinates [cell][3][n3], and an L2-sized scratch for the metric of one
   // chunk of cells (per arithmetic: 0 double-word, 1 FP64, 2 FP32)
   double* xyz64 = nullptr;
@@ -411,6 +412,9 @@ fe_status fe_cuda_check(cudaError_t e, const char* what);
 #define FE_CUDA(expr, what) FE_TRY(fe_cuda_check((expr), (what)))
 
 fe_status fe_ensure_geometry(const fe_mesh* m, int prec, bool native);  // fe_mesh.cu
+// fe_mesh_create with an optional trilinear block map (8 corners, 24 doubles; null = unit cube)
+fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void* stream,
+                              fe_mesh** out);
 
 // Stream-ordered device memory from a library-owned pool of the current device (fe_mesh.cu).
 // Frees never synchronize the device; the pool keeps freed memory for reuse until fe_pool_trim.

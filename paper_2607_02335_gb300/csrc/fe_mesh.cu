@@ -98,8 +98,30 @@ struct GeoArgs {
   long long ncells;
   int mx, my, mz;
   double amp;
+  int tri;              // 1: trilinear block map of `corners` instead of the unit-cube map Phi
+  double corners[24];   // block corners c = i + 2j + 4k (x, y, z each)
   GeoTab tab;
 };
+
+// physical point of the block-reference point X in [0,1]^3
+__device__ __forceinline__ void geo_point(const GeoArgs& a, double X0, double X1, double X2,
+                                          double out[3]) {
+  if (a.tri) {
+    out[0] = out[1] = out[2] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const double w = ((c & 1) ? X0 : 1.0 - X0) * ((c & 2) ? X1 : 1.0 - X1) *
+                       ((c & 4) ? X2 : 1.0 - X2);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) out[d] = fma(w, a.corners[3 * c + d], out[d]);
+    }
+  } else {
+    const double s = a.amp * sinpi(X0) * sinpi(X1) * sinpi(X2);
+    out[0] = X0 + s;
+    out[1] = X1 + s;
+    out[2] = X2 + s;
+  }
+}
 
 template <int N>
 __global__ void __launch_bounds__(N* N* N) k_geometry(const __grid_constant__ GeoArgs a) {
@@ -117,19 +139,18 @@ __global__ void __launch_bounds__(N* N* N) k_geometry(const __grid_constant__ Ge
   const int cx = (int)(cell % a.mx), cy = (int)((cell / a.mx) % a.my),
             cz = (int)(cell / ((long long)a.mx * a.my));
   {
-    const double X0 = (cx + a.tab.t[i]) / a.mx, X1 = (cy + a.tab.t[j]) / a.my,
-                 X2 = (cz + a.tab.t[k]) / a.mz;
-    const double s = a.amp * sinpi(X0) * sinpi(X1) * sinpi(X2);
-    sX[0 * N3 + t] = X0 + s;
-    sX[1 * N3 + t] = X1 + s;
-    sX[2 * N3 + t] = X2 + s;
+    double x[3];
+    geo_point(a, (cx + a.tab.t[i]) / a.mx, (cy + a.tab.t[j]) / a.my, (cz + a.tab.t[k]) / a.mz, x);
+    sX[0 * N3 + t] = x[0];
+    sX[1 * N3 + t] = x[1];
+    sX[2 * N3 + t] = x[2];
     if (a.xyz) {  // offsets from the cell's first node (the corner, GLL node 0 is 0)
-      const double C0 = (double)cx / a.mx, C1 = (double)cy / a.my, C2 = (double)cz / a.mz;
-      const double sc = a.amp * sinpi(C0) * sinpi(C1) * sinpi(C2);
+      double c0[3];
+      geo_point(a, (double)cx / a.mx, (double)cy / a.my, (double)cz / a.mz, c0);
       double* out = a.xyz + (size_t)cell * 3 * N3;
-      out[0 * N3 + t] = (X0 + s) - (C0 + sc);
-      out[1 * N3 + t] = (X1 + s) - (C1 + sc);
-      out[2 * N3 + t] = (X2 + s) - (C2 + sc);
+      out[0 * N3 + t] = x[0] - c0[0];
+      out[1 * N3 + t] = x[1] - c0[1];
+      out[2 * N3 + t] = x[2] - c0[2];
     }
   }
   if (!a.geo) return;
@@ -377,6 +398,12 @@ void fe_mesh_drop_geo64(fe_mesh* m, cudaStream_t st) {
 }
 
 extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh** out) {
+  return fe_mesh_create_impl(d, nullptr, stream, out);
+}
+
+// corners: null for the unit-cube map Phi, else the 8 corners of a trilinear block (24 doubles)
+fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void* stream,
+                              fe_mesh** out) {
   if (!d || !out) {
     fe_set_error("fe_mesh_create: null argument");
     return FE_ERR_INVALID;
@@ -438,6 +465,11 @@ extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh
   g.my = d->my;
   g.mz = d->mz;
   g.amp = d->deform_amp;
+  if (corners) {
+    g.tri = 1;
+    for (int c = 0; c < 24; ++c) g.corners[c] = corners[c];
+    m->tri = true;
+  }
   for (int a = 0; a < m->n; ++a) {
     g.tab.t[a] = m->tab.t[a];
     g.tab.w[a] = m->tab.w[a];

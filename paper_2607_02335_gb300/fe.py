@@ -53,6 +53,12 @@ class fe_cg_result(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class fe_mb_desc(ctypes.Structure):
+    _fields_ = [("nblocks", ctypes.c_int), ("nverts", ctypes.c_int), ("degree", ctypes.c_int),
+                ("dims", ctypes.POINTER(ctypes.c_int)), ("block_verts", ctypes.POINTER(ctypes.c_int)),
+                ("vxyz", ctypes.POINTER(ctypes.c_double)), ("device", ctypes.c_int)]
+
+
 _vp, _i, _u, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double
 _MESH = ctypes.c_void_p
 _SIGS = {
@@ -77,6 +83,13 @@ _SIGS = {
     "fe_cg_solve_batched": [_i, ctypes.POINTER(_MESH), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                             ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_cg_result), _vp],
     "fe_l2_error": [_MESH, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp],
+    "fe_mb_create": [ctypes.POINTER(fe_mb_desc), _vp, ctypes.POINTER(_vp)],
+    "fe_mb_destroy": [_vp],
+    "fe_mb_layout": [_vp, ctypes.POINTER(fe_layout)],
+    "fe_mb_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_i),
+                   ctypes.POINTER(_i)],
+    "fe_mb_apply": [_vp, _i, _i, _vp, _vp, _u, _vp],
+    "fe_mb_dss": [_vp, _i, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -315,3 +328,85 @@ class Mesh:
         if history:
             return res, hist.reshape(maxit, 3)[: res.iters]
         return res
+
+
+# ---- block-structured meshes (Sec. 4.2) ---------------------------------------------------------
+def fe_mb_create(desc: fe_mb_desc, stream=None) -> int:
+    h = _vp()
+    _check(_lib.fe_mb_create(ctypes.byref(desc), _stream(stream), ctypes.byref(h)), "fe_mb_create")
+    return h.value
+
+
+def fe_mb_destroy(mesh: int) -> None:
+    _check(_lib.fe_mb_destroy(mesh), "fe_mb_destroy")
+
+
+def fe_mb_layout(mesh: int) -> fe_layout:
+    out = fe_layout()
+    _check(_lib.fe_mb_layout(mesh, ctypes.byref(out)), "fe_mb_layout")
+    return out
+
+
+def fe_mb_info(mesh: int):
+    f, v, mv = _i(), _i(), _i()
+    e = ctypes.c_longlong()
+    _check(_lib.fe_mb_info(mesh, ctypes.byref(f), ctypes.byref(e), ctypes.byref(v), ctypes.byref(mv)),
+           "fe_mb_info")
+    return {"face_pairs": f.value, "edge_entities": e.value, "vertex_entities": v.value,
+            "max_valence": mv.value}
+
+
+def fe_mb_apply(mesh: int, op: int, prec: int, x, y, flags: int = 0, stream=None) -> None:
+    _check(_lib.fe_mb_apply(mesh, op, prec, _ptr(x), _ptr(y), flags, _stream(stream)), "fe_mb_apply")
+
+
+def fe_mb_dss(mesh: int, prec: int, r, z, stream=None) -> None:
+    _check(_lib.fe_mb_dss(mesh, prec, _ptr(r), _ptr(z), _stream(stream)), "fe_mb_dss")
+
+
+class MBMesh:
+    """Block-structured mesh handle: vertex coordinates, eight corner vertices per block (local
+    corner c = i + 2j + 4k) and the cells per block direction."""
+
+    def __init__(self, vxyz, block_verts, dims, degree: int, device: int = 0, stream=None):
+        import numpy as np
+        self._v = np.ascontiguousarray(np.asarray(vxyz, dtype=np.float64).reshape(-1, 3))
+        self._b = np.ascontiguousarray(np.asarray(block_verts, dtype=np.int32).reshape(-1, 8))
+        self._d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+        desc = fe_mb_desc(len(self._b), len(self._v), degree,
+                          self._d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                          self._b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                          self._v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), device)
+        self.handle = fe_mb_create(desc, stream)
+        lay = fe_mb_layout(self.handle)
+        self.n_cells, self.cellwise_len, self.unique_dofs = lay.n_cells, lay.cellwise_len, lay.unique_dofs
+        self.device = device
+
+    def info(self):
+        return fe_mb_info(self.handle)
+
+    def empty(self, prec=FE_F64):
+        import torch
+        dt = torch.float64 if prec == FE_F64 else torch.float32
+        return torch.empty(self.cellwise_len, dtype=dt, device=f"cuda:{self.device}")
+
+    def apply(self, x, op=FE_LAPLACE, prec=FE_F64, flags=0, y=None, stream=None):
+        y = self.empty(prec) if y is None else y
+        fe_mb_apply(self.handle, op, prec, x, y, flags, stream)
+        return y
+
+    def dss(self, r, prec=FE_F64, z=None, stream=None):
+        z = self.empty(prec) if z is None else z
+        fe_mb_dss(self.handle, prec, r, z, stream)
+        return z
+
+    def close(self):
+        if self.handle:
+            fe_mb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
