@@ -200,7 +200,7 @@ def run_reference(args, rank):
 # ---------------------------------------------------------------- our arm
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("fe_apply_kernel.cuh", "fe_internal.h", "fe_apply_launch.cuh"):
+    for f in ("fe_apply_kernel.cuh", "fe_arith.h", "fe_apply_launch.cuh"):
         with open(os.path.join(ROOT, "paper_2607_02335_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -377,6 +377,7 @@ def run_ours(args, rank, world):
         extras["geometry_recompute"] = recompute_geometry(fe, torch, sweep, per_case, flush, stream,
                                                           reps)
         extras["reduced_precision_apply"] = reduced_precision_apply(fe, torch, flush, stream)
+        extras["block_structured_dss"] = multiblock_dss(fe, torch, flush, stream)
         extras["solve_mixed_vs_fp64"] = mixed_vs_fp64_solve(fe, torch)
         extras["batched"] = batched_solve(fe, torch, count=args.batch_count)
         extras["serving"] = {
@@ -467,6 +468,57 @@ def recompute_geometry(fe, torch, sweep, per_case, flush, stream, reps):
                 "time_vs_stored": round(res["volumetric_ms"] / st["volumetric_ms"], 3)})
         del x, y
         gm.close()
+    return out
+
+
+def multiblock_dss(fe, torch, flush, stream, m=32, p=3, reps=20):
+    """DSS and assembled apply of the seven-block cube-in-cube (m^3 cells of degree p per block,
+    every block frame turned at random) next to one structured mesh with the same cell count
+    (64 x 56 x 64 for m = 32): the cost of the inter-block summation (Sec. 4.2)."""
+    from paper_2607_02335_gb300 import synth as S
+
+    def med(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    out = {"workload": f"cube-in-cube, 7 blocks of {m}^3 cells, Q{p}, random block frames; "
+                       f"structured reference mesh 64x56x64 cells, Q{p}"}
+    mb = fe.MBMesh(*S.mb_cube_in_cube(m, seed=0), p)
+    r = torch.randn(mb.cellwise_len, dtype=torch.float64, device="cuda")
+    z = mb.empty()
+    info = mb.info()
+    t_dss = med(lambda: fe.fe_mb_dss(mb.handle, fe.FE_F64, r, z, stream))
+    t_asm = med(lambda: fe.fe_mb_apply(mb.handle, fe.FE_LAPLACE, fe.FE_F64, r, z, fe.FE_ASSEMBLE,
+                                        stream))
+    out["block_structured"] = {"unique_dofs": mb.unique_dofs, "cellwise_dofs": mb.cellwise_len,
+                               "interfaces": info, "dss_ms": round(t_dss, 4),
+                               "dss_gdofs_unique": round(mb.unique_dofs / t_dss / 1e6, 3),
+                               "laplace_assembled_ms": round(t_asm, 4),
+                               "laplace_assembled_gdofs_unique": round(mb.unique_dofs / t_asm / 1e6, 3)}
+    del r, z
+    mb.close()
+    gm = fe.Mesh((64, 56, 64), p)
+    r = torch.randn(gm.cellwise_len, dtype=torch.float64, device="cuda")
+    z = gm.empty()
+    t_dss = med(lambda: fe.fe_dss(gm.handle, fe.FE_F64, r, z, stream))
+    t_asm = med(lambda: fe.fe_apply(gm.handle, fe.FE_LAPLACE, fe.FE_F64, r, z, fe.FE_ASSEMBLE,
+                                     stream))
+    out["structured"] = {"unique_dofs": gm.unique_dofs, "cellwise_dofs": gm.cellwise_len,
+                         "dss_ms": round(t_dss, 4),
+                         "dss_gdofs_unique": round(gm.unique_dofs / t_dss / 1e6, 3),
+                         "laplace_assembled_ms": round(t_asm, 4),
+                         "laplace_assembled_gdofs_unique": round(gm.unique_dofs / t_asm / 1e6, 3)}
+    del r, z
+    gm.close()
     return out
 
 

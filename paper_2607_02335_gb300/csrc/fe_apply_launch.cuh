@@ -168,6 +168,10 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
     if (m->d.geom_mode == FE_GEOM_RECOMPUTE) {
       FE_TRY((L.op == FE_LAPLACE ? launch_recompute<N, V, FE_LAPLACE>(a, L, xyz, scratch)
                                  : launch_recompute<N, V, FE_MASS>(a, L, xyz, scratch)));
+      if (L.assemble && L.brick_out) {
+        L.brick_out[0] = L.brick_out[1] = 1;
+        return FE_OK;
+      }
       return L.assemble ? fe_launch_dss(m, PREC, L.y, L.st) : FE_OK;
     }
   }
@@ -184,6 +188,11 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
   else
     FE_TRY((launch_geom<N, V, false>(a, L.op, affine, L.st)));
   if (!L.assemble) return FE_OK;
+  if (L.brick_out) {  // the caller runs the passes (one launch over many blocks)
+    L.brick_out[0] = fuse ? Brick<N>::BX : 1;
+    L.brick_out[1] = fuse ? Brick<N>::BY : 1;
+    return FE_OK;
+  }
   return fuse ? fe_launch_dss_strided(m, PREC, L.y, Brick<N>::BX, Brick<N>::BY, L.st)
               : fe_launch_dss(m, PREC, L.y, L.st);
 }

@@ -592,9 +592,7 @@ extern "C" fe_status fe_mb_dss(const fe_mbmesh* M, fe_prec prec, const void* r, 
   const size_t es = prec == FE_F64 ? sizeof(double) : sizeof(float);
   if (r != z)
     FE_CUDA(cudaMemcpyAsync(z, r, (size_t)M->ncw * es, cudaMemcpyDeviceToDevice, st), "mb dss copy");
-  const long long n3 = (long long)M->n * M->n * M->n;
-  for (int b = 0; b < M->nblocks; ++b)
-    FE_TRY(fe_launch_dss(M->blocks[b], prec, (char*)z + (size_t)M->off[b] * n3 * es, st));
+  FE_TRY(fe_launch_dss_blocks(M->blocks.data(), M->off.data(), M->nblocks, prec, z, 1, 1, st));
   return prec == FE_F64 ? interblock<double>(M, (double*)z, st) : interblock<float>(M, (float*)z, st);
 }
 
@@ -619,16 +617,21 @@ extern "C" fe_status fe_mb_apply(const fe_mbmesh* M, fe_op op, fe_prec prec, con
   cudaStream_t st = (cudaStream_t)stream;
   const bool native = (flags & FE_NATIVE_F64) && prec == FE_F64;
   const long long n3 = (long long)M->n * M->n * M->n;
+  int brick[2] = {1, 1};
   for (int b = 0; b < M->nblocks; ++b) {
     const fe_mesh* bm = M->blocks[b];
     FE_TRY(fe_ensure_geometry(bm, prec, native));
     const size_t o = (size_t)M->off[b] * n3 * es;
-    ApplyLaunch L{bm, (int)op, xb + o, (char*)y + o, st, nullptr, (flags & FE_ASSEMBLE) != 0};
+    ApplyLaunch L{bm, (int)op, xb + o, (char*)y + o, st, nullptr, (flags & FE_ASSEMBLE) != 0,
+                  brick};
     if (prec == FE_F64)
       FE_TRY(native ? fe_launch_apply_f64native(L) : fe_launch_apply_f64dw(L));
     else
       FE_TRY(fe_launch_apply_f32(L));
   }
   if (!(flags & FE_ASSEMBLE)) return FE_OK;
+  // structured passes of all blocks (between bricks where the kernel fused), then inter-block
+  FE_TRY(fe_launch_dss_blocks(M->blocks.data(), M->off.data(), M->nblocks, prec, y, brick[0],
+                              brick[1], st));
   return prec == FE_F64 ? interblock<double>(M, (double*)y, st) : interblock<float>(M, (float*)y, st);
 }

@@ -14,42 +14,70 @@
 // ---------------------------------------------------------------------------------------------
 // stride s > 1 (x and y only): just the interfaces whose left cell index is s-1 mod s, the
 // boundaries between bricks of s cells along that axis (nb = (m-1)/s of them per line)
+// the node pair of work item e of one axis pass (cells L, R and local nodes locL, locR)
 template <class S>
-__global__ void k_dss_pass(S* __restrict__ v, int axis, int n, int mx, int my, int mz, int stride,
-                           long long nwork) {
+__device__ __forceinline__ void dss_pair(S* __restrict__ v, int axis, int n, int mx, int my,
+                                         int stride, long long e) {
   const int p = n - 1, n2 = n * n, n3 = n2 * n;
-  const int nbx = (mx - 1) / stride, nby = (my - 1) / stride;
+  const int f = (int)(e % n2);
+  const long long q = e / n2;
+  const int fa = f % n, fb = f / n;
+  long long L, R;
+  int locL, locR;
+  if (axis == 0) {  // faces normal to x
+    const int nbx = (mx - 1) / stride;
+    const long long u = q % nbx, r = q / nbx;
+    L = r * mx + (u * stride + stride - 1);  // r = cz*my + cy
+    R = L + 1;
+    locL = (fb * n + fa) * n + p;
+    locR = (fb * n + fa) * n + 0;
+  } else if (axis == 1) {  // faces normal to y
+    const int nby = (my - 1) / stride;
+    const long long cx = q % mx, r = q / mx, u = r % nby, cz = r / nby;
+    const long long cyL = u * stride + stride - 1;
+    L = (cz * my + cyL) * mx + cx;
+    R = L + mx;
+    locL = (fb * n + p) * n + fa;
+    locR = (fb * n + 0) * n + fa;
+  } else {  // faces normal to z
+    L = q;  // q = (czL*my + cy)*mx + cx
+    R = L + (long long)mx * my;
+    locL = (p * n + fb) * n + fa;
+    locR = (0 * n + fb) * n + fa;
+  }
+  S* pl = v + L * n3 + locL;
+  S* pr = v + R * n3 + locR;
+  const S s = *pl + *pr;
+  *pl = s;
+  *pr = s;
+}
+
+template <class S>
+__global__ void k_dss_pass(S* __restrict__ v, int axis, int n, int mx, int my, int stride,
+                           long long nwork) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nwork;
+       e += (long long)gridDim.x * blockDim.x)
+    dss_pair(v, axis, n, mx, my, stride, e);
+}
+
+// One axis pass over every block of a block-structured mesh in one launch: block b owns the work
+// items [first[b], first[b+1]) and the cell-wise slice starting at cell off[b].
+constexpr int DSS_MAXB = 32;
+struct DssBlocks {
+  int nb, stride;  // stride: brick size along this axis (x and y passes after a fused apply)
+  int mx[DSS_MAXB], my[DSS_MAXB];
+  long long off[DSS_MAXB], first[DSS_MAXB + 1];
+};
+
+template <class S>
+__global__ void k_dss_pass_blocks(S* __restrict__ v, int axis, int n,
+                                  const __grid_constant__ DssBlocks B) {
+  const long long n3 = (long long)n * n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < B.first[B.nb];
        e += (long long)gridDim.x * blockDim.x) {
-    const int f = (int)(e % n2);
-    const long long q = e / n2;
-    const int fa = f % n, fb = f / n;
-    long long L, R;
-    int locL, locR;
-    if (axis == 0) {  // faces normal to x
-      const long long u = q % nbx, r = q / nbx;
-      L = r * mx + (u * stride + stride - 1);  // r = cz*my + cy
-      R = L + 1;
-      locL = (fb * n + fa) * n + p;
-      locR = (fb * n + fa) * n + 0;
-    } else if (axis == 1) {  // faces normal to y
-      const long long cx = q % mx, r = q / mx, u = r % nby, cz = r / nby;
-      const long long cyL = u * stride + stride - 1;
-      L = (cz * my + cyL) * mx + cx;
-      R = L + mx;
-      locL = (fb * n + p) * n + fa;
-      locR = (fb * n + 0) * n + fa;
-    } else {  // faces normal to z
-      L = q;  // q = (czL*my + cy)*mx + cx
-      R = L + (long long)mx * my;
-      locL = (p * n + fb) * n + fa;
-      locR = (0 * n + fb) * n + fa;
-    }
-    S* pl = v + L * n3 + locL;
-    S* pr = v + R * n3 + locR;
-    const S s = *pl + *pr;
-    *pl = s;
-    *pr = s;
+    int b = 0;
+    while (e >= B.first[b + 1]) ++b;
+    dss_pair(v + B.off[b] * n3, axis, n, B.mx[b], B.my[b], B.stride, e - B.first[b]);
   }
 }
 
@@ -70,7 +98,7 @@ static fe_status dss_t(const fe_mesh* m, S* v, int sx, int sy, cudaStream_t st) 
                              (long long)mx * my * (mz - 1) * n2};
   for (int axis = 2; axis >= 0; --axis) {  // z, y, x
     if (work[axis] <= 0) continue;
-    k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, mz, stride[axis],
+    k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, stride[axis],
                                                              work[axis]);
   }
   return fe_cuda_check(cudaGetLastError(), "dss launch");
@@ -90,6 +118,50 @@ fe_status fe_launch_dss_strided(const fe_mesh* m, int prec, void* v, int bx, int
 
 fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st) {
   return fe_launch_dss_strided(m, prec, v, 1, 1, st);
+}
+
+template <class S>
+static fe_status dss_blocks_t(const fe_mesh* const* blocks, const long long* off, int nb, S* v,
+                              int sx, int sy, cudaStream_t st) {
+  const int n = blocks[0]->n, n2 = n * n;
+  for (int axis = 2; axis >= 0; --axis) {  // z, y, x
+    DssBlocks B;
+    std::memset(&B, 0, sizeof(B));
+    B.nb = nb;
+    B.stride = axis == 0 ? sx : (axis == 1 ? sy : 1);
+    for (int b = 0; b < nb; ++b) {
+      const int mx = blocks[b]->d.mx, my = blocks[b]->d.my, mz = blocks[b]->d.mz;
+      B.mx[b] = mx;
+      B.my[b] = my;
+      B.off[b] = off[b];
+      const long long w = axis == 0 ? (long long)((mx - 1) / sx) * my * mz * n2
+                          : axis == 1 ? (long long)mx * ((my - 1) / sy) * mz * n2
+                                      : (long long)mx * my * (mz - 1) * n2;
+      B.first[b + 1] = B.first[b] + w;
+    }
+    if (B.first[nb] > 0)
+      k_dss_pass_blocks<S><<<grid_cap(B.first[nb], 256), 256, 0, st>>>(v, axis, n, B);
+  }
+  return fe_cuda_check(cudaGetLastError(), "dss launch");
+}
+
+fe_status fe_launch_dss_blocks(const fe_mesh* const* blocks, const long long* off, int nb,
+                               int prec, void* v, int sx, int sy, cudaStream_t st) {
+  if (sx < 1 || sy < 1) {
+    fe_set_error("dss: bad brick %d x %d", sx, sy);
+    return FE_ERR_INVALID;
+  }
+  if (nb > DSS_MAXB) {  // one launch triple per block
+    const size_t es = prec == FE_F64 ? sizeof(double) : sizeof(float);
+    for (int b = 0; b < nb; ++b)
+      FE_TRY(fe_launch_dss_strided(blocks[b], prec, (char*)v + (size_t)off[b] * blocks[b]->n3 * es,
+                                   sx, sy, st));
+    return FE_OK;
+  }
+  if (prec == FE_F64) return dss_blocks_t<double>(blocks, off, nb, (double*)v, sx, sy, st);
+  if (prec == FE_F32) return dss_blocks_t<float>(blocks, off, nb, (float*)v, sx, sy, st);
+  fe_set_error("dss: unsupported precision %d", prec);
+  return FE_ERR_INVALID;
 }
 
 // ---------------------------------------------------------------------------------------------
