@@ -441,3 +441,73 @@ class MBMesh:
     def apply_assembled(self, op: int, xg, nthreads: int = 0):
         """A_CG x_glob = G^T (blockdiag A_K) G x_glob (Sec. 3.1)."""
         return self.scatter(self.apply_local(op, self.gather(xg), nthreads))
+
+
+class Packed:
+    """2^3 packing of a structured mesh (Sec. 2.2, the optional storage unit of Table
+    "tab:memory_overhead"): each unit stores the (2p+1)^3 distinct nodes of a 2x2x2 cluster of
+    cells, unit (ux, uy, uz) lexicographic over (mx/2, my/2, mz/2), local node (i, j, k) at
+    (k N + j) N + i with N = 2p+1.  Built on the structured oracle: P maps a unit vector to the
+    cell-wise copies of its eight cells, so the unit-level operators are the definitions
+    P^T A_K P (local), G_u = P^{-1}-free gather from global nodes, and S_u = G_u G_u^T."""
+
+    def __init__(self, mesh: Mesh):
+        if mesh.mx % 2 or mesh.my % 2 or mesh.mz % 2:
+            raise ValueError("packing needs even cell counts")
+        self.mesh = mesh
+        p, n = mesh.p, mesh.n
+        self.N = N = 2 * p + 1
+        self.ux, self.uy, self.uz = mesh.mx // 2, mesh.my // 2, mesh.mz // 2
+        self.n_units = self.ux * self.uy * self.uz
+        self.length = self.n_units * N ** 3
+        Nx, Ny = mesh.mx * p + 1, mesh.my * p + 1
+        # global node of every unit-storage entry
+        u = np.arange(self.n_units)
+        ux, uy, uz = u % self.ux, (u // self.ux) % self.uy, u // (self.ux * self.uy)
+        loc = np.arange(N ** 3)
+        i, j, k = loc % N, (loc // N) % N, loc // (N * N)
+        gx = (2 * p * ux)[:, None] + i[None, :]
+        gy = (2 * p * uy)[:, None] + j[None, :]
+        gz = (2 * p * uz)[:, None] + k[None, :]
+        self.gid = ((gz * Ny + gy) * Nx + gx).ravel()
+        # P: for every cell-wise entry, the unit-storage entry holding the same node
+        c = np.arange(mesh.mx * mesh.my * mesh.mz)
+        cx, cy, cz = c % mesh.mx, (c // mesh.mx) % mesh.my, c // (mesh.mx * mesh.my)
+        cl = np.arange(n ** 3)
+        ci, cj, ck = cl % n, (cl // n) % n, cl // (n * n)
+        unit = ((cz // 2) * self.uy + cy // 2) * self.ux + cx // 2
+        li = (p * (cx % 2))[:, None] + ci[None, :]
+        lj = (p * (cy % 2))[:, None] + cj[None, :]
+        lk = (p * (cz % 2))[:, None] + ck[None, :]
+        self.P = (unit[:, None] * N ** 3 + (lk * N + lj) * N + li).ravel()
+
+    def gather(self, xg):
+        return np.asarray(xg, dtype=np.float64)[self.gid]
+
+    def scatter(self, yu):
+        yg = np.zeros(or_n_unique(self.mesh))
+        np.add.at(yg, self.gid, np.asarray(yu, dtype=np.float64))
+        return yg
+
+    def dss(self, yu):
+        return self.gather(self.scatter(yu))
+
+    def multiplicity(self):
+        return self.gather(np.bincount(self.gid, minlength=or_n_unique(self.mesh)).astype(float))
+
+    def to_cellwise(self, xu):
+        return np.asarray(xu, dtype=np.float64)[self.P]
+
+    def from_cellwise(self, yc):
+        yu = np.zeros(self.length)
+        np.add.at(yu, self.P, np.asarray(yc, dtype=np.float64))
+        return yu
+
+    def apply_local(self, op: int, xu, nthreads: int = 0):
+        """sum over the unit's cells K of P_K^T A_K P_K x_unit (Dirichlet rows/columns as in the
+        structured oracle)."""
+        return self.from_cellwise(apply_local(self.mesh, op, self.to_cellwise(xu), nthreads))
+
+
+def or_n_unique(mesh: Mesh) -> int:
+    return int(_L().or_n_unique(mesh.ref))
