@@ -83,14 +83,27 @@ typedef struct {
   int geom_mode;     /* FE_GEOM_* */
   int dirichlet;     /* 1 = homogeneous Dirichlet on the whole boundary */
   int device;        /* CUDA device ordinal */
+  int layout;        /* storage of cell-wise vectors: FE_LAYOUT_CELLS or FE_LAYOUT_PACKED2 */
 } fe_mesh_desc;
 
+/* Storage layouts (Sec. 2.2 "Persistent cell-wise storage", Table "tab:memory_overhead").
+ *  FE_LAYOUT_CELLS   (0) -- one cell per storage unit: cell-major, cells lexicographic, n^3 values
+ *                          per cell, local node (i,j,k) at (k n + j) n + i.
+ *  FE_LAYOUT_PACKED2 (1) -- a 2x2x2 cluster of cells per storage unit with its interior interface
+ *                          nodes stored once: units lexicographic over (mx/2, my/2, mz/2),
+ *                          (2p+1)^3 values per unit, local node (i,j,k) at (k N + j) N + i with
+ *                          N = 2p+1.  Even cell counts, degree 1 to 3, FE_GEOM_STORED or
+ *                          FE_GEOM_AFFINE.  fe_apply (its unassembled output is assembled inside
+ *                          each unit), fe_dss and fe_pairing accept it; the solvers, fe_diag,
+ *                          fe_gather, fe_rhs and fe_l2_error take FE_LAYOUT_CELLS meshes only. */
+enum { FE_LAYOUT_CELLS = 0, FE_LAYOUT_PACKED2 = 1 };
+
 typedef struct {
-  long long n_cells;        /* mx*my*mz */
-  long long nodes_per_cell; /* (p+1)^3 */
-  long long cellwise_len;   /* n_cells * nodes_per_cell (no padding in layout 0) */
+  long long n_cells;        /* storage units: mx*my*mz cells (layout 0), mx*my*mz/8 units (1) */
+  long long nodes_per_cell; /* values per storage unit: (p+1)^3, or (2p+1)^3 packed */
+  long long cellwise_len;   /* n_cells * nodes_per_cell: the length of every mesh vector */
   long long unique_dofs;    /* (mx p + 1)(my p + 1)(mz p + 1), Sec. 5 closed form */
-  int layout_id;            /* 0 = cell-major lexicographic (see above) */
+  int layout_id;            /* FE_LAYOUT_CELLS or FE_LAYOUT_PACKED2 */
 } fe_layout;
 
 typedef struct fe_mesh fe_mesh;

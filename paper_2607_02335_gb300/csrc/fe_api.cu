@@ -87,6 +87,10 @@ extern "C" fe_status fe_diag(const fe_mesh* m, fe_op op, double* d, void* stream
     return FE_ERR_INVALID;
   }
   FE_TRY(check_vec(m, d, "fe_diag d"));
+  if (m->packed) {
+    fe_set_error("fe_diag: FE_LAYOUT_CELLS meshes only");
+    return FE_ERR_INVALID;
+  }
   if (op != FE_LAPLACE && op != FE_MASS) {
     fe_set_error("fe_diag: unknown operator %d", (int)op);
     return FE_ERR_INVALID;

@@ -212,12 +212,31 @@ struct CellPos {
   bool active;
 };
 
-// Cell of tile slot cl.  Unfused: cells cell0 + cl (below ncells).  Fused: cell0 is the brick
-// index over (bricks along x, bricks along y, z-layers).
-template <int N, bool FUSE, class A>
+// Tile placement modes of an apply launch
+enum { MODE_CELLS = 0, MODE_BRICK = 1, MODE_PACKED = 2 };
+// 2^3-packed storage units (Sec. 2.2): 8 cells per unit, whole units per CTA
+template <int N>
+struct Packed {
+  static constexpr int P = N - 1, NU = 2 * N - 1, NU3 = NU * NU * NU;
+  static constexpr int UPB = Cfg<N>::CPB / 8;  // units per CTA
+};
+
+// Cell of tile slot cl.  MODE_CELLS: cells cell0 + cl (below ncells).  MODE_BRICK: cell0 is the
+// brick index over (bricks along x, bricks along y, z-layers).  MODE_PACKED: cell0 is the first
+// storage unit of the CTA; slot cl is sub-cell cl % 8 (x fastest) of unit cell0 + cl / 8.
+template <int N, int MODE, class A>
 __device__ __forceinline__ CellPos cell_pos(const A& a, long long cell0, int cl) {
   CellPos c;
-  if constexpr (FUSE) {  // brick index < 2^31: 32-bit index arithmetic
+  if constexpr (MODE == MODE_PACKED) {
+    const int ux_n = a.mx / 2, uy_n = a.my / 2;
+    const long long u = cell0 + cl / 8;
+    const int sub = cl % 8;
+    c.cx = (int)(u % ux_n) * 2 + (sub & 1);
+    c.cy = (int)((u / ux_n) % uy_n) * 2 + ((sub >> 1) & 1);
+    c.cz = (int)(u / ((long long)ux_n * uy_n)) * 2 + ((sub >> 2) & 1);
+    c.active = cl / 8 < Packed<N>::UPB && u < a.ncells / 8;
+    c.cell = ((long long)c.cz * a.my + c.cy) * a.mx + c.cx;
+  } else if constexpr (MODE == MODE_BRICK) {  // brick index < 2^31: 32-bit index arithmetic
     constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
     const unsigned nbx = (unsigned)(a.mx + BX - 1) / BX, nby = (unsigned)(a.my + BY - 1) / BY;
     const unsigned b = (unsigned)cell0, rb = b / nbx;
@@ -249,7 +268,7 @@ __device__ __forceinline__ void brick_sums(const Sm<V>& s, int cb, int cl, int l
   constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
   const int dx = cl % BX, dy = cl / BX;
   const int mx = a.mx, my = a.my;
-  const CellPos c = cell_pos<N, true>(a, cell0, cl);  // recomputed: nothing held across sweeps
+  const CellPos c = cell_pos<N, MODE_BRICK>(a, cell0, cl);  // recomputed: nothing held across sweeps
   if (c.active && dx < BX - 1 && c.cx + 1 < mx) {
     const int eL = cb + lb * C::PS + la * C::RS + (N - 1);
     const int eR = cb + C::CS + lb * C::PS + la * C::RS;
@@ -289,7 +308,7 @@ __device__ __forceinline__ void sweep_rolled(const EO<N, V>& M, const V (&in)[N]
   eo_line<N, V, SIG, true>(M, in, [&](int q, V v) { s.put(base + q * stride, v); });
 }
 
-template <int N, class V, int OP, int GEOM, bool FUSE>
+template <int N, class V, int OP, int GEOM, int MODE>
 __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
                                                    long long cell0, unsigned char* smraw,
                                                    int tile_stride) {
@@ -306,7 +325,7 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
   const int lt = t - cl * N2;
   const int la = lt % N, lb = lt / N;
   const int cb = cl * C::CS;
-  const CellPos pos = cell_pos<N, FUSE>(a, cell0, cl);
+  const CellPos pos = cell_pos<N, MODE>(a, cell0, cl);
   const long long cell = pos.cell;
   const bool active = pos.active;
   const long long gbase = cell * N3;
@@ -431,7 +450,7 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
   load_line(s0, by, RS, in);
   sweep_rolled<N, V, 1>(tab.eVT, in, s0, by, RS);
   __syncthreads();
-  if constexpr (FUSE) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
+  if constexpr (MODE == MODE_BRICK) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
   if (active) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -447,12 +466,13 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
 // threads.  Threads beyond that (a CTA wider than the tile, as in the batched persistent kernel)
 // work on a spare slot of the tile that nobody reads and still reach every barrier; the caller
 // then sizes each array tile_stride = TILE + CS.
-template <int N, class V, int OP, int GEOM, bool FUSE = false>
+template <int N, class V, int OP, int GEOM, int MODE = MODE_CELLS>
 __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
                                             long long cell0, unsigned char* smraw,
                                             int tile_stride) {
-  if constexpr (N >= FE_ROLL_MINN) {
-    apply_cells_rolled<N, V, OP, GEOM, FUSE>(a, tab, cell0, smraw, tile_stride);
+  static_assert(MODE != MODE_PACKED || N < FE_ROLL_MINN, "packed units: unrolled degrees only");
+  if constexpr (N >= FE_ROLL_MINN && MODE != MODE_PACKED) {
+    apply_cells_rolled<N, V, OP, GEOM, MODE>(a, tab, cell0, smraw, tile_stride);
     return;
   }
   using T = NT<V>;
@@ -468,7 +488,7 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   const int lt = t - cl * N2;
   const int la = lt % N, lb = lt / N;  // line coordinates (a, b) of this thread
   const int cb = cl * C::CS;           // this cell's offset in the tile
-  const CellPos pos = cell_pos<N, FUSE>(a, cell0, cl);
+  const CellPos pos = cell_pos<N, MODE>(a, cell0, cl);
   const long long cell = pos.cell;
   const bool active = pos.active;
   const long long gbase = cell * N3;
@@ -486,10 +506,22 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   auto masked = [&](int k) { return bnd_line || (k == 0 && bnd_k0) || (k == N - 1 && bnd_k1); };
 
   // ---- load x (z-line owner, coalesced) and interpolate along z in registers
+  // (packed: the sub-cell's z-line inside its storage unit of (2n-1)^3 nodes)
+  auto xaddr = [&](int k) -> long long {
+    if constexpr (MODE == MODE_PACKED) {
+      constexpr int P = Packed<N>::P, NU = Packed<N>::NU;
+      const int sub = cl % 8;
+      return (cell0 + cl / 8) * Packed<N>::NU3 +
+             ((long long)(((sub >> 2) & 1) * P + k) * NU + ((sub >> 1) & 1) * P + lb) * NU +
+             (sub & 1) * P + la;
+    } else {
+      return gbase + k * N2 + lt;
+    }
+  };
   V u[N], w[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    V v = active ? T::load_stream(a.x + gbase + k * N2 + lt) : T::zero();
+    V v = active ? T::load_stream(a.x + xaddr(k)) : T::zero();
     u[k] = masked(k) ? T::zero() : v;
   }
   // low degrees: issue the metric loads now so that their latency hides behind the sweeps
@@ -628,7 +660,37 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   __syncthreads();
   tile_sweep<N, V, 1, 1>(s0, cb, la, lb, tab.eVT);
   __syncthreads();
-  if constexpr (FUSE) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
+  if constexpr (MODE == MODE_BRICK) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
+  if constexpr (MODE == MODE_PACKED) {
+    // unit output: every stored node sums the copies of the sub-cells that contain it (fixed
+    // order), the unit-internal part of the assembly
+    constexpr int P = Packed<N>::P, NU = Packed<N>::NU, NU3 = Packed<N>::NU3, UT = 8 * N2;
+    const int us = cl / 8, ut = t - us * UT;
+    const long long unit = cell0 + us;
+    if (us < Packed<N>::UPB && unit < a.ncells / 8) {
+      const int ux_n = a.mx / 2, uy_n = a.my / 2;
+      const int gx0 = (int)(unit % ux_n) * 2 * P, gy0 = (int)((unit / ux_n) % uy_n) * 2 * P,
+                gz0 = (int)(unit / ((long long)ux_n * uy_n)) * 2 * P;
+      for (int e = ut; e < NU3; e += UT) {
+        const int i = e % NU, j = (e / NU) % NU, k = e / (NU * NU);
+        V acc = T::zero();
+        for (int sz = (k > P ? 1 : 0); sz <= (k < P ? 0 : 1); ++sz)
+          for (int sy = (j > P ? 1 : 0); sy <= (j < P ? 0 : 1); ++sy)
+            for (int sx = (i > P ? 1 : 0); sx <= (i < P ? 0 : 1); ++sx) {
+              const int slot = us * 8 + sz * 4 + sy * 2 + sx;
+              acc = T::add(acc, s0.get(slot * C::CS + zl<N>(i - sx * P, j - sy * P, k - sz * P)));
+            }
+        if (a.dirichlet) {
+          const int gx = gx0 + i, gy = gy0 + j, gz = gz0 + k;
+          if (gx == 0 || gx == a.mx * P || gy == 0 || gy == a.my * P || gz == 0 || gz == a.mz * P)
+            acc = T::zero();
+        }
+        if constexpr (T::LOWP) acc.v *= a.oscale;
+        T::store(a.y + unit * NU3 + e, acc);
+      }
+    }
+    return;
+  }
   if (active) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -645,13 +707,18 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 #else
 #define FE_APPLY_BOUNDS __launch_bounds__(Cfg<N>::THREADS)
 #endif
-template <int N, class V, int OP, int GEOM, bool FUSE>
+template <int N, class V, int OP, int GEOM, int MODE>
 __global__ void FE_APPLY_BOUNDS k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.skip && *(volatile const int*)a.skip) return;  // uniform over the grid
-  const long long cell0 =
-      FUSE ? (long long)blockIdx.x : a.c.cell_base + (long long)blockIdx.x * Cfg<N>::CPB;
-  apply_cells<N, V, OP, GEOM, FUSE>(a.c, a.tab, cell0, smraw, Cfg<N>::TILE);
+  long long cell0;
+  if constexpr (MODE == MODE_BRICK)
+    cell0 = (long long)blockIdx.x;
+  else if constexpr (MODE == MODE_PACKED)
+    cell0 = (long long)blockIdx.x * Packed<N>::UPB;
+  else
+    cell0 = a.c.cell_base + (long long)blockIdx.x * Cfg<N>::CPB;
+  apply_cells<N, V, OP, GEOM, MODE>(a.c, a.tab, cell0, smraw, Cfg<N>::TILE);
 }
 
 template <int N, class V>

@@ -61,11 +61,11 @@ Tab1D<N, V> make_tab(const HostTab& h) {
   return t;
 }
 
-template <int N, class V, int OP, int GEOM, bool FUSE = false>
+template <int N, class V, int OP, int GEOM, int MODE = MODE_CELLS>
 static fe_status launch_one(const ApplyArgs<N, V>& a, cudaStream_t st) {
   using C = Cfg<N>;
   const size_t smem = apply_smem_bytes<N, V>(OP);
-  auto kern = k_apply<N, V, OP, GEOM, FUSE>;
+  auto kern = k_apply<N, V, OP, GEOM, MODE>;
   static bool attr_done[64] = {};  // one attribute call per instantiation and device
   int dev = 0;
   FE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -76,10 +76,12 @@ static fe_status launch_one(const ApplyArgs<N, V>& a, cudaStream_t st) {
   }
   long long blocks;
   int threads = C::THREADS;
-  if constexpr (FUSE) {
+  if constexpr (MODE == MODE_BRICK) {
     constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
     blocks = (long long)((a.c.mx + BX - 1) / BX) * ((a.c.my + BY - 1) / BY) * a.c.mz;
     threads = BX * BY * C::N2;
+  } else if constexpr (MODE == MODE_PACKED) {
+    blocks = (a.c.ncells / 8 + Packed<N>::UPB - 1) / Packed<N>::UPB;
   } else {
     blocks = (a.c.ncells - a.c.cell_base + C::CPB - 1) / C::CPB;
   }
@@ -123,15 +125,15 @@ static fe_status launch_recompute(ApplyArgs<N, V> a, const ApplyLaunch& L,
 }
 
 // the kernel of (operator, geometry mode); 16-bit operand types have stored geometry only
-template <int N, class V, bool FUSE>
+template <int N, class V, int MODE>
 static fe_status launch_geom(const ApplyArgs<N, V>& a, int op, bool affine, cudaStream_t st) {
   if constexpr (!NT<V>::LOWP) {
     if (affine)
-      return op == FE_LAPLACE ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K, FUSE>(a, st)
-                              : launch_one<N, V, FE_MASS, GEOM_AFFINE_K, FUSE>(a, st);
+      return op == FE_LAPLACE ? launch_one<N, V, FE_LAPLACE, GEOM_AFFINE_K, MODE>(a, st)
+                              : launch_one<N, V, FE_MASS, GEOM_AFFINE_K, MODE>(a, st);
   }
-  return op == FE_LAPLACE ? launch_one<N, V, FE_LAPLACE, GEOM_STORED_K, FUSE>(a, st)
-                          : launch_one<N, V, FE_MASS, GEOM_STORED_K, FUSE>(a, st);
+  return op == FE_LAPLACE ? launch_one<N, V, FE_LAPLACE, GEOM_STORED_K, MODE>(a, st)
+                          : launch_one<N, V, FE_MASS, GEOM_STORED_K, MODE>(a, st);
 }
 
 template <int N, class V>
@@ -176,6 +178,20 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
     }
   }
   const bool affine = m->d.geom_mode == FE_GEOM_AFFINE;
+  if (m->packed) {  // 2^3-packed storage units: unit-internal assembly in the kernel
+    if constexpr (N < FE_ROLL_MINN && N <= 4) {
+      FE_TRY((launch_geom<N, V, MODE_PACKED>(a, L.op, affine, L.st)));
+      if (!L.assemble) return FE_OK;
+      if (L.brick_out) {
+        L.brick_out[0] = L.brick_out[1] = 1;
+        return FE_OK;
+      }
+      return fe_launch_dss(m, PREC, L.y, L.st);
+    } else {
+      fe_set_error("apply: packed storage units are provided for degrees 1 to 3");
+      return FE_ERR_INVALID;
+    }
+  }
 // Assembled applies sum the intra-brick interfaces in the kernel up to n = FE_FUSE_MAXN.  Above it
 // the bricks hold fewer cells than the unfused tile (n = 6, 7) or the kernel needs more
 // registers, and the measured assembled time was no better than apply + full DSS.
@@ -184,9 +200,9 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
 #endif
   const bool fuse = L.assemble && N <= FE_FUSE_MAXN;
   if (fuse)
-    FE_TRY((launch_geom<N, V, true>(a, L.op, affine, L.st)));
+    FE_TRY((launch_geom<N, V, MODE_BRICK>(a, L.op, affine, L.st)));
   else
-    FE_TRY((launch_geom<N, V, false>(a, L.op, affine, L.st)));
+    FE_TRY((launch_geom<N, V, MODE_CELLS>(a, L.op, affine, L.st)));
   if (!L.assemble) return FE_OK;
   if (L.brick_out) {  // the caller runs the passes (one launch over many blocks)
     L.brick_out[0] = fuse ? Brick<N>::BX : 1;

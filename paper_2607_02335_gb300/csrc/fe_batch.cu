@@ -892,7 +892,8 @@ extern "C" fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes
       fe_set_error("fe_cg_solve_batched: problem %d: null or misaligned argument", i);
       return FE_ERR_INVALID;
     }
-    if (meshes[i]->d.geom_mode == FE_GEOM_RECOMPUTE || meshes[i]->d.device != meshes[0]->d.device) {
+    if (meshes[i]->d.geom_mode == FE_GEOM_RECOMPUTE || meshes[i]->packed ||
+        meshes[i]->d.device != meshes[0]->d.device) {
       fe_set_error("fe_cg_solve_batched: problem %d: needs stored/affine geometry on one device", i);
       return FE_ERR_INVALID;
     }

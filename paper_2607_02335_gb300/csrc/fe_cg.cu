@@ -572,6 +572,10 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
                  opts->rtol, opts->mixed);
     return FE_ERR_INVALID;
   }
+  if (m->packed) {
+    fe_set_error("fe_cg_solve: FE_LAYOUT_CELLS meshes only");
+    return FE_ERR_INVALID;
+  }
   if (lowp && m->d.geom_mode != FE_GEOM_STORED) {
     fe_set_error("fe_cg_solve: a 16-bit inner operator needs FE_GEOM_STORED geometry");
     return FE_ERR_INVALID;

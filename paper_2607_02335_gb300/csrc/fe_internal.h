@@ -56,6 +56,10 @@ struct fe_mesh {
   unsigned short* geo16[2] = {nullptr, nullptr};  // bf16 / fp16 metric, scaled by gscale[op]
   float gscale[2] = {1.0f, 1.0f};                 // powers of two: Laplace terms, w detJ
   bool tri = false;  // a block of a block-structured mesh (trilinear map of its corners)
+  // storage grid of the vectors (FE_LAYOUT_PACKED2: units of 2x2x2 cells with sn = 2p+1 nodes per
+  // side; otherwise the cells with sn = n) -- what the DSS passes walk
+  bool packed = false;
+  int sgx = 0, sgy = 0, sgz = 0, sn = 0;
   // recompute mode: nodal coordinates [cell][3][n3], and an L2-sized scratch for the metric of one
   // chunk of cells (per arithmetic: 0 double-word, 1 FP64, 2 FP32)
   double* xyz64 = nullptr;

@@ -303,6 +303,10 @@ extern "C" fe_status fe_rhs(const fe_mesh* m, int kind, double* b, void* stream)
     fe_set_error("fe_rhs: unknown kind %d", kind);
     return FE_ERR_INVALID;
   }
+  if (m->packed) {
+    fe_set_error("fe_rhs: FE_LAYOUT_CELLS meshes only");
+    return FE_ERR_INVALID;
+  }
   FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
   return dispatch<false>(m, kind, nullptr, b, (cudaStream_t)stream);
 }
@@ -315,6 +319,10 @@ extern "C" fe_status fe_l2_error(const fe_mesh* m, int kind, const double* u, do
   }
   if (kind != FE_RHS_SINE && kind != FE_RHS_QUADRATIC) {
     fe_set_error("fe_l2_error: unknown kind %d", kind);
+    return FE_ERR_INVALID;
+  }
+  if (m->packed) {
+    fe_set_error("fe_l2_error: FE_LAYOUT_CELLS meshes only");
     return FE_ERR_INVALID;
   }
   FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");

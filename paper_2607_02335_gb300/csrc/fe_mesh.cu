@@ -425,6 +425,16 @@ fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void
     fe_set_error("fe_mesh_create: FE_GEOM_AFFINE needs deform_amp == 0");
     return FE_ERR_INVALID;
   }
+  if (d->layout != FE_LAYOUT_CELLS && d->layout != FE_LAYOUT_PACKED2) {
+    fe_set_error("fe_mesh_create: unknown layout %d", d->layout);
+    return FE_ERR_INVALID;
+  }
+  if (d->layout == FE_LAYOUT_PACKED2 &&
+      ((d->mx | d->my | d->mz) & 1 || d->degree > 3 || d->geom_mode == FE_GEOM_RECOMPUTE)) {
+    fe_set_error("fe_mesh_create: FE_LAYOUT_PACKED2 needs even cell counts, degree 1 to 3 and "
+                 "stored or affine geometry");
+    return FE_ERR_INVALID;
+  }
   if (!(std::fabs(d->deform_amp) <= 0.2)) {
     fe_set_error("fe_mesh_create: |deform_amp| must be <= 0.2 (keeps the map invertible)");
     return FE_ERR_INVALID;
@@ -448,6 +458,12 @@ fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void
   m->ncells = ncells;
   m->ncw = ncells * n3;
   m->nu = (long long)(d->mx * m->p + 1) * (d->my * m->p + 1) * (d->mz * m->p + 1);
+  m->packed = d->layout == FE_LAYOUT_PACKED2;
+  m->sgx = m->packed ? d->mx / 2 : d->mx;
+  m->sgy = m->packed ? d->my / 2 : d->my;
+  m->sgz = m->packed ? d->mz / 2 : d->mz;
+  m->sn = m->packed ? 2 * m->p + 1 : m->n;
+  if (m->packed) m->ncw = (long long)m->sgx * m->sgy * m->sgz * m->sn * m->sn * m->sn;
   fe_host_tables(m->p, &m->tab);
   cudaStream_t st = (cudaStream_t)stream;
   {
@@ -480,10 +496,12 @@ fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void
   }
   fe_status s = FE_OK;
   if (d->geom_mode == FE_GEOM_STORED) {
-    s = fe_dalloc((void**)&m->geo64, m->ncw * FE_GEO_COMPS * sizeof(double), st, "geometry");
+    // per cell and quadrature point, whatever the storage layout of the vectors
+    s = fe_dalloc((void**)&m->geo64, m->ncells * n3 * FE_GEO_COMPS * sizeof(double), st,
+                  "geometry");
     g.geo = m->geo64;
   } else if (d->geom_mode == FE_GEOM_RECOMPUTE) {
-    s = fe_dalloc((void**)&m->xyz64, m->ncw * 3 * sizeof(double), st, "coordinates");
+    s = fe_dalloc((void**)&m->xyz64, m->ncells * n3 * 3 * sizeof(double), st, "coordinates");
     g.xyz = m->xyz64;
   }
   if (s == FE_OK && d->geom_mode != FE_GEOM_AFFINE) {
@@ -523,11 +541,11 @@ extern "C" fe_status fe_mesh_layout(const fe_mesh* m, fe_layout* out) {
     fe_set_error("fe_mesh_layout: null argument");
     return FE_ERR_INVALID;
   }
-  out->n_cells = m->ncells;
-  out->nodes_per_cell = m->n3;
+  out->n_cells = (long long)m->sgx * m->sgy * m->sgz;
+  out->nodes_per_cell = (long long)m->sn * m->sn * m->sn;
   out->cellwise_len = m->ncw;
   out->unique_dofs = m->nu;
-  out->layout_id = 0;
+  out->layout_id = m->packed ? FE_LAYOUT_PACKED2 : FE_LAYOUT_CELLS;
   return FE_OK;
 }
 
@@ -552,6 +570,10 @@ extern "C" fe_status fe_gather(const fe_mesh* m, const double* xu_host, double* 
                                void* stream) {
   if (!m || !xu_host || !xc_dev || !fe_aligned(xc_dev)) {
     fe_set_error("fe_gather: null or misaligned argument");
+    return FE_ERR_INVALID;
+  }
+  if (m->packed) {
+    fe_set_error("fe_gather: FE_LAYOUT_CELLS meshes only");
     return FE_ERR_INVALID;
   }
   cudaStream_t st = (cudaStream_t)stream;

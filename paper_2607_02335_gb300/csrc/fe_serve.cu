@@ -306,7 +306,8 @@ extern "C" fe_status fe_serve_submit(fe_server* S, const fe_mesh_desc* desc, con
     return FE_ERR_INVALID;
   }
   if (desc->degree < 1 || desc->degree > 7 || desc->mx < 1 || desc->my < 1 || desc->mz < 1 ||
-      desc->geom_mode == FE_GEOM_RECOMPUTE || desc->device != S->device) {
+      desc->geom_mode == FE_GEOM_RECOMPUTE || desc->layout != FE_LAYOUT_CELLS ||
+      desc->device != S->device) {
     fe_set_error("fe_serve_submit: invalid mesh description");
     return FE_ERR_INVALID;
   }

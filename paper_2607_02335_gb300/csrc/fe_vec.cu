@@ -90,8 +90,9 @@ static unsigned grid_cap(long long n, int threads) {
 
 template <class S>
 static fe_status dss_t(const fe_mesh* m, S* v, int sx, int sy, cudaStream_t st) {
-  const int n = m->n, n2 = n * n;
-  const int mx = m->d.mx, my = m->d.my, mz = m->d.mz;
+  // the storage grid: cells, or 2^3-packed units whose sides carry 2p+1 nodes
+  const int n = m->sn, n2 = n * n;
+  const int mx = m->sgx, my = m->sgy, mz = m->sgz;
   const int stride[3] = {sx, sy, 1};
   const long long work[3] = {(long long)((mx - 1) / sx) * my * mz * n2,
                              (long long)mx * ((my - 1) / sy) * mz * n2,

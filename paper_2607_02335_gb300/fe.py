@@ -22,6 +22,7 @@ FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN, FE_ERR_TIMEOUT, FE_ERR_BUSY = 4, 5, 6, 7
 FE_LAPLACE, FE_MASS = 0, 1
 FE_F64, FE_F32, FE_BF16_F32ACC, FE_F16_F32ACC = 0, 1, 2, 3
 FE_GEOM_STORED, FE_GEOM_RECOMPUTE, FE_GEOM_AFFINE = 0, 1, 2
+FE_LAYOUT_CELLS, FE_LAYOUT_PACKED2 = 0, 1
 FE_ASSEMBLE, FE_NATIVE_F64 = 1, 2
 FE_RHS_SINE, FE_RHS_QUADRATIC = 0, 1
 
@@ -33,7 +34,8 @@ STATUS_NAMES = {0: "FE_OK", 1: "FE_ERR_INVALID", 2: "FE_ERR_OOM", 3: "FE_ERR_CUD
 class fe_mesh_desc(ctypes.Structure):
     _fields_ = [("mx", ctypes.c_int), ("my", ctypes.c_int), ("mz", ctypes.c_int),
                 ("degree", ctypes.c_int), ("deform_amp", ctypes.c_double),
-                ("geom_mode", ctypes.c_int), ("dirichlet", ctypes.c_int), ("device", ctypes.c_int)]
+                ("geom_mode", ctypes.c_int), ("dirichlet", ctypes.c_int), ("device", ctypes.c_int),
+                ("layout", ctypes.c_int)]
 
 
 class fe_layout(ctypes.Structure):
@@ -257,9 +259,10 @@ class Mesh:
     """Owns an ``fe_mesh``; vectors are torch CUDA tensors of ``cellwise_len`` elements."""
 
     def __init__(self, m, degree: int, deform_amp: float = 0.0, geom_mode: int = FE_GEOM_STORED,
-                 dirichlet: bool = False, device: int = 0, stream=None):
+                 dirichlet: bool = False, device: int = 0, stream=None, layout: int = 0):
         mx, my, mz = (m, m, m) if isinstance(m, int) else tuple(m)
-        self.desc = fe_mesh_desc(mx, my, mz, degree, deform_amp, geom_mode, int(dirichlet), device)
+        self.desc = fe_mesh_desc(mx, my, mz, degree, deform_amp, geom_mode, int(dirichlet), device,
+                                 layout)
         self.handle = fe_mesh_create(self.desc, stream)
         lay = fe_mesh_layout(self.handle)
         self.n_cells, self.nodes_per_cell = lay.n_cells, lay.nodes_per_cell
