@@ -395,6 +395,7 @@ def run_ours(args, rank, world):
                                                           reps)
         extras["reduced_precision_apply"] = reduced_precision_apply(fe, torch, flush, stream)
         extras["block_structured_dss"] = multiblock_dss(fe, torch, flush, stream)
+        extras["packed_storage"] = packed_storage(fe, torch, flush, stream)
         extras["solve_mixed_vs_fp64"] = mixed_vs_fp64_solve(fe, torch)
         extras["batched"] = batched_solve(fe, torch, count=args.batch_count)
         extras["serving"] = {
@@ -485,6 +486,43 @@ def recompute_geometry(fe, torch, sweep, per_case, flush, stream, reps):
                 "time_vs_stored": round(res["volumetric_ms"] / st["volumetric_ms"], 3)})
         del x, y
         gm.close()
+    return out
+
+
+def packed_storage(fe, torch, flush, stream, reps=20):
+    """2^3-packed storage units against one cell per unit, FP64 Laplace and mass at Q2 48^3 and
+    Q3 96^3 (deformed): volumetric and assembled time, stored values and bytes per unique DoF."""
+    from paper_2607_02335_gb300 import synth as S
+
+    def med(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    out = []
+    for p, m in ((2, 48), (3, 96)):
+        for layout, name in ((fe.FE_LAYOUT_CELLS, "cells"), (fe.FE_LAYOUT_PACKED2, "packed2")):
+            gm = fe.Mesh(m, p, deform_amp=AMP, layout=layout)
+            x = torch.randn(gm.cellwise_len, dtype=torch.float64, device="cuda")
+            y = gm.empty()
+            for op in (fe.FE_LAPLACE, fe.FE_MASS):
+                tv = med(lambda: fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, 0, stream))
+                ta = med(lambda: fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, fe.FE_ASSEMBLE, stream))
+                out.append({"case": f"Q{p} {m}^3", "layout": name,
+                            "op": "laplace" if op == fe.FE_LAPLACE else "mass",
+                            "stored_per_unique": round(gm.cellwise_len / gm.unique_dofs, 3),
+                            "volumetric_ms": round(tv, 4), "assembled_ms": round(ta, 4),
+                            "gdofs_unique_assembled": round(gm.unique_dofs / ta / 1e6, 3)})
+            del x, y
+            gm.close()
     return out
 
 

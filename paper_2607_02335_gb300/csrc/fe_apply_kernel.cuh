@@ -662,31 +662,35 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   __syncthreads();
   if constexpr (MODE == MODE_BRICK) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
   if constexpr (MODE == MODE_PACKED) {
-    // unit output: every stored node sums the copies of the sub-cells that contain it (fixed
-    // order), the unit-internal part of the assembly
-    constexpr int P = Packed<N>::P, NU = Packed<N>::NU, NU3 = Packed<N>::NU3, UT = 8 * N2;
-    const int us = cl / 8, ut = t - us * UT;
-    const long long unit = cell0 + us;
-    if (us < Packed<N>::UPB && unit < a.ncells / 8) {
-      const int ux_n = a.mx / 2, uy_n = a.my / 2;
-      const int gx0 = (int)(unit % ux_n) * 2 * P, gy0 = (int)((unit / ux_n) % uy_n) * 2 * P,
-                gz0 = (int)(unit / ((long long)ux_n * uy_n)) * 2 * P;
-      for (int e = ut; e < NU3; e += UT) {
-        const int i = e % NU, j = (e / NU) % NU, k = e / (NU * NU);
-        V acc = T::zero();
-        for (int sz = (k > P ? 1 : 0); sz <= (k < P ? 0 : 1); ++sz)
-          for (int sy = (j > P ? 1 : 0); sy <= (j < P ? 0 : 1); ++sy)
-            for (int sx = (i > P ? 1 : 0); sx <= (i < P ? 0 : 1); ++sx) {
-              const int slot = us * 8 + sz * 4 + sy * 2 + sx;
-              acc = T::add(acc, s0.get(slot * C::CS + zl<N>(i - sx * P, j - sy * P, k - sz * P)));
-            }
-        if (a.dirichlet) {
-          const int gx = gx0 + i, gy = gy0 + j, gz = gz0 + k;
-          if (gx == 0 || gx == a.mx * P || gy == 0 || gy == a.my * P || gz == 0 || gz == a.mz * P)
-            acc = T::zero();
-        }
-        if constexpr (T::LOWP) acc.v *= a.oscale;
-        T::store(a.y + unit * NU3 + e, acc);
+    // unit-internal assembly: sum the copies on the x-, y- and z-interfaces between the unit's
+    // sub-cells in the tile (as the structured DSS passes do, z then y then x), then every stored
+    // node is written once, by the sub-cell with the lowest index along each axis that holds it
+    constexpr int P = Packed<N>::P, NU = Packed<N>::NU;
+    const int sub = cl % 8, sx = sub & 1, sy = (sub >> 1) & 1, sz = (sub >> 2) & 1;
+    auto pair_sum = [&](int eL, int eR) {
+      const V v = T::add(s0.get(eL), s0.get(eR));
+      s0.put(eL, v);
+      s0.put(eR, v);
+    };
+    if (active && sz == 0)  // z-interface: (k = P of sz 0) + (k = 0 of sz 1), thread (i, j)
+      pair_sum(cb + zl<N>(la, lb, P), cb + 4 * C::CS + zl<N>(la, lb, 0));
+    __syncthreads();
+    if (active && sy == 0)  // y-interface, thread (i, k) = (la, lb)
+      pair_sum(cb + zl<N>(la, P, lb), cb + 2 * C::CS + zl<N>(la, 0, lb));
+    __syncthreads();
+    if (active && sx == 0)  // x-interface, thread (j, k) = (la, lb)
+      pair_sum(cb + zl<N>(P, la, lb), cb + 1 * C::CS + zl<N>(0, la, lb));
+    __syncthreads();
+    if (active && (sx == 0 || la > 0) && (sy == 0 || lb > 0)) {
+      typename NT<V>::SV* yu = a.y + (cell0 + cl / 8) * Packed<N>::NU3 +
+                               (long long)(sy * P + lb) * NU + sx * P + la;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        if (sz == 1 && k == 0) continue;
+        V v = s0.get(cb + zl<N>(la, lb, k));
+        if (masked(k)) v = T::zero();
+        if constexpr (T::LOWP) v.v *= a.oscale;
+        T::store(yu + (long long)(sz * P + k) * NU * NU, v);
       }
     }
     return;
