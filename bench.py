@@ -46,11 +46,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="tiny sizes (plumbing check only)")
     ap.add_argument("--batch-count", type=int, default=256, help="problems of the batched solve")
-    ap.add_argument("--serve-requests", type=int, default=300, help="requests per serving run")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests per serving run")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate (1/s)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-slots", type=int, default=256)
-    ap.add_argument("--serve-cap-s", type=float, default=45.0, help="wall-time cap per serving run")
+    ap.add_argument("--serve-cap-s", type=float, default=60.0, help="wall-time cap per serving run")
     ap.add_argument("--no-extras", action="store_true", help="operator sweep only")
     ap.add_argument("--profile-case", default=None,
                     help="p,m,op: only run K+W applies of one case (for profiler captures)")
