@@ -511,3 +511,140 @@ class Packed:
 
 def or_n_unique(mesh: Mesh) -> int:
     return int(_L().or_n_unique(mesh.ref))
+
+
+class Adaptive:
+    """Two-level Cartesian refinement of the unit cube (Appendix "Extension of DSS algorithms onto
+    Non-Conforming Interfaces"): a coarse grid of mc^3 cells, the cells of the box
+    [lo, hi) (coarse cell coordinates, strictly inside the domain) each refined into 2x2x2 fine
+    cells.  Storage: the full coarse grid (the cells inside the box are dormant and stay zero),
+    then the fine grid of the box, both in layout 0.  The conforming space constrains every fine
+    node on the box boundary to the trace of the coarse polynomial of its parent cell, so the
+    gather G_c maps global DoFs (nodes of the active coarse cells, fine nodes off the box boundary)
+    to copies, with interpolation weights P(i, J) = prod_d l_J_d(xi_d(i)) on the constrained fine
+    copies.  DSS is S = G_c G_c^T on the active copies, zero on the dormant ones."""
+
+    def __init__(self, mc: int, lo, hi, p: int):
+        self.mc, self.lo, self.hi, self.p = mc, tuple(lo), tuple(hi), p
+        n = self.n = p + 1
+        assert all(1 <= lo[d] < hi[d] <= mc - 1 for d in range(3)), "box strictly inside"
+        self.fd = tuple(2 * (hi[d] - lo[d]) for d in range(3))  # fine cells per direction
+        nc_coarse = mc ** 3
+        nc_fine = self.fd[0] * self.fd[1] * self.fd[2]
+        n3 = n ** 3
+        self.length = (nc_coarse + nc_fine) * n3
+        t = (1.0 + gll(p)) / 2.0
+        self.t = t
+        rows, cols, vals = [], [], []
+        key_id = {}
+
+        def node_key(x):  # coinciding nodes agree to rounding; distinct ones differ by >= 1e-4
+            return tuple(int(round(v * 2 ** 30)) for v in x)
+
+        def dof(x):
+            k = node_key(x)
+            if k not in key_id:
+                key_id[k] = len(key_id)
+            return key_id[k]
+
+        self.active = np.zeros(nc_coarse + nc_fine, dtype=bool)
+        # coarse active cells
+        for cz in range(mc):
+            for cy in range(mc):
+                for cx in range(mc):
+                    c = (cz * mc + cy) * mc + cx
+                    if all(lo[d] <= (cx, cy, cz)[d] < hi[d] for d in range(3)):
+                        continue
+                    self.active[c] = True
+                    for a in range(n3):
+                        i, j, k = a % n, (a // n) % n, a // (n * n)
+                        x = ((cx + t[i]) / mc, (cy + t[j]) / mc, (cz + t[k]) / mc)
+                        rows.append(c * n3 + a)
+                        cols.append(dof(x))
+                        vals.append(1.0)
+        # fine cells: free nodes, or constrained to the parent's coarse nodes on the box boundary
+        H = 2 * mc
+        fine_cols, fine_rows, fine_vals = [], [], []
+        for fz in range(self.fd[2]):
+            for fy in range(self.fd[1]):
+                for fx in range(self.fd[0]):
+                    c = nc_coarse + (fz * self.fd[1] + fy) * self.fd[0] + fx
+                    self.active[c] = True
+                    g = (2 * lo[0] + fx, 2 * lo[1] + fy, 2 * lo[2] + fz)  # fine cell, global
+                    par = tuple(gg // 2 for gg in g)
+                    half = tuple(gg % 2 for gg in g)
+                    for a in range(n3):
+                        ijk = (a % n, (a // n) % n, a // (n * n))
+                        x = tuple((g[d] + t[ijk[d]]) / H for d in range(3))
+                        fidx = [g[d] * p + ijk[d] for d in range(3)]  # fine node lattice index
+                        on_bnd = any(fidx[d] in (2 * lo[d] * p, 2 * hi[d] * p) for d in range(3))
+                        if not on_bnd:
+                            fine_rows.append(c * n3 + a)
+                            fine_cols.append(x)
+                            fine_vals.append(None)
+                            continue
+                        xi = [(half[d] + t[ijk[d]]) / 2.0 for d in range(3)]  # in the parent
+                        for b in range(n3):
+                            J = (b % n, (b // n) % n, b // (n * n))
+                            w = 1.0
+                            for d in range(3):
+                                w *= lagrange(t, J[d], xi[d])
+                            if w == 0.0:
+                                continue
+                            xJ = tuple((par[d] + t[J[d]]) / mc for d in range(3))
+                            fine_rows.append(c * n3 + a)
+                            fine_cols.append(xJ)
+                            fine_vals.append(w)
+        ncoarse_dofs = len(key_id)
+        for r, x, w in zip(fine_rows, fine_cols, fine_vals):
+            if w is None:
+                rows.append(r)
+                cols.append(dof(x))
+                vals.append(1.0)
+            else:
+                k = node_key(x)
+                assert k in key_id and key_id[k] < ncoarse_dofs, "constraint to a non-coarse node"
+                rows.append(r)
+                cols.append(key_id[k])
+                vals.append(w)
+        self.n_unique = len(key_id)
+        import scipy.sparse as sp
+        self.G = sp.csr_matrix((vals, (rows, cols)), shape=(self.length, self.n_unique))
+        self.active_entries = np.repeat(self.active, n3)
+
+    def gather(self, xg):
+        return self.G @ np.asarray(xg, dtype=np.float64)
+
+    def scatter(self, yc):
+        return self.G.T @ np.asarray(yc, dtype=np.float64)
+
+    def dss(self, yc):
+        return self.G @ (self.G.T @ np.asarray(yc, dtype=np.float64))
+
+    def cell_corners(self, c):
+        """(8, 3) corner coordinates of storage cell c (coarse or fine)."""
+        mc, n = self.mc, self.n
+        if c < mc ** 3:
+            g, h = ((c % mc), (c // mc) % mc, c // (mc * mc)), 1.0 / mc
+        else:
+            f = c - mc ** 3
+            fx, fy = f % self.fd[0], (f // self.fd[0]) % self.fd[1]
+            fz = f // (self.fd[0] * self.fd[1])
+            g = (2 * self.lo[0] + fx, 2 * self.lo[1] + fy, 2 * self.lo[2] + fz)
+            h = 1.0 / (2 * mc)
+        return np.array([[(g[0] + (k & 1)) * h, (g[1] + ((k >> 1) & 1)) * h,
+                          (g[2] + ((k >> 2) & 1)) * h] for k in range(8)])
+
+    def apply_local(self, op: int, xc):
+        """Per active cell A_K x_K (element matrices of the oracle's trilinear cells)."""
+        n3 = self.n ** 3
+        ncell = len(self.active)
+        vx = np.concatenate([self.cell_corners(c) for c in range(ncell)])
+        mb = MBMesh(vx, np.arange(8 * ncell).reshape(ncell, 8), np.ones((ncell, 3)), self.p,
+                    tol=-1.0)
+        yc = np.zeros(self.length)
+        xc = np.asarray(xc, dtype=np.float64)
+        for c in np.nonzero(self.active)[0]:
+            A = mb.element_matrix(op, int(c))
+            yc[c * n3:(c + 1) * n3] = A @ xc[c * n3:(c + 1) * n3]
+        return yc
