@@ -282,6 +282,33 @@ fe_status fe_mb_apply(const fe_mbmesh* mesh, fe_op op, fe_prec prec, const void*
  * "Dimensionally-Split Structured Summation"), then the inter-block summation.  r == z allowed. */
 fe_status fe_mb_dss(const fe_mbmesh* mesh, fe_prec prec, const void* r, void* z, void* stream);
 
+/* Hanging nodes (Appendix "Extension of DSS algorithms onto Non-Conforming Interfaces",
+ * Algorithm "Full DSS Operator with Hanging Node Resolution") on a two-level Cartesian
+ * refinement of the unit cube: a coarse grid of mc^3 cells whose cells inside the box
+ * [lo, hi) (coarse cell coordinates, strictly inside: 1 <= lo < hi <= mc-1) are each refined
+ * into 2x2x2 fine cells.  The conforming space constrains every fine node on the box boundary to
+ * the trace of its parent's coarse polynomial.  Vectors (cellwise_len entries, layout 0 per
+ * level): the full coarse grid -- its cells inside the box are dormant, zero on output, and act
+ * as the shadow cells of the exchange -- then the fine grid of the box (2(hi-lo) cells per
+ * direction).  unique_dofs counts the conforming space.  Stored trilinear geometry, no Dirichlet
+ * masking.  fe_amr_dss: shadow restriction, structured DSS on both levels, prolongation (an
+ * assignment, which makes the paper's vertex save-and-restore unnecessary), result G_c G_c^T r on
+ * the active copies.  fe_amr_apply: the local operator of every active cell, with FE_ASSEMBLE
+ * followed by fe_amr_dss.  FE_F64 / FE_F32; FE_NATIVE_F64 accepted. */
+typedef struct {
+  int mc;         /* coarse cells per direction, >= 3 */
+  int lo[3], hi[3];
+  int degree;     /* p in [1, 7] */
+  int device;
+} fe_amr_desc;
+typedef struct fe_amr fe_amr;
+fe_status fe_amr_create(const fe_amr_desc* desc, void* stream, fe_amr** out);
+fe_status fe_amr_destroy(fe_amr* mesh);
+fe_status fe_amr_layout(const fe_amr* mesh, fe_layout* out);
+fe_status fe_amr_apply(const fe_amr* mesh, fe_op op, fe_prec prec, const void* x, void* y,
+                       unsigned flags, void* stream);
+fe_status fe_amr_dss(const fe_amr* mesh, fe_prec prec, const void* r, void* z, void* stream);
+
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char* fe_last_error(void);
 

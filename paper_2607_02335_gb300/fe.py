@@ -61,6 +61,11 @@ class fe_mb_desc(ctypes.Structure):
                 ("vxyz", ctypes.POINTER(ctypes.c_double)), ("device", ctypes.c_int)]
 
 
+class fe_amr_desc(ctypes.Structure):
+    _fields_ = [("mc", ctypes.c_int), ("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3),
+                ("degree", ctypes.c_int), ("device", ctypes.c_int)]
+
+
 _vp, _i, _u, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double
 _MESH = ctypes.c_void_p
 _SIGS = {
@@ -92,6 +97,11 @@ _SIGS = {
                    ctypes.POINTER(_i)],
     "fe_mb_apply": [_vp, _i, _i, _vp, _vp, _u, _vp],
     "fe_mb_dss": [_vp, _i, _vp, _vp, _vp],
+    "fe_amr_create": [ctypes.POINTER(fe_amr_desc), _vp, ctypes.POINTER(_vp)],
+    "fe_amr_destroy": [_vp],
+    "fe_amr_layout": [_vp, ctypes.POINTER(fe_layout)],
+    "fe_amr_apply": [_vp, _i, _i, _vp, _vp, _u, _vp],
+    "fe_amr_dss": [_vp, _i, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -406,6 +416,69 @@ class MBMesh:
     def close(self):
         if self.handle:
             fe_mb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- hanging nodes on a two-level Cartesian refinement (Appendix) ---------------------------------
+def fe_amr_create(desc: fe_amr_desc, stream=None) -> int:
+    h = _vp()
+    _check(_lib.fe_amr_create(ctypes.byref(desc), _stream(stream), ctypes.byref(h)), "fe_amr_create")
+    return h.value
+
+
+def fe_amr_destroy(mesh: int) -> None:
+    _check(_lib.fe_amr_destroy(mesh), "fe_amr_destroy")
+
+
+def fe_amr_layout(mesh: int) -> fe_layout:
+    out = fe_layout()
+    _check(_lib.fe_amr_layout(mesh, ctypes.byref(out)), "fe_amr_layout")
+    return out
+
+
+def fe_amr_apply(mesh: int, op: int, prec: int, x, y, flags: int = 0, stream=None) -> None:
+    _check(_lib.fe_amr_apply(mesh, op, prec, _ptr(x), _ptr(y), flags, _stream(stream)),
+           "fe_amr_apply")
+
+
+def fe_amr_dss(mesh: int, prec: int, r, z, stream=None) -> None:
+    _check(_lib.fe_amr_dss(mesh, prec, _ptr(r), _ptr(z), _stream(stream)), "fe_amr_dss")
+
+
+class AMRMesh:
+    """Two-level Cartesian refinement: coarse grid mc^3, cells of the box [lo, hi) refined."""
+
+    def __init__(self, mc: int, lo, hi, degree: int, device: int = 0, stream=None):
+        desc = fe_amr_desc(mc, (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi), degree, device)
+        self.handle = fe_amr_create(desc, stream)
+        lay = fe_amr_layout(self.handle)
+        self.cellwise_len, self.unique_dofs = lay.cellwise_len, lay.unique_dofs
+        self.device = device
+
+    def empty(self, prec=FE_F64):
+        import torch
+        dt = torch.float64 if prec == FE_F64 else torch.float32
+        return torch.empty(self.cellwise_len, dtype=dt, device=f"cuda:{self.device}")
+
+    def apply(self, x, op=FE_LAPLACE, prec=FE_F64, flags=0, y=None, stream=None):
+        y = self.empty(prec) if y is None else y
+        fe_amr_apply(self.handle, op, prec, x, y, flags, stream)
+        return y
+
+    def dss(self, r, prec=FE_F64, z=None, stream=None):
+        z = self.empty(prec) if z is None else z
+        fe_amr_dss(self.handle, prec, r, z, stream)
+        return z
+
+    def close(self):
+        if self.handle:
+            fe_amr_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
