@@ -396,6 +396,7 @@ def run_ours(args, rank, world):
         extras["reduced_precision_apply"] = reduced_precision_apply(fe, torch, flush, stream)
         extras["block_structured_dss"] = multiblock_dss(fe, torch, flush, stream)
         extras["packed_storage"] = packed_storage(fe, torch, flush, stream)
+        extras["hanging_node_dss"] = hanging_node_dss(fe, torch, flush, stream)
         extras["solve_mixed_vs_fp64"] = mixed_vs_fp64_solve(fe, torch)
         extras["batched"] = batched_solve(fe, torch, count=args.batch_count)
         extras["serving"] = {
@@ -486,6 +487,35 @@ def recompute_geometry(fe, torch, sweep, per_case, flush, stream, reps):
                 "time_vs_stored": round(res["volumetric_ms"] / st["volumetric_ms"], 3)})
         del x, y
         gm.close()
+    return out
+
+
+def hanging_node_dss(fe, torch, flush, stream, reps=20):
+    """DSS with hanging nodes (shadow cells) on a 48^3 coarse grid whose central 24^3 cells are
+    refined (48^3 fine cells), p = 1..5, per unique DoF of the conforming space, next to the
+    structured DSS of the same number of cells (Appendix, Table "tab:dss_adaptive")."""
+    out = {"workload": "coarse 48^3, box [12,36)^3 refined 2x2x2 (48^3 fine cells), FP64"}
+    rows = []
+    for p in (1, 2, 3, 4, 5):
+        am = fe.AMRMesh(48, (12, 12, 12), (36, 36, 36), p)
+        r = torch.randn(am.cellwise_len, dtype=torch.float64, device="cuda")
+        z = am.empty()
+        fe.fe_amr_dss(am.handle, fe.FE_F64, r, z, stream)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fe.fe_amr_dss(am.handle, fe.FE_F64, r, z, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        rows.append({"degree": p, "unique_dofs": am.unique_dofs, "stored": am.cellwise_len,
+                     "dss_ms": round(ms, 4), "gdofs_unique": round(am.unique_dofs / ms / 1e6, 3)})
+        del r, z
+        am.close()
+    out["rows"] = rows
     return out
 
 

@@ -9,7 +9,8 @@
 //   1. clear the coarse cells of the box;
 //   2. restrict-add: every coarse node J of a shadow cell receives sum_i P(i, J) r_i over the
 //      copies i of its fine children that lie on the box boundary, P(i, J) = prod_d l_J_d(xi_d(i))
-//      the parent's basis function J at the child node (P^T of the prolongation);
+//      the parent's basis function J at the child node (P^T of the prolongation), one box-face
+//      orientation at a time (2D tangent weights);
 //   3. zero the fine copies on the box boundary (they are now represented by the shadows);
 //   4. the structured DSS of the coarse grid and of the fine grid (Algorithm
 //      "Dimensionally-Split Structured Summation"), shadows taking part as ordinary cells;
@@ -32,11 +33,6 @@ struct AmrGeo {
   long long fine_off;    // first storage entry of the fine grid
   double P[2][FE_MAXN][FE_MAXN];  // P[h][i][j] = l_j((h + t_i) / 2): coarse basis at child nodes
 };
-
-__device__ __forceinline__ bool in_box(const AmrGeo& g, int cx, int cy, int cz) {
-  return cx >= g.lo[0] && cx < g.hi[0] && cy >= g.lo[1] && cy < g.hi[1] && cz >= g.lo[2] &&
-         cz < g.hi[2];
-}
 
 // zero the coarse cells of the box (dormant and shadow)
 template <class S>
@@ -62,43 +58,114 @@ __device__ __forceinline__ bool fine_on_bnd(const AmrGeo& g, int fx, int fy, int
          Z == g.fd[2] * g.p;
 }
 
-// step 2: one thread per (coarse cell of the box, node J); cells off the box boundary skip
+// Steps 2 and 5 run per face orientation o = 2*axis + side of the box, in a fixed order; a fine
+// node on the box boundary belongs to the first orientation whose face contains it, so every fine
+// copy is restricted and prolongated exactly once, and a shadow node on a box edge collects the
+// contributions of its faces in separate launches.  On a box face the parent's trace weights
+// factor into the two tangent directions (the normal factor is 1 on the face).
+__device__ __forceinline__ bool owned_by(const AmrGeo& g, int o, const int X[3]) {
+  for (int o2 = 0; o2 < o; ++o2) {
+    const int a2 = o2 >> 1;
+    if (X[a2] == ((o2 & 1) ? g.fd[a2] * g.p : 0)) return false;
+  }
+  return true;
+}
+
+// step 2, orientation o: one thread per (shadow cell on that box face, node J of its face)
 template <class S>
-__global__ void k_amr_restrict(S* __restrict__ v, const __grid_constant__ AmrGeo g) {
+__global__ void k_amr_restrict(S* __restrict__ v, const __grid_constant__ AmrGeo g, int o) {
   const int n = g.n, n3 = n * n * n, p = g.p;
-  const int bx = g.hi[0] - g.lo[0], by = g.hi[1] - g.lo[1], bz = g.hi[2] - g.lo[2];
-  const long long total = (long long)bx * by * bz * n3;
+  const int axis = o >> 1, side = o & 1;
+  const int t1 = axis == 0 ? 1 : 0, t2 = axis == 2 ? 1 : 2;
+  int b[3];
+  for (int a = 0; a < 3; ++a) b[a] = g.hi[a] - g.lo[a];
+  const long long total = (long long)b[t1] * b[t2] * n * n;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const long long c = e / n3;
-    const int J = (int)(e - c * n3);
-    const int Jx = J % n, Jy = (J / n) % n, Jz = J / (n * n);
-    const int ox = (int)(c % bx), oy = (int)((c / bx) % by), oz = (int)(c / ((long long)bx * by));
-    // the parent's node J lies on the box boundary (otherwise no constrained child touches it)
-    const int CX = ox * p + Jx, CY = oy * p + Jy, CZ = oz * p + Jz;
-    if (!(CX == 0 || CX == bx * p || CY == 0 || CY == by * p || CZ == 0 || CZ == bz * p)) continue;
+    const int Ja = (int)(e % n), Jb = (int)((e / n) % n);
+    const long long sc = e / (n * n);
+    int oc[3];  // shadow cell, box-local
+    oc[axis] = side ? b[axis] - 1 : 0;
+    oc[t1] = (int)(sc % b[t1]);
+    oc[t2] = (int)(sc / b[t1]);
     S acc = S(0);
-    for (int h = 0; h < 8; ++h) {
-      const int hx = h & 1, hy = (h >> 1) & 1, hz = (h >> 2) & 1;
-      const int fx = 2 * ox + hx, fy = 2 * oy + hy, fz = 2 * oz + hz;
-      const long long fbase =
-          g.fine_off + (((long long)fz * g.fd[1] + fy) * g.fd[0] + fx) * n3;
-      for (int a = 0; a < n3; ++a) {
-        const int i = a % n, j = (a / n) % n, k = a / (n * n);
-        if (!fine_on_bnd(g, fx, fy, fz, i, j, k)) continue;
-        const double w = g.P[hx][i][Jx] * g.P[hy][j][Jy] * g.P[hz][k][Jz];
-        if (w != 0.0) acc += S(w) * v[fbase + a];
+    for (int hb = 0; hb < 2; ++hb)
+      for (int ha = 0; ha < 2; ++ha) {
+        int fc[3];
+        fc[axis] = 2 * oc[axis] + side;
+        fc[t1] = 2 * oc[t1] + ha;
+        fc[t2] = 2 * oc[t2] + hb;
+        const long long fbase =
+            g.fine_off + (((long long)fc[2] * g.fd[1] + fc[1]) * g.fd[0] + fc[0]) * n3;
+        for (int ib = 0; ib < n; ++ib)
+          for (int ia = 0; ia < n; ++ia) {
+            int l[3], X[3];
+            l[axis] = side ? p : 0;
+            l[t1] = ia;
+            l[t2] = ib;
+            for (int a = 0; a < 3; ++a) X[a] = fc[a] * p + l[a];
+            if (!owned_by(g, o, X)) continue;
+            const double w = g.P[ha][ia][Ja] * g.P[hb][ib][Jb];
+            if (w != 0.0) acc += S(w) * v[fbase + ((long long)l[2] * n + l[1]) * n + l[0]];
+          }
       }
-    }
-    const int cx = g.lo[0] + ox, cy = g.lo[1] + oy, cz = g.lo[2] + oz;
-    v[(((long long)cz * g.mc + cy) * g.mc + cx) * n3 + J] = acc;
+    int J[3];
+    J[axis] = side ? p : 0;
+    J[t1] = Ja;
+    J[t2] = Jb;
+    const long long cidx = (((long long)(g.lo[2] + oc[2]) * g.mc + g.lo[1] + oc[1]) * g.mc +
+                            g.lo[0] + oc[0]) * n3 + ((long long)J[2] * n + J[1]) * n + J[0];
+    v[cidx] += acc;
   }
 }
 
-// step 3 (assign = false): zero the fine copies on the box boundary; step 5 (assign = true): set
-// them to the parent's interpolated value
-template <class S, bool ASSIGN>
-__global__ void k_amr_fine_bnd(S* __restrict__ v, const __grid_constant__ AmrGeo g) {
+// step 5, orientation o: one thread per (shadow cell on that box face, child on it, node)
+template <class S>
+__global__ void k_amr_prolong(S* __restrict__ v, const __grid_constant__ AmrGeo g, int o) {
+  const int n = g.n, n3 = n * n * n, p = g.p;
+  const int axis = o >> 1, side = o & 1;
+  const int t1 = axis == 0 ? 1 : 0, t2 = axis == 2 ? 1 : 2;
+  int b[3];
+  for (int a = 0; a < 3; ++a) b[a] = g.hi[a] - g.lo[a];
+  const long long total = (long long)b[t1] * b[t2] * 4 * n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int ia = (int)(e % n), ib = (int)((e / n) % n);
+    const int h = (int)((e / (n * n)) % 4), ha = h & 1, hb = h >> 1;
+    const long long sc = e / (4 * n * n);
+    int oc[3], fc[3], l[3], X[3];
+    oc[axis] = side ? b[axis] - 1 : 0;
+    oc[t1] = (int)(sc % b[t1]);
+    oc[t2] = (int)(sc / b[t1]);
+    fc[axis] = 2 * oc[axis] + side;
+    fc[t1] = 2 * oc[t1] + ha;
+    fc[t2] = 2 * oc[t2] + hb;
+    l[axis] = side ? p : 0;
+    l[t1] = ia;
+    l[t2] = ib;
+    for (int a = 0; a < 3; ++a) X[a] = fc[a] * p + l[a];
+    if (!owned_by(g, o, X)) continue;
+    const long long sbase = (((long long)(g.lo[2] + oc[2]) * g.mc + g.lo[1] + oc[1]) * g.mc +
+                             g.lo[0] + oc[0]) * n3;
+    S val = S(0);
+    for (int Jb = 0; Jb < n; ++Jb)
+      for (int Ja = 0; Ja < n; ++Ja) {
+        const double w = g.P[ha][ia][Ja] * g.P[hb][ib][Jb];
+        if (w == 0.0) continue;
+        int J[3];
+        J[axis] = side ? p : 0;
+        J[t1] = Ja;
+        J[t2] = Jb;
+        val += S(w) * v[sbase + ((long long)J[2] * n + J[1]) * n + J[0]];
+      }
+    v[g.fine_off + (((long long)fc[2] * g.fd[1] + fc[1]) * g.fd[0] + fc[0]) * n3 +
+      ((long long)l[2] * n + l[1]) * n + l[0]] = val;
+  }
+}
+
+// step 3: zero the fine copies on the box boundary
+template <class S>
+__global__ void k_amr_fine_bnd_zero(S* __restrict__ v, const __grid_constant__ AmrGeo g) {
   const int n = g.n, n3 = n * n * n;
   const long long total = (long long)g.fd[0] * g.fd[1] * g.fd[2] * n3;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -107,20 +174,7 @@ __global__ void k_amr_fine_bnd(S* __restrict__ v, const __grid_constant__ AmrGeo
     const int a = (int)(e - f * n3);
     const int fx = (int)(f % g.fd[0]), fy = (int)((f / g.fd[0]) % g.fd[1]),
               fz = (int)(f / ((long long)g.fd[0] * g.fd[1]));
-    const int i = a % n, j = (a / n) % n, k = a / (n * n);
-    if (!fine_on_bnd(g, fx, fy, fz, i, j, k)) continue;
-    S val = S(0);
-    if (ASSIGN) {
-      const int hx = fx & 1, hy = fy & 1, hz = fz & 1;
-      const int cx = g.lo[0] + fx / 2, cy = g.lo[1] + fy / 2, cz = g.lo[2] + fz / 2;
-      const long long sbase = (((long long)cz * g.mc + cy) * g.mc + cx) * n3;
-      for (int J = 0; J < n3; ++J) {
-        const int Jx = J % n, Jy = (J / n) % n, Jz = J / (n * n);
-        const double w = g.P[hx][i][Jx] * g.P[hy][j][Jy] * g.P[hz][k][Jz];
-        if (w != 0.0) val += S(w) * v[sbase + J];
-      }
-    }
-    v[g.fine_off + e] = val;
+    if (fine_on_bnd(g, fx, fy, fz, a % n, (a / n) % n, a / (n * n))) v[g.fine_off + e] = S(0);
   }
 }
 
@@ -252,12 +306,21 @@ static fe_status amr_dss(const fe_amr* A, S* v, cudaStream_t st) {
                          (A->g.hi[2] - A->g.lo[2]) * A->coarse->n3;
   const long long nfine = A->fine->ncells * A->fine->n3;
   const int prec = sizeof(S) == 8 ? FE_F64 : FE_F32;
+  const int n2 = A->g.n * A->g.n;
+  int b[3];
+  for (int a = 0; a < 3; ++a) b[a] = A->g.hi[a] - A->g.lo[a];
+  auto face_items = [&](int o) {
+    const int axis = o >> 1, t1 = axis == 0 ? 1 : 0, t2 = axis == 2 ? 1 : 2;
+    return (long long)b[t1] * b[t2] * n2;
+  };
   k_amr_clear<S><<<grid_cap(nbox, 256), 256, 0, st>>>(v, A->g);
-  k_amr_restrict<S><<<grid_cap(nbox, 128), 128, 0, st>>>(v, A->g);
-  k_amr_fine_bnd<S, false><<<grid_cap(nfine, 256), 256, 0, st>>>(v, A->g);
+  for (int o = 0; o < 6; ++o)
+    k_amr_restrict<S><<<grid_cap(face_items(o), 128), 128, 0, st>>>(v, A->g, o);
+  k_amr_fine_bnd_zero<S><<<grid_cap(nfine, 256), 256, 0, st>>>(v, A->g);
   FE_TRY(fe_launch_dss(A->coarse, prec, v, st));
   FE_TRY(fe_launch_dss(A->fine, prec, v + A->g.fine_off, st));
-  k_amr_fine_bnd<S, true><<<grid_cap(nfine, 128), 128, 0, st>>>(v, A->g);
+  for (int o = 0; o < 6; ++o)
+    k_amr_prolong<S><<<grid_cap(4 * face_items(o), 128), 128, 0, st>>>(v, A->g, o);
   k_amr_clear<S><<<grid_cap(nbox, 256), 256, 0, st>>>(v, A->g);
   return fe_cuda_check(cudaGetLastError(), "hanging-node DSS launch");
 }
