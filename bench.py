@@ -397,6 +397,7 @@ def run_ours(args, rank, world):
         extras["block_structured_dss"] = multiblock_dss(fe, torch, flush, stream)
         extras["packed_storage"] = packed_storage(fe, torch, flush, stream)
         extras["hanging_node_dss"] = hanging_node_dss(fe, torch, flush, stream)
+        extras["slab_decomposition"] = slab_decomposition(fe, torch, flush, stream)
         extras["solve_mixed_vs_fp64"] = mixed_vs_fp64_solve(fe, torch)
         extras["batched"] = batched_solve(fe, torch, count=args.batch_count)
         extras["serving"] = {
@@ -516,6 +517,94 @@ def hanging_node_dss(fe, torch, flush, stream, reps=20):
         del r, z
         am.close()
     out["rows"] = rows
+    return out
+
+
+def slab_decomposition(fe, torch, flush, stream, reps=20):
+    """Slab decomposition measured on one GPU.  (1) The Q3 mesh 48 x 48 x 96 (deformed) against its
+    upper slab of 48^3 cells: assembled apply inside the slab, and the pack / add kernels of its
+    interface plane (the device work a slab adds per exchanged DSS; the transfer itself is the
+    caller's).  (2) PCG on Q3 32^3 (Dirichlet, sine load, rtol 1e-10): the whole mesh against two
+    slabs driven by two threads of this process on the same GPU, exchanging through host barriers
+    and device copies, so the second figure carries that orchestration, not a link."""
+    import threading
+    from paper_2607_02335_gb300 import slab as SL
+
+    def med(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    p, m = 3, (48, 48, 96)
+    whole = fe.Mesh(m, p, deform_amp=AMP)
+    x = torch.randn(whole.cellwise_len, dtype=torch.float64, device="cuda")
+    y = whole.empty()
+    t_whole = med(lambda: fe.fe_apply(whole.handle, fe.FE_LAPLACE, fe.FE_F64, x, y, fe.FE_ASSEMBLE,
+                                      stream))
+    del x, y
+    whole.close()
+    s = SL.Slab(m, p, 48, 96, deform_amp=AMP)
+    x = torch.randn(s.cellwise_len, dtype=torch.float64, device="cuda")
+    y = s.empty()
+    plane = torch.empty(s.plane_len, dtype=torch.float64, device="cuda")
+    t_slab = med(lambda: fe.fe_apply(s.handle, fe.FE_LAPLACE, fe.FE_F64, x, y, fe.FE_ASSEMBLE, stream))
+    t_pack = med(lambda: fe.fe_slab_face_pack(s.handle, fe.FE_F64, y, 0, plane, stream))
+    t_add = med(lambda: fe.fe_slab_face_add(s.handle, fe.FE_F64, y, 0, plane, stream))
+    out = {"apply": {"mesh": "Q3 48x48x96, deformed, FP64, Laplace, FE_ASSEMBLE",
+                     "whole_ms": round(t_whole, 4), "slab_48cubed_ms": round(t_slab, 4),
+                     "plane_pack_ms": round(t_pack, 4), "plane_add_ms": round(t_add, 4),
+                     "plane_bytes_per_neighbour": s.plane_len * 8,
+                     "slab_gdofs_unique": round(s.unique_dofs / (t_slab + t_pack + t_add) / 1e6, 3)}}
+    del x, y, plane
+    s.close()
+
+    mc = (32, 32, 32)
+    whole = fe.Mesh(mc, p, deform_amp=AMP, dirichlet=True)
+    b = whole.rhs()
+    xw = torch.zeros(whole.cellwise_len, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rw = whole.cg_solve(b, xw, rtol=1e-10, maxit=5000)
+    t_w = time.perf_counter() - t0
+    whole.close()
+    slabs = [SL.Slab(mc, p, z0, z1, deform_amp=AMP, dirichlet=True) for z0, z1 in
+             SL.slab_ranges(mc[2], 2)]
+    grp = SL.ThreadSlabGroup(2)
+    comms = [grp.comm(r, slabs[r].plane_len, "cuda:0") for r in range(2)]
+    bs = [sl_.rhs() for sl_ in slabs]
+    xs = [torch.zeros(sl_.cellwise_len, dtype=torch.float64, device="cuda") for sl_ in slabs]
+    res = [None, None]
+
+    def body(r):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            res[r] = slabs[r].cg_solve(bs[r], xs[r], comm=comms[r], rtol=1e-10, maxit=5000)
+        st.synchronize()
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=body, args=(r,)) for r in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    t_s = time.perf_counter() - t0
+    out["pcg"] = {"mesh": "Q3 32^3, deformed, Dirichlet, sine load, rtol 1e-10",
+                  "whole": {"iters": rw.iters, "s": round(t_w, 4),
+                            "ms_per_iter": round(1e3 * t_w / max(rw.iters, 1), 4)},
+                  "two_thread_slabs_one_gpu": {
+                      "iters": res[0].iters, "status": [int(r.status) for r in res],
+                      "s": round(t_s, 4), "ms_per_iter": round(1e3 * t_s / max(res[0].iters, 1), 4)}}
+    for sl_ in slabs:
+        sl_.close()
     return out
 
 

@@ -46,7 +46,8 @@ typedef enum {
   FE_ERR_NOT_CONVERGED = 4, /* CG reached maxit */
   FE_ERR_BREAKDOWN = 5,     /* CG breakdown: <q,p> <= 0 or a non-finite scalar */
   FE_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
-  FE_ERR_BUSY = 7           /* fe_serve_poll: the request is still pending */
+  FE_ERR_BUSY = 7,          /* fe_serve_poll: the request is still pending */
+  FE_ERR_COMM = 8           /* a communication callback of an fe_comm returned non-zero */
 } fe_status;
 
 typedef enum { FE_LAPLACE = 0, FE_MASS = 1 } fe_op;
@@ -308,6 +309,88 @@ fe_status fe_amr_layout(const fe_amr* mesh, fe_layout* out);
 fe_status fe_amr_apply(const fe_amr* mesh, fe_op op, fe_prec prec, const void* x, void* y,
                        unsigned flags, void* stream);
 fe_status fe_amr_dss(const fe_amr* mesh, fe_prec prec, const void* r, void* z, void* stream);
+
+/* ---- Slab decomposition of a structured mesh over several processes or devices ----------------
+ * The cells of a structured mesh (fe_mesh_desc, FE_LAYOUT_CELLS) split into slabs of whole
+ * z-layers; slab s holds the layers z0 <= cz < z1.  Cells are lexicographic with z slowest, so a
+ * slab's cell-wise vectors are the contiguous range of cells [z0 mx my, z1 mx my) of the whole
+ * mesh's vectors.  The volumetric apply is independent per cell; the structured DSS (Sec. 4.1)
+ * needs one exchange per call.  Its passes run in the order z, y, x; a node's copies on the two
+ * sides of a slab interface form one pair of the z-pass, so after the z-pass inside the slab each
+ * slab adds the neighbour's copy of the interface plane to its own, and the y- and x-passes
+ * follow.  The result is bitwise the whole mesh's.  A slab sends and receives mx * my * n^2
+ * values per neighbour and DSS.
+ *
+ * fe_slab_create: an fe_mesh of mx x my x (z1 - z0) cells whose geometry, affine scaling,
+ *   Dirichlet boundary and manufactured data (fe_rhs, fe_l2_error) are those of the whole mesh
+ *   desc->global describes; the interface planes to neighbouring slabs are not Dirichlet
+ *   boundary.  Every fe_* call on a single mesh accepts it and works on the slab alone (fe_dss,
+ *   fe_diag and FE_ASSEMBLE sum inside the slab; fe_layout.unique_dofs counts the slab's nodes,
+ *   interface planes included; fe_pairing of a dual and a primal vector is this slab's part of the
+ *   whole pairing), except fe_cg_solve and fe_cg_solve_batched (use fe_slab_cg_solve).
+ *   FE_ERR_INVALID unless 0 <= z0 < z1 <= global.mz and layout is FE_LAYOUT_CELLS.
+ * Interface planes: side 0 is the slab's bottom (local node k = 0 of layer 0), side 1 its top
+ *   (k = p of the last layer).  A plane holds mx my n^2 values, entry ((cy mx + cx) n + j) n + i
+ *   for node (i, j) of cell (cx, cy); two slabs that share an interface see it in the same order.
+ * fe_slab_face_pack: plane[e] = v[node e of `side`].  fe_slab_face_add: v[node e] += plane[e].
+ *   v and plane are device arrays of double (FE_F64) or float (FE_F32).  Building blocks for
+ *   callers that run their own exchange; fe_slab_dss uses them between its z- and y-passes.
+ * fe_slab_plane_len: mx my n^2. */
+typedef struct {
+  fe_mesh_desc global; /* the whole mesh */
+  int z0, z1;          /* this slab's layers: z0 <= cz < z1 */
+} fe_slab_desc;
+fe_status fe_slab_create(const fe_slab_desc* desc, void* stream, fe_mesh** out);
+fe_status fe_slab_plane_len(const fe_mesh* slab, long long* count);
+fe_status fe_slab_face_pack(const fe_mesh* slab, fe_prec prec, const void* v, int side, void* plane,
+                            void* stream);
+fe_status fe_slab_face_add(const fe_mesh* slab, fe_prec prec, void* v, int side, const void* plane,
+                           void* stream);
+
+/* Communication between the slabs, supplied by the caller (NCCL, MPI, host threads ...).  All
+ * slabs call the same fe_slab_* functions in the same order; each call invokes the callbacks the
+ * same number of times on every slab.  Buffers are caller-owned device memory on the slab's
+ * device: send[s] / recv[s] hold plane_len doubles for the neighbour on side s (NULL where the slab
+ * has no neighbour), red_send 4 doubles and red_all 4 * size doubles.
+ *  exchange(ctx, sides, elem_bytes, count, stream): for every side s in the bitmask `sides`
+ *    (1: below, 2: above) send the first count elements of elem_bytes bytes of send[s] to the
+ *    neighbour there and receive its plane into recv[s].
+ *  allgather(ctx, n, stream): every slab's red_send[0..n) into red_all[r * n + i], r the slab's
+ *    rank (slab r - 1 lies below slab r).
+ * The library enqueues the work that fills the send buffers on `stream` before a call; the callback
+ * must order its transfers after that work (issue them on `stream`, or synchronize it) and leave
+ * the received data ready for work enqueued on `stream` after it returns.  A non-zero return
+ * makes the calling fe_slab_* function return FE_ERR_COMM. */
+typedef struct {
+  int rank, size;      /* this slab's rank and the number of slabs (rank 0 holds z0 = 0) */
+  void* send[2];
+  void* recv[2];
+  double* red_send;
+  double* red_all;
+  int (*exchange)(void* ctx, int sides, int elem_bytes, long long count, void* stream);
+  int (*allgather)(void* ctx, int n, void* stream);
+  void* ctx;
+} fe_comm;
+
+/* fe_slab_dss: z = S r on the whole mesh, restricted to this slab: the z-pass, one exchange of both
+ *   interface planes, the y- and x-passes.  Bitwise fe_dss of the whole mesh.  FE_F64 / FE_F32.
+ * fe_slab_apply: fe_apply on the slab; with FE_ASSEMBLE the DSS passes run as in fe_slab_dss, so y
+ *   is this slab's part of the whole mesh's assembled output, bit for bit.  comm may be NULL
+ *   without FE_ASSEMBLE.
+ * fe_slab_cg_solve: Jacobi PCG on the whole mesh (Sec. 3.2 with P = D^{-1} S, Sec. 3.3), this
+ *   slab's part of b (dual) and x (primal, in/out) in its cell-wise vectors.  The iteration is the
+ *   single-reduction recurrence of Chronopoulos and Gear (1989): per iteration one apply
+ *   s = A z, one DSS with its plane exchange, and one allgather of three scalars (<r,z>, <s,z> and
+ *   sum w^2/mult for the residual) summed over the slabs in rank order, so every slab takes the
+ *   same decisions.  The Jacobi diagonal is assembled across the interfaces once per call.  Same
+ *   stopping rule, result and history semantics as fe_cg_solve; opts->mixed and opts->flexible
+ *   must be 0 (FE_ERR_INVALID).  Synchronous. */
+fe_status fe_slab_dss(const fe_mesh* slab, fe_prec prec, const void* r, void* z, const fe_comm* comm,
+                      void* stream);
+fe_status fe_slab_apply(const fe_mesh* slab, fe_op op, fe_prec prec, const void* x, void* y,
+                        unsigned flags, const fe_comm* comm, void* stream);
+fe_status fe_slab_cg_solve(const fe_mesh* slab, const double* b, double* x, const fe_cg_opts* opts,
+                           const fe_comm* comm, fe_cg_result* res, void* stream);
 
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char* fe_last_error(void);

@@ -18,8 +18,8 @@ static fe_status check_vec(const fe_mesh* m, const void* p, const char* what) {
 // formats keep float vectors)
 static size_t elem_size(int prec) { return prec == FE_F64 ? sizeof(double) : sizeof(float); }
 
-extern "C" fe_status fe_apply(const fe_mesh* m, fe_op op, fe_prec prec, const void* x, void* y,
-                              unsigned flags, void* stream) {
+fe_status fe_apply_impl(const fe_mesh* m, fe_op op, fe_prec prec, const void* x, void* y,
+                        unsigned flags, void* stream, int* brick_out) {
   if (!m) {
     fe_set_error("fe_apply: null mesh");
     return FE_ERR_INVALID;
@@ -52,7 +52,8 @@ extern "C" fe_status fe_apply(const fe_mesh* m, fe_op op, fe_prec prec, const vo
   FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
   const bool native = (flags & FE_NATIVE_F64) && prec == FE_F64;
   FE_TRY(fe_ensure_geometry(m, prec, native));
-  ApplyLaunch L{m, (int)op, x, y, (cudaStream_t)stream, nullptr, (flags & FE_ASSEMBLE) != 0};
+  ApplyLaunch L{m, (int)op, x, y, (cudaStream_t)stream, nullptr, (flags & FE_ASSEMBLE) != 0,
+                brick_out};
   if (prec == FE_F64)
     FE_TRY(native ? fe_launch_apply_f64native(L) : fe_launch_apply_f64dw(L));
   else if (lowp)
@@ -60,6 +61,11 @@ extern "C" fe_status fe_apply(const fe_mesh* m, fe_op op, fe_prec prec, const vo
   else
     FE_TRY(fe_launch_apply_f32(L));
   return FE_OK;
+}
+
+extern "C" fe_status fe_apply(const fe_mesh* m, fe_op op, fe_prec prec, const void* x, void* y,
+                              unsigned flags, void* stream) {
+  return fe_apply_impl(m, op, prec, x, y, flags, stream, nullptr);
 }
 
 extern "C" fe_status fe_dss(const fe_mesh* m, fe_prec prec, const void* r, void* z, void* stream) {

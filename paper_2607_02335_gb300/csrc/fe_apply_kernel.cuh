@@ -174,7 +174,7 @@ struct CellArgs {
   long long cell_base;            // first cell of the launch (k_apply)
   long long geo_cell0;            // cell whose metric is geo[0] (a chunk's scratch in recompute mode)
   int mx, my, mz;
-  int dirichlet;
+  int dirichlet;  // FE_DIR_* mask of the Dirichlet faces (0: none)
   V aff[4];      // affine mode: detJ/h_x^2, detJ/h_y^2, detJ/h_z^2, detJ
   float oscale;  // 16-bit operand types: 1 / (power-of-two scale of the stored metric)
 };
@@ -337,8 +337,8 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
     const int cx = pos.cx, cy = pos.cy, cz = pos.cz;
     bnd_line = (cx == 0 && la == 0) || (cx == a.mx - 1 && la == N - 1) || (cy == 0 && lb == 0) ||
                (cy == a.my - 1 && lb == N - 1);
-    bnd_k0 = (cz == 0);
-    bnd_k1 = (cz == a.mz - 1);
+    bnd_k0 = (a.dirichlet & FE_DIR_ZLO) && cz == 0;
+    bnd_k1 = (a.dirichlet & FE_DIR_ZHI) && cz == a.mz - 1;
   }
   auto masked = [&](int k) { return bnd_line || (k == 0 && bnd_k0) || (k == N - 1 && bnd_k1); };
   auto load_line = [&](const Sm<V>& s, int base, int stride, V (&v)[N]) {
@@ -500,8 +500,8 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
     const int cx = pos.cx, cy = pos.cy, cz = pos.cz;
     bnd_line = (cx == 0 && la == 0) || (cx == a.mx - 1 && la == N - 1) || (cy == 0 && lb == 0) ||
                (cy == a.my - 1 && lb == N - 1);
-    bnd_k0 = (cz == 0);
-    bnd_k1 = (cz == a.mz - 1);
+    bnd_k0 = (a.dirichlet & FE_DIR_ZLO) && cz == 0;
+    bnd_k1 = (a.dirichlet & FE_DIR_ZHI) && cz == a.mz - 1;
   }
   auto masked = [&](int k) { return bnd_line || (k == 0 && bnd_k0) || (k == N - 1 && bnd_k1); };
 

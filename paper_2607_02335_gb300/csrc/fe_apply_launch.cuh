@@ -149,9 +149,10 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
   a.c.mx = m->d.mx;
   a.c.my = m->d.my;
   a.c.mz = m->d.mz;
-  a.c.dirichlet = m->d.dirichlet;
+  a.c.dirichlet = fe_dir_mask(m);
   a.skip = L.skip;
-  const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / m->d.mz, det = hx * hy * hz;
+  const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / fe_mz_global(m),
+               det = hx * hy * hz;
   a.c.aff[0] = fe_cast<V>(det / (hx * hx));
   a.c.aff[1] = fe_cast<V>(det / (hy * hy));
   a.c.aff[2] = fe_cast<V>(det / (hz * hz));

@@ -794,7 +794,7 @@ fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const do
   P.mx = m->d.mx;
   P.my = m->d.my;
   P.mz = m->d.mz;
-  P.dirichlet = m->d.dirichlet;
+  P.dirichlet = fe_dir_mask(m);
   const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / m->d.mz, det = hx * hy * hz;
   P.aff[0] = det / (hx * hx);
   P.aff[1] = det / (hy * hy);
@@ -892,9 +892,10 @@ extern "C" fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes
       fe_set_error("fe_cg_solve_batched: problem %d: null or misaligned argument", i);
       return FE_ERR_INVALID;
     }
-    if (meshes[i]->d.geom_mode == FE_GEOM_RECOMPUTE || meshes[i]->packed ||
+    if (meshes[i]->d.geom_mode == FE_GEOM_RECOMPUTE || meshes[i]->packed || meshes[i]->mzg > 0 ||
         meshes[i]->d.device != meshes[0]->d.device) {
-      fe_set_error("fe_cg_solve_batched: problem %d: needs stored/affine geometry on one device", i);
+      fe_set_error("fe_cg_solve_batched: problem %d: needs whole meshes with stored/affine geometry "
+                   "on one device", i);
       return FE_ERR_INVALID;
     }
     for (int j = 0; j < i; ++j)

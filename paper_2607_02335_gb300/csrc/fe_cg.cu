@@ -27,8 +27,10 @@
 namespace {
 
 // ---- element-wise kernels -------------------------------------------------------------------
+// 1/multiplicity per cell-wise node (0 on Dirichlet nodes).  A slab's bottom / top nodes have a
+// copy in the neighbouring slab when nbr_lo / nbr_hi; `mask` holds the FE_DIR_* Dirichlet faces.
 __global__ void k_invmult(float* __restrict__ out, long long ncells, int n, int mx, int my, int mz,
-                          int dirichlet) {
+                          int mask, int nbr_lo, int nbr_hi) {
   const int n3 = n * n * n, p = n - 1;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -41,9 +43,10 @@ __global__ void k_invmult(float* __restrict__ out, long long ncells, int n, int 
       int mult = 1;
       if (gx % p == 0 && gx > 0 && gx < mx * p) mult *= 2;
       if (gy % p == 0 && gy > 0 && gy < my * p) mult *= 2;
-      if (gz % p == 0 && gz > 0 && gz < mz * p) mult *= 2;
-      const bool bnd = dirichlet && (gx == 0 || gx == mx * p || gy == 0 || gy == my * p ||
-                                     gz == 0 || gz == mz * p);
+      if (gz % p == 0 && ((gz > 0 && gz < mz * p) || (gz == 0 && nbr_lo) || (gz == mz * p && nbr_hi)))
+        mult *= 2;
+      const bool bnd = ((mask & FE_DIR_XY) && (gx == 0 || gx == mx * p || gy == 0 || gy == my * p)) ||
+                       ((mask & FE_DIR_ZLO) && gz == 0) || ((mask & FE_DIR_ZHI) && gz == mz * p);
       out[c * n3 + l] = bnd ? 0.0f : 1.0f / (float)mult;
     }
   }
@@ -305,6 +308,13 @@ static void free_work(CgWork* w, cudaStream_t st) {
   delete w;
 }
 
+fe_status fe_launch_invmult(const fe_mesh* m, float* out, cudaStream_t st) {
+  k_invmult<<<grid_for(m->ncells * 32), 256, 0, st>>>(out, m->ncells, m->n, m->d.mx, m->d.my,
+                                                      m->d.mz, fe_dir_mask(m), m->nbr_lo,
+                                                      m->nbr_hi);
+  return fe_cuda_check(cudaGetLastError(), "invmult launch");
+}
+
 fe_status fe_cg_get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
   fe_mesh* m = const_cast<fe_mesh*>(cm);
   CgWork* w = static_cast<CgWork*>(m->cg_work);
@@ -327,9 +337,7 @@ fe_status fe_cg_get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
                      "cg partials"));
     FE_TRY(fe_dalloc((void**)&w->sc, 2 * sizeof(CgScal), w->st, "cg scalars"));
     FE_CUDA(cudaMallocHost(&w->hsc, 2 * sizeof(CgScal)), "cudaMallocHost cg scalars");
-    k_invmult<<<grid_for(m->ncells * 32), 256, 0, w->st>>>(w->invmult, m->ncells, m->n, m->d.mx,
-                                                           m->d.my, m->d.mz, m->d.dirichlet);
-    FE_CUDA(cudaGetLastError(), "invmult launch");
+    FE_TRY(fe_launch_invmult(m, w->invmult, w->st));
   }
   if (mixed && !w->r32) {
     float** f[] = {&w->r32, &w->z32, &w->p32, &w->q32, &w->w32, &w->d32};
@@ -572,8 +580,8 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
                  opts->rtol, opts->mixed);
     return FE_ERR_INVALID;
   }
-  if (m->packed) {
-    fe_set_error("fe_cg_solve: FE_LAYOUT_CELLS meshes only");
+  if (m->packed || m->mzg > 0) {
+    fe_set_error("fe_cg_solve: FE_LAYOUT_CELLS meshes only (slabs: fe_slab_cg_solve)");
     return FE_ERR_INVALID;
   }
   if (lowp && m->d.geom_mode != FE_GEOM_STORED) {

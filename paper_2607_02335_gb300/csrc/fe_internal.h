@@ -56,6 +56,11 @@ struct fe_mesh {
   unsigned short* geo16[2] = {nullptr, nullptr};  // bf16 / fp16 metric, scaled by gscale[op]
   float gscale[2] = {1.0f, 1.0f};                 // powers of two: Laplace terms, w detJ
   bool tri = false;  // a block of a block-structured mesh (trilinear map of its corners)
+  // slab of a larger structured mesh (fe_slab_create): d.mz is the slab's own layer count, the
+  // slab starts at global layer zoff of mzg, and has neighbouring slabs below / above when
+  // nbr_lo / nbr_hi (their interface planes are not Dirichlet boundary)
+  int zoff = 0, mzg = 0;
+  bool nbr_lo = false, nbr_hi = false;
   // storage grid of the vectors (FE_LAYOUT_PACKED2: units of 2x2x2 cells with sn = 2p+1 nodes per
   // side; otherwise the cells with sn = n) -- what the DSS passes walk
   bool packed = false;
@@ -82,6 +87,16 @@ struct fe_mesh {
   cudaStream_t st = nullptr;  // stream of the mesh's own set-up work
 };
 
+// Dirichlet faces of a mesh as the kernels take them: bit 0 the x and y faces, bit 1 the bottom
+// z face, bit 2 the top z face (0: no Dirichlet boundary)
+enum { FE_DIR_XY = 1, FE_DIR_ZLO = 2, FE_DIR_ZHI = 4 };
+inline int fe_dir_mask(const fe_mesh* m) {
+  if (!m->d.dirichlet) return 0;
+  return FE_DIR_XY | (m->nbr_lo ? 0 : FE_DIR_ZLO) | (m->nbr_hi ? 0 : FE_DIR_ZHI);
+}
+// global layer count of the mesh a (slab) mesh belongs to
+inline int fe_mz_global(const fe_mesh* m) { return m->mzg > 0 ? m->mzg : m->d.mz; }
+
 // ---------------------------------------------------------------------------------------------
 // helpers shared by the translation units of the library
 // ---------------------------------------------------------------------------------------------
@@ -96,8 +111,9 @@ fe_status fe_cuda_check(cudaError_t e, const char* what);
 
 fe_status fe_ensure_geometry(const fe_mesh* m, int prec, bool native);  // fe_mesh.cu
 // fe_mesh_create with an optional trilinear block map (8 corners, 24 doubles; null = unit cube)
+// z0 < z1: build only the slab of layers [z0, z1) of the mesh d describes (z1 = 0: all of it)
 fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void* stream,
-                              fe_mesh** out);
+                              fe_mesh** out, int z0 = 0, int z1 = 0);
 
 // Stream-ordered device memory from a library-owned pool of the current device (fe_mesh.cu).
 // Frees never synchronize the device; the pool keeps freed memory for reuse until fe_pool_trim.
@@ -123,6 +139,10 @@ struct ApplyLaunch {
   int* brick_out = nullptr;   // assembled launches with this set leave the DSS passes to the
                               // caller and report the brick (bx, by) the kernel summed inside
 };
+// fe_apply with its checks; an assembled call with brick_out set leaves the DSS passes to the
+// caller as ApplyLaunch::brick_out does (fe_api.cu)
+fe_status fe_apply_impl(const fe_mesh* m, fe_op op, fe_prec prec, const void* x, void* y,
+                        unsigned flags, void* stream, int* brick_out);
 fe_status fe_launch_apply_f64dw(const ApplyLaunch& a);
 fe_status fe_launch_apply_f64native(const ApplyLaunch& a);
 fe_status fe_launch_apply_f32(const ApplyLaunch& a);
@@ -135,11 +155,17 @@ fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st);
 // bx x by cells: all z-interfaces, then the y- and x-interfaces between bricks
 fe_status fe_launch_dss_strided(const fe_mesh* m, int prec, void* v, int bx, int by,
                                 cudaStream_t st);
+// the passes of axes axis_hi down to axis_lo (2 = z, 1 = y, 0 = x) of fe_launch_dss_strided
+fe_status fe_launch_dss_axes(const fe_mesh* m, int prec, void* v, int bx, int by, int axis_hi,
+                             int axis_lo, cudaStream_t st);
 // the structured passes inside every block of a block-structured mesh, one launch per axis
 // (sx, sy > 1: only the x/y interfaces between bricks, after a brick-fused apply)
 fe_status fe_launch_dss_blocks(const fe_mesh* const* blocks, const long long* off, int nb,
                                int prec, void* v, int sx, int sy, cudaStream_t st);
 fe_status fe_launch_diag(const fe_mesh* m, int op, double* d, cudaStream_t st);
+// 1 / multiplicity of every cell-wise node (interface copies of neighbouring slabs counted), 0 on
+// Dirichlet nodes (fe_cg.cu)
+fe_status fe_launch_invmult(const fe_mesh* m, float* out, cudaStream_t st);
 fe_status fe_launch_pairing(const fe_mesh* m, int prec, const void* a, const void* b,
                             double* out, cudaStream_t st);
 

@@ -27,7 +27,8 @@ struct ManArgs {
   const double* u;  // l2: cell-wise solution; rhs: unused
   double* out;      // rhs: cell-wise load vector; l2: per-cell error^2
   long long ncells;
-  int mx, my, mz, kind;
+  int mx, my, mz, kind;  // mz: layers of the whole mesh (a slab's cells start at layer z0)
+  int z0;
   double amp;
   QTab tab;
 };
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(NQ* NQ* NQ) k_manufactured(const __grid_consta
   const long long cell = blockIdx.x;
   const int t = threadIdx.x;
   const int cx = (int)(cell % a.mx), cy = (int)((cell / a.mx) % a.my),
-            cz = (int)(cell / ((long long)a.mx * a.my));
+            cz = a.z0 + (int)(cell / ((long long)a.mx * a.my));
   // nodes
   if (t < N3) {
     const int i = t % N, j = (t / N) % N, k = t / N2;
@@ -255,7 +256,8 @@ fe_status run_man(const fe_mesh* m, int kind, const double* u, double* out, cuda
   a.ncells = m->ncells;
   a.mx = m->d.mx;
   a.my = m->d.my;
-  a.mz = m->d.mz;
+  a.mz = fe_mz_global(m);
+  a.z0 = m->zoff;
   a.kind = kind;
   a.amp = m->d.deform_amp;
   double s[MAXQ], w[MAXQ];

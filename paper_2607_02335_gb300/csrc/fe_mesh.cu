@@ -96,7 +96,8 @@ struct GeoArgs {
   double* geo;  // [cell][7][n3] or null
   double* xyz;  // [cell][3][n3] or null
   long long ncells;
-  int mx, my, mz;
+  int mx, my, mz;  // cells of the whole mesh
+  int z0;          // global layer of the first layer of cells built (a slab's offset)
   double amp;
   int tri;              // 1: trilinear block map of `corners` instead of the unit-cube map Phi
   double corners[24];   // block corners c = i + 2j + 4k (x, y, z each)
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(N* N* N) k_geometry(const __grid_constant__ Ge
   const int t = threadIdx.x;
   const int i = t % N, j = (t / N) % N, k = t / N2;
   const int cx = (int)(cell % a.mx), cy = (int)((cell / a.mx) % a.my),
-            cz = (int)(cell / ((long long)a.mx * a.my));
+            cz = a.z0 + (int)(cell / ((long long)a.mx * a.my));
   {
     double x[3];
     geo_point(a, (cx + a.tab.t[i]) / a.mx, (cy + a.tab.t[j]) / a.my, (cz + a.tab.t[k]) / a.mz, x);
@@ -403,7 +404,7 @@ extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, void* stream, fe_mesh
 
 // corners: null for the unit-cube map Phi, else the 8 corners of a trilinear block (24 doubles)
 fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void* stream,
-                              fe_mesh** out) {
+                              fe_mesh** out, int z0, int z1) {
   if (!d || !out) {
     fe_set_error("fe_mesh_create: null argument");
     return FE_ERR_INVALID;
@@ -435,11 +436,18 @@ fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void
                  "stored or affine geometry");
     return FE_ERR_INVALID;
   }
+  const bool slab = z1 > 0;
+  if (slab && (z0 < 0 || z1 <= z0 || z1 > d->mz || d->layout != FE_LAYOUT_CELLS || corners)) {
+    fe_set_error("fe_slab_create: need 0 <= z0 < z1 <= mz (%d, %d, %d) and FE_LAYOUT_CELLS", z0, z1,
+                 d->mz);
+    return FE_ERR_INVALID;
+  }
+  const int mzl = slab ? z1 - z0 : d->mz;  // layers of cells built here
   if (!(std::fabs(d->deform_amp) <= 0.2)) {
     fe_set_error("fe_mesh_create: |deform_amp| must be <= 0.2 (keeps the map invertible)");
     return FE_ERR_INVALID;
   }
-  const long long ncells = (long long)d->mx * d->my * d->mz;
+  const long long ncells = (long long)d->mx * d->my * mzl;
   const long long n3 = (long long)(d->degree + 1) * (d->degree + 1) * (d->degree + 1);
   if (ncells * n3 > (1LL << 40)) {
     fe_set_error("fe_mesh_create: mesh too large");
@@ -452,16 +460,23 @@ fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void
     return FE_ERR_OOM;
   }
   m->d = *d;
+  m->d.mz = mzl;
+  if (slab) {
+    m->zoff = z0;
+    m->mzg = d->mz;
+    m->nbr_lo = z0 > 0;
+    m->nbr_hi = z1 < d->mz;
+  }
   m->p = d->degree;
   m->n = d->degree + 1;
   m->n3 = (int)n3;
   m->ncells = ncells;
   m->ncw = ncells * n3;
-  m->nu = (long long)(d->mx * m->p + 1) * (d->my * m->p + 1) * (d->mz * m->p + 1);
+  m->nu = (long long)(d->mx * m->p + 1) * (d->my * m->p + 1) * ((long long)mzl * m->p + 1);
   m->packed = d->layout == FE_LAYOUT_PACKED2;
   m->sgx = m->packed ? d->mx / 2 : d->mx;
   m->sgy = m->packed ? d->my / 2 : d->my;
-  m->sgz = m->packed ? d->mz / 2 : d->mz;
+  m->sgz = m->packed ? d->mz / 2 : mzl;
   m->sn = m->packed ? 2 * m->p + 1 : m->n;
   if (m->packed) m->ncw = (long long)m->sgx * m->sgy * m->sgz * m->sn * m->sn * m->sn;
   fe_host_tables(m->p, &m->tab);
@@ -480,6 +495,7 @@ fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void
   g.mx = d->mx;
   g.my = d->my;
   g.mz = d->mz;
+  g.z0 = slab ? z0 : 0;
   g.amp = d->deform_amp;
   if (corners) {
     g.tri = 1;

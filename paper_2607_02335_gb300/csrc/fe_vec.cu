@@ -89,7 +89,8 @@ static unsigned grid_cap(long long n, int threads) {
 }
 
 template <class S>
-static fe_status dss_t(const fe_mesh* m, S* v, int sx, int sy, cudaStream_t st) {
+static fe_status dss_t(const fe_mesh* m, S* v, int sx, int sy, cudaStream_t st, int axis_hi = 2,
+                       int axis_lo = 0) {
   // the storage grid: cells, or 2^3-packed units whose sides carry 2p+1 nodes
   const int n = m->sn, n2 = n * n;
   const int mx = m->sgx, my = m->sgy, mz = m->sgz;
@@ -97,7 +98,7 @@ static fe_status dss_t(const fe_mesh* m, S* v, int sx, int sy, cudaStream_t st) 
   const long long work[3] = {(long long)((mx - 1) / sx) * my * mz * n2,
                              (long long)mx * ((my - 1) / sy) * mz * n2,
                              (long long)mx * my * (mz - 1) * n2};
-  for (int axis = 2; axis >= 0; --axis) {  // z, y, x
+  for (int axis = axis_hi; axis >= axis_lo; --axis) {  // z, y, x
     if (work[axis] <= 0) continue;
     k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, stride[axis],
                                                              work[axis]);
@@ -113,6 +114,18 @@ fe_status fe_launch_dss_strided(const fe_mesh* m, int prec, void* v, int bx, int
   }
   if (prec == FE_F64) return dss_t<double>(m, (double*)v, bx, by, st);
   if (prec == FE_F32) return dss_t<float>(m, (float*)v, bx, by, st);
+  fe_set_error("dss: unsupported precision %d", prec);
+  return FE_ERR_INVALID;
+}
+
+fe_status fe_launch_dss_axes(const fe_mesh* m, int prec, void* v, int bx, int by, int axis_hi,
+                             int axis_lo, cudaStream_t st) {
+  if (bx < 1 || by < 1 || axis_hi > 2 || axis_lo < 0) {
+    fe_set_error("dss: bad brick %d x %d or axes %d..%d", bx, by, axis_hi, axis_lo);
+    return FE_ERR_INVALID;
+  }
+  if (prec == FE_F64) return dss_t<double>(m, (double*)v, bx, by, st, axis_hi, axis_lo);
+  if (prec == FE_F32) return dss_t<float>(m, (float*)v, bx, by, st, axis_hi, axis_lo);
   fe_set_error("dss: unsupported precision %d", prec);
   return FE_ERR_INVALID;
 }
@@ -328,7 +341,7 @@ static fe_status launch_diag_n(const fe_mesh* m, DiagArgs a, cudaStream_t st) {
 
 // Dirichlet nodes -> 1 (one warp per cell, lanes over the cell's nodes)
 __global__ void k_dirichlet_fill(double* __restrict__ v, double val, long long ncells, int n, int mx,
-                                 int my, int mz) {
+                                 int my, int mz, int mask) {
   const int n3 = n * n * n, p = n - 1;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -339,7 +352,8 @@ __global__ void k_dirichlet_fill(double* __restrict__ v, double val, long long n
     for (int l = lane; l < n3; l += 32) {
       const int i = l % n, j = (l / n) % n, k = l / (n * n);
       if ((cx == 0 && i == 0) || (cx == mx - 1 && i == p) || (cy == 0 && j == 0) ||
-          (cy == my - 1 && j == p) || (cz == 0 && k == 0) || (cz == mz - 1 && k == p))
+          (cy == my - 1 && j == p) || ((mask & FE_DIR_ZLO) && cz == 0 && k == 0) ||
+          ((mask & FE_DIR_ZHI) && cz == mz - 1 && k == p))
         v[c * n3 + l] = val;
     }
   }
@@ -353,7 +367,8 @@ fe_status fe_launch_diag(const fe_mesh* m, int op, double* d, cudaStream_t st) {
   a.ncells = m->ncells;
   a.op = op;
   a.affine = m->d.geom_mode == FE_GEOM_AFFINE;
-  const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / m->d.mz, det = hx * hy * hz;
+  const double hx = 1.0 / m->d.mx, hy = 1.0 / m->d.my, hz = 1.0 / fe_mz_global(m),
+               det = hx * hy * hz;
   a.aff[0] = det / (hx * hx);
   a.aff[1] = det / (hy * hy);
   a.aff[2] = det / (hz * hz);
@@ -385,8 +400,8 @@ fe_status fe_launch_diag(const fe_mesh* m, int op, double* d, cudaStream_t st) {
   if (s != FE_OK) return s;
   FE_TRY(fe_launch_dss(m, FE_F64, d, st));
   if (m->d.dirichlet) {
-    k_dirichlet_fill<<<grid_cap(m->ncells * 32, 256), 256, 0, st>>>(d, 1.0, m->ncells, m->n,
-                                                                    m->d.mx, m->d.my, m->d.mz);
+    k_dirichlet_fill<<<grid_cap(m->ncells * 32, 256), 256, 0, st>>>(
+        d, 1.0, m->ncells, m->n, m->d.mx, m->d.my, m->d.mz, fe_dir_mask(m));
     FE_TRY(fe_cuda_check(cudaGetLastError(), "dirichlet fill"));
   }
   return FE_OK;

@@ -18,7 +18,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 # ---- enums (mirrors of include/fe.h) ----------------------------------------------------------
 FE_OK, FE_ERR_INVALID, FE_ERR_OOM, FE_ERR_CUDA = 0, 1, 2, 3
-FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN, FE_ERR_TIMEOUT, FE_ERR_BUSY = 4, 5, 6, 7
+FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN, FE_ERR_TIMEOUT, FE_ERR_BUSY, FE_ERR_COMM = 4, 5, 6, 7, 8
 FE_LAPLACE, FE_MASS = 0, 1
 FE_F64, FE_F32, FE_BF16_F32ACC, FE_F16_F32ACC = 0, 1, 2, 3
 FE_GEOM_STORED, FE_GEOM_RECOMPUTE, FE_GEOM_AFFINE = 0, 1, 2
@@ -28,7 +28,7 @@ FE_RHS_SINE, FE_RHS_QUADRATIC = 0, 1
 
 STATUS_NAMES = {0: "FE_OK", 1: "FE_ERR_INVALID", 2: "FE_ERR_OOM", 3: "FE_ERR_CUDA",
                 4: "FE_ERR_NOT_CONVERGED", 5: "FE_ERR_BREAKDOWN", 6: "FE_ERR_TIMEOUT",
-                7: "FE_ERR_BUSY"}
+                7: "FE_ERR_BUSY", 8: "FE_ERR_COMM"}
 
 
 class fe_mesh_desc(ctypes.Structure):
@@ -64,6 +64,24 @@ class fe_mb_desc(ctypes.Structure):
 class fe_amr_desc(ctypes.Structure):
     _fields_ = [("mc", ctypes.c_int), ("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3),
                 ("degree", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class fe_slab_desc(ctypes.Structure):
+    _fields_ = [("global_", fe_mesh_desc), ("z0", ctypes.c_int), ("z1", ctypes.c_int)]
+
+
+# int exchange(void* ctx, int sides, int elem_bytes, long long count, void* stream)
+FE_EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_longlong, ctypes.c_void_p)
+# int allgather(void* ctx, int n, void* stream)
+FE_ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
+
+
+class fe_comm(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int), ("size", ctypes.c_int), ("send", ctypes.c_void_p * 2),
+                ("recv", ctypes.c_void_p * 2), ("red_send", ctypes.c_void_p),
+                ("red_all", ctypes.c_void_p), ("exchange", FE_EXCHANGE_FN),
+                ("allgather", FE_ALLGATHER_FN), ("ctx", ctypes.c_void_p)]
 
 
 _vp, _i, _u, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double
@@ -102,6 +120,14 @@ _SIGS = {
     "fe_amr_layout": [_vp, ctypes.POINTER(fe_layout)],
     "fe_amr_apply": [_vp, _i, _i, _vp, _vp, _u, _vp],
     "fe_amr_dss": [_vp, _i, _vp, _vp, _vp],
+    "fe_slab_create": [ctypes.POINTER(fe_slab_desc), _vp, ctypes.POINTER(_MESH)],
+    "fe_slab_plane_len": [_MESH, ctypes.POINTER(ctypes.c_longlong)],
+    "fe_slab_face_pack": [_MESH, _i, _vp, _i, _vp, _vp],
+    "fe_slab_face_add": [_MESH, _i, _vp, _i, _vp, _vp],
+    "fe_slab_dss": [_MESH, _i, _vp, _vp, ctypes.POINTER(fe_comm), _vp],
+    "fe_slab_apply": [_MESH, _i, _i, _vp, _vp, _u, ctypes.POINTER(fe_comm), _vp],
+    "fe_slab_cg_solve": [_MESH, _vp, _vp, ctypes.POINTER(fe_cg_opts), ctypes.POINTER(fe_comm),
+                         ctypes.POINTER(fe_cg_result), _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -486,3 +512,48 @@ class AMRMesh:
             self.close()
         except Exception:
             pass
+
+
+# ---- slab decomposition (one structured mesh over several slabs) ---------------------------------
+def fe_slab_create(desc: fe_slab_desc, stream=None) -> int:
+    h = _MESH()
+    _check(_lib.fe_slab_create(ctypes.byref(desc), _stream(stream), ctypes.byref(h)), "fe_slab_create")
+    return h.value
+
+
+def fe_slab_plane_len(mesh: int) -> int:
+    c = ctypes.c_longlong(0)
+    _check(_lib.fe_slab_plane_len(mesh, ctypes.byref(c)), "fe_slab_plane_len")
+    return c.value
+
+
+def fe_slab_face_pack(mesh: int, prec: int, v, side: int, plane, stream=None) -> None:
+    _check(_lib.fe_slab_face_pack(mesh, prec, _ptr(v), side, _ptr(plane), _stream(stream)),
+           "fe_slab_face_pack")
+
+
+def fe_slab_face_add(mesh: int, prec: int, v, side: int, plane, stream=None) -> None:
+    _check(_lib.fe_slab_face_add(mesh, prec, _ptr(v), side, _ptr(plane), _stream(stream)),
+           "fe_slab_face_add")
+
+
+def fe_slab_dss(mesh: int, prec: int, r, z, comm: fe_comm, stream=None) -> None:
+    _check(_lib.fe_slab_dss(mesh, prec, _ptr(r), _ptr(z), ctypes.byref(comm), _stream(stream)),
+           "fe_slab_dss")
+
+
+def fe_slab_apply(mesh: int, op: int, prec: int, x, y, flags: int, comm, stream=None) -> None:
+    c = None if comm is None else ctypes.byref(comm)
+    _check(_lib.fe_slab_apply(mesh, op, prec, _ptr(x), _ptr(y), flags, c, _stream(stream)),
+           "fe_slab_apply")
+
+
+def fe_slab_cg_solve(mesh: int, b, x, opts: fe_cg_opts, comm: fe_comm, stream=None) -> fe_cg_result:
+    """As fe_cg_solve: FE_ERR_NOT_CONVERGED / FE_ERR_BREAKDOWN are reported in result.status."""
+    res = fe_cg_result()
+    st = _lib.fe_slab_cg_solve(mesh, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(comm),
+                               ctypes.byref(res), _stream(stream))
+    if st not in (FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN):
+        raise FeError(st, "fe_slab_cg_solve")
+    res.status = st
+    return res
