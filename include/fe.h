@@ -124,6 +124,22 @@ fe_status fe_mesh_layout(const fe_mesh* mesh, fe_layout* out);
 fe_status fe_gather(const fe_mesh* mesh, const double* x_unique_host, double* x_cell_dev,
                     void* stream);
 
+/* Operator apply on HOST vectors in unique-node form: for each of the nop (1 or 2) operators
+ * ops[k], y_unique_host[k] = G^T A_D G x_unique_host, the assembled operator on the global node
+ * vector (Sec. 2.1: G the gather, A_D the operator of fe_apply).  x_unique_host and each
+ * y_unique_host[k] hold unique_dofs doubles in fe_gather's lexicographic order.  Only these
+ * unique-node vectors cross the host link (cell-wise storage, 2.4x larger at Q3, stays on the
+ * device): the call copies x in once, expands it to cell-wise form with a kernel, runs fe_apply
+ * with FE_ASSEMBLE per operator, and copies one copy of every node back, each read-back
+ * overlapping the next operator's apply.  Stream-ordered: it returns once the work is enqueued;
+ * with page-locked host buffers (cudaHostAlloc) the copies are asynchronous and the buffers must
+ * stay untouched until `stream` has passed the call (synchronize it or wait on an event).  The
+ * device staging (one unique and two cell-wise vectors, plus one unique vector per output) belongs
+ * to the mesh and is allocated on first use, so calls on one mesh must be ordered on one stream.
+ * FE_F64 arithmetic; flags 0 or FE_NATIVE_F64; FE_LAYOUT_CELLS meshes (slabs included). */
+fe_status fe_apply_host(const fe_mesh* mesh, int nop, const fe_op* ops, const double* x_unique_host,
+                        double* const* y_unique_host, unsigned flags, void* stream);
+
 /* Local operator apply (Sec. 3.1 "local operator"; Eq. (mass_operator) / (laplace_operator)
  * with per-quadrature-point geometry): y_K = A_K x_K for every cell K (dual, unassembled).
  * With FE_ASSEMBLE the structured DSS follows (Sec. 4.1): y = S(A x), continuous.  x and y must

@@ -81,6 +81,12 @@ struct fe_mesh {
   // reduction scratch
   double* red = nullptr;
   int red_len = 0;
+  // host-vector applies (fe_host.cu): device staging of the unique-node input, its cell-wise
+  // expansion, the assembled cell-wise output and up to two unique-node outputs; a copy stream for
+  // the read-backs and events ordering it against the caller's stream
+  double *hs_xu = nullptr, *hs_xc = nullptr, *hs_yc = nullptr, *hs_yu[2] = {nullptr, nullptr};
+  cudaStream_t hs_copy = nullptr;
+  cudaEvent_t hs_ev[3] = {nullptr, nullptr, nullptr};
   // conjugate-gradient workspace (fe_cg.cu), released through cg_free
   void* cg_work = nullptr;
   void (*cg_free)(void*, cudaStream_t) = nullptr;

@@ -385,8 +385,12 @@ static void free_mesh(fe_mesh* m, cudaStream_t st) {
                   m->xyz32, m->rc_scratch[0],
                   m->rc_scratch[1], m->rc_scratch[2], m->diag64[0],
                   m->diag64[1], m->invdiag32[0], m->invdiag32[1], m->invdiag64[0],
-                  m->invdiag64[1], m->invmult64, m->red};
+                  m->invdiag64[1], m->invmult64, m->red, m->hs_xu, m->hs_xc, m->hs_yc,
+                  m->hs_yu[0], m->hs_yu[1]};
   for (void* b : bufs) fe_dfree(b, st);
+  for (cudaEvent_t e : m->hs_ev)
+    if (e) cudaEventDestroy(e);
+  if (m->hs_copy) cudaStreamDestroy(m->hs_copy);
   if (m->st) cudaStreamDestroy(m->st);
   delete m;
 }

@@ -92,6 +92,7 @@ _SIGS = {
     "fe_mesh_layout": [_MESH, ctypes.POINTER(fe_layout)],
     "fe_gather": [_MESH, _vp, _vp, _vp],
     "fe_apply": [_MESH, _i, _i, _vp, _vp, _u, _vp],
+    "fe_apply_host": [_MESH, _i, ctypes.POINTER(_i), _vp, ctypes.POINTER(_vp), _u, _vp],
     "fe_dss": [_MESH, _i, _vp, _vp, _vp],
     "fe_diag": [_MESH, _i, _vp, _vp],
     "fe_pairing": [_MESH, _i, _vp, _vp, _vp, _vp],
@@ -193,6 +194,23 @@ def fe_gather(mesh: int, x_unique_host, x_cell_dev, stream=None) -> None:
 
 def fe_apply(mesh: int, op: int, prec: int, x, y, flags: int = 0, stream=None) -> None:
     _check(_lib.fe_apply(mesh, op, prec, _ptr(x), _ptr(y), flags, _stream(stream)), "fe_apply")
+
+
+def fe_apply_host(mesh: int, ops, x_unique_host, y_unique_host, flags: int = 0, stream=None) -> None:
+    """ops: sequence of 1 or 2 operators; x_unique_host / y_unique_host: host buffers (numpy arrays,
+    pinned torch CPU tensors or raw addresses) of unique_dofs doubles; stream-ordered (see
+    include/fe.h)."""
+    def addr(b):
+        if isinstance(b, int):
+            return b
+        if hasattr(b, "data_ptr"):
+            return b.data_ptr()
+        return b.ctypes.data
+    n = len(ops)
+    o = (_i * max(n, 1))(*ops)
+    ys = (_vp * max(len(y_unique_host), 1))(*[addr(y) for y in y_unique_host])
+    _check(_lib.fe_apply_host(mesh, n, o, addr(x_unique_host), ys, flags, _stream(stream)),
+           "fe_apply_host")
 
 
 def fe_dss(mesh: int, prec: int, r, z, stream=None) -> None:
