@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-cap-s", type=float, default=60.0, help="wall-time cap per serving run")
     ap.add_argument("--no-extras", action="store_true", help="operator sweep only")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of extra blocks to run (default all): geometry_recompute, "
+                         "reduced_precision_apply, block_structured_dss, packed_storage, "
+                         "hanging_node_dss, slab_decomposition, solve_mixed_vs_fp64, batched, "
+                         "serving")
     ap.add_argument("--profile-case", default=None,
                     help="p,m,op: only run K+W applies of one case (for profiler captures)")
     return ap.parse_args()
@@ -165,6 +170,29 @@ class OracleSampler:
         return (f"element-by-element FP64 apply with precomputed element matrices on the first "
                 f"{SAMPLE_CELLS} cells (per degree) of each sweep mesh, Laplace and mass, rates "
                 f"scaled to the full step (DSS not included)")
+
+
+def csr_spmv_baseline(threads, p=2, m=48, reps=10):
+    """The oracle's assembled CSR matrix of the Q2 48^3 deformed Laplace (about 1.1e8 nonzeros)
+    and its OpenMP SpMV on the host cores: the sparse-matrix baseline of the unique-DoF rate."""
+    import oracle as O
+    from paper_2607_02335_gb300 import synth as S
+    mesh = O.Mesh(m, p, amp=AMP)
+    t0 = time.perf_counter()
+    csr = O.assemble_csr(mesh, O.LAPLACE, nthreads=threads)
+    t_asm = time.perf_counter() - t0
+    x = S.primal_unique(m, p, seed=0)
+    O.csr_spmv(csr, x)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.csr_spmv(csr, x)
+        ts.append(time.perf_counter() - t0)
+    t = float(np.median(ts))
+    return {"mesh": f"Q{p} {m}^3 deformed (amp {AMP}), Laplace A_CG in CSR (oracle assembly)",
+            "nnz": int(len(csr[2])), "unique_dofs": mesh.n_unique, "assembly_s": round(t_asm, 3),
+            "spmv_ms": round(t * 1e3, 3), "gdofs_unique": round(mesh.n_unique / t / 1e9, 4),
+            "cores": threads}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -380,23 +408,29 @@ def run_ours(args, rank, world):
             gm.close()
         del cases, meshes
         torch.cuda.empty_cache()
-        extras["geometry_recompute"] = recompute_geometry(fe, torch, sweep, per_case, flush, stream,
-                                                          reps)
-        extras["reduced_precision_apply"] = reduced_precision_apply(fe, torch, flush, stream)
-        extras["block_structured_dss"] = multiblock_dss(fe, torch, flush, stream)
-        extras["packed_storage"] = packed_storage(fe, torch, flush, stream)
-        extras["hanging_node_dss"] = hanging_node_dss(fe, torch, flush, stream)
-        extras["slab_decomposition"] = slab_decomposition(fe, torch, flush, stream)
-        extras["solve_mixed_vs_fp64"] = mixed_vs_fp64_solve(fe, torch)
-        extras["batched"] = batched_solve(fe, torch, count=args.batch_count)
-        extras["serving"] = {
+        want = None if args.extras == "all" else set(args.extras.split(","))
+
+        def run(name, fn):
+            if want is None or name in want:
+                extras[name] = fn()
+
+        run("geometry_recompute",
+            lambda: recompute_geometry(fe, torch, sweep, per_case, flush, stream, reps))
+        run("reduced_precision_apply", lambda: reduced_precision_apply(fe, torch, flush, stream))
+        run("block_structured_dss", lambda: multiblock_dss(fe, torch, flush, stream))
+        run("packed_storage", lambda: packed_storage(fe, torch, flush, stream))
+        run("hanging_node_dss", lambda: hanging_node_dss(fe, torch, flush, stream))
+        run("slab_decomposition", lambda: slab_decomposition(fe, torch, flush, stream))
+        run("solve_mixed_vs_fp64", lambda: mixed_vs_fp64_solve(fe, torch))
+        run("batched", lambda: batched_solve(fe, torch, count=args.batch_count))
+        run("serving", lambda: {
             "workload": f"Poisson arrivals {args.serve_rate}/s, {args.serve_requests} requests, m "
                         f"lognormal (median 16, sigma 0.5, max 64), p in {{2,3,7}}, amp {AMP}, sine "
                         f"load, rtol 1e-10, budget {args.serve_budget_gb} GB, {args.serve_slots} slots",
             "fp64": serving_run(fe, False, args.serve_requests, args.serve_rate, args.serve_budget_gb,
                                 args.serve_slots, args.serve_cap_s),
             "mixed": serving_run(fe, True, args.serve_requests, args.serve_rate, args.serve_budget_gb,
-                                 args.serve_slots, args.serve_cap_s)}
+                                 args.serve_slots, args.serve_cap_s)})
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -433,6 +467,7 @@ def run_ours(args, rank, world):
         smp.time_once()
         t1, _ = smp.full_step_estimate()
         line["cpu_baseline"]["value_1core"] = round(nu / t1 / 1e9, 6)
+        line["cpu_baseline"]["csr_spmv"] = csr_spmv_baseline(threads)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
