@@ -183,7 +183,18 @@ template <int N, class V>
 struct ApplyArgs {
   CellArgs<N, V> c;
   const int* skip;  // optional device flag: the whole launch returns at once when *skip != 0
+  int zchunk;       // MODE_BRICKZ: z-layers per CTA
   Tab1D<N, V> tab;
+};
+
+// MODE_BRICKZ state of one thread between the layers of its chunk: the stored value of the top
+// node (k = n-1) of its z-line in the previous layer, whose store waits for the pair sum with the
+// bottom node of the same line in the next layer.
+template <class SV>
+struct ZCarry {
+  SV top;
+  bool pending;  // top waits for this layer
+  bool last;     // this layer is the chunk's last: its top node is stored at once
 };
 
 enum { GEOM_STORED_K = 0, GEOM_AFFINE_K = 2 };
@@ -212,8 +223,9 @@ struct CellPos {
   bool active;
 };
 
-// Tile placement modes of an apply launch
-enum { MODE_CELLS = 0, MODE_BRICK = 1, MODE_PACKED = 2 };
+// Tile placement modes of an apply launch.  MODE_BRICKZ: a CTA walks a chunk of z-layers of one
+// brick column, one MODE_BRICK tile per layer, and sums the z-interfaces inside the chunk itself.
+enum { MODE_CELLS = 0, MODE_BRICK = 1, MODE_PACKED = 2, MODE_BRICKZ = 3 };
 // 2^3-packed storage units (Sec. 2.2): 8 cells per unit, whole units per CTA
 template <int N>
 struct Packed {
@@ -236,7 +248,7 @@ __device__ __forceinline__ CellPos cell_pos(const A& a, long long cell0, int cl)
     c.cz = (int)(u / ((long long)ux_n * uy_n)) * 2 + ((sub >> 2) & 1);
     c.active = cl / 8 < Packed<N>::UPB && u < a.ncells / 8;
     c.cell = ((long long)c.cz * a.my + c.cy) * a.mx + c.cx;
-  } else if constexpr (MODE == MODE_BRICK) {  // brick index < 2^31: 32-bit index arithmetic
+  } else if constexpr (MODE == MODE_BRICK || MODE == MODE_BRICKZ) {  // brick index < 2^31
     constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
     const unsigned nbx = (unsigned)(a.mx + BX - 1) / BX, nby = (unsigned)(a.my + BY - 1) / BY;
     const unsigned b = (unsigned)cell0, rb = b / nbx;
@@ -469,8 +481,11 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
 template <int N, class V, int OP, int GEOM, int MODE = MODE_CELLS>
 __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
                                             long long cell0, unsigned char* smraw,
-                                            int tile_stride) {
+                                            int tile_stride,
+                                            ZCarry<typename NT<V>::SV>* zc = nullptr) {
   static_assert(MODE != MODE_PACKED || N < FE_ROLL_MINN, "packed units: unrolled degrees only");
+  static_assert(MODE != MODE_BRICKZ || (N < FE_ROLL_MINN && !NT<V>::LOWP),
+                "z-carry bricks: unrolled degrees, FP64 / double-word / FP32 values");
   if constexpr (N >= FE_ROLL_MINN && MODE != MODE_PACKED) {
     apply_cells_rolled<N, V, OP, GEOM, MODE>(a, tab, cell0, smraw, tile_stride);
     return;
@@ -660,7 +675,36 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   __syncthreads();
   tile_sweep<N, V, 1, 1>(s0, cb, la, lb, tab.eVT);
   __syncthreads();
-  if constexpr (MODE == MODE_BRICK) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
+  if constexpr (MODE == MODE_BRICK || MODE == MODE_BRICKZ) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
+  if constexpr (MODE == MODE_BRICKZ) {
+    // The z-interface with the previous layer of the chunk: the structured DSS's z-pass pair sum
+    // (lower + upper copy), formed on the stored values, so the result is that of the pass.
+    // The x/y sums inside the brick came first, as they do before the pass.
+    if (active) {
+      using SV = typename NT<V>::SV;
+      SV bottom = T::to_sv(masked(0) ? T::zero() : s0.get(cb + zl<N>(la, lb, 0)));
+      if (zc->pending) {
+        bottom = zc->top + bottom;
+        T::store_sv(a.y + gbase - (long long)a.mx * a.my * N3 + (N - 1) * N2 + lt, bottom);
+      }
+      T::store_sv(a.y + gbase + lt, bottom);
+#pragma unroll
+      for (int k = 1; k < N - 1; ++k) {
+        V v = s0.get(cb + zl<N>(la, lb, k));
+        if (masked(k)) v = T::zero();
+        T::store(a.y + gbase + k * N2 + lt, v);
+      }
+      const SV top = T::to_sv(masked(N - 1) ? T::zero() : s0.get(cb + zl<N>(la, lb, N - 1)));
+      if (zc->last) {
+        T::store_sv(a.y + gbase + (N - 1) * N2 + lt, top);
+        zc->pending = false;
+      } else {
+        zc->top = top;
+        zc->pending = true;
+      }
+    }
+    return;
+  }
   if constexpr (MODE == MODE_PACKED) {
     // unit-internal assembly: sum the copies on the x-, y- and z-interfaces between the unit's
     // sub-cells in the tile (as the structured DSS passes do, z then y then x), then every stored
@@ -711,6 +755,15 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 #else
 #define FE_APPLY_BOUNDS __launch_bounds__(Cfg<N>::THREADS)
 #endif
+// z-carry bricks: held to a register budget for 3 CTAs per SM (Laplace, as the one-layer brick
+// kernel; left to itself the compiler gives the layer loop 98 registers, 2 CTAs per SM) or 6
+// (mass, whose one-layer kernel needs 32 registers)
+#ifndef FE_ZCARRY_MINB_LAPLACE
+#define FE_ZCARRY_MINB_LAPLACE 3
+#endif
+#ifndef FE_ZCARRY_MINB_MASS
+#define FE_ZCARRY_MINB_MASS 6
+#endif
 template <int N, class V, int OP, int GEOM, int MODE>
 __global__ void FE_APPLY_BOUNDS k_apply(const __grid_constant__ ApplyArgs<N, V> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -723,6 +776,30 @@ __global__ void FE_APPLY_BOUNDS k_apply(const __grid_constant__ ApplyArgs<N, V> 
   else
     cell0 = a.c.cell_base + (long long)blockIdx.x * Cfg<N>::CPB;
   apply_cells<N, V, OP, GEOM, MODE>(a.c, a.tab, cell0, smraw, Cfg<N>::TILE);
+}
+
+// MODE_BRICKZ: blockIdx.x = chunk * (bricks per layer) + brick column; the CTA applies the layers
+// [z0, z1) of its column one after the other
+template <int N, class V, int OP, int GEOM>
+__global__ void __launch_bounds__(Cfg<N>::THREADS,
+                                  OP == FE_LAPLACE ? FE_ZCARRY_MINB_LAPLACE : FE_ZCARRY_MINB_MASS)
+    k_apply_zcarry(const __grid_constant__ ApplyArgs<N, V> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (a.skip && *(volatile const int*)a.skip) return;  // uniform over the grid
+  constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
+  const unsigned per_layer =
+      (unsigned)((a.c.mx + BX - 1) / BX) * (unsigned)((a.c.my + BY - 1) / BY);
+  const unsigned col = blockIdx.x % per_layer, chunk = blockIdx.x / per_layer;
+  const int z0 = (int)chunk * a.zchunk;
+  const int z1 = z0 + a.zchunk < a.c.mz ? z0 + a.zchunk : a.c.mz;
+  ZCarry<typename NT<V>::SV> zc;
+  zc.pending = false;
+  for (int cz = z0; cz < z1; ++cz) {
+    zc.last = cz == z1 - 1;
+    apply_cells<N, V, OP, GEOM, MODE_BRICKZ>(a.c, a.tab, (long long)cz * per_layer + col, smraw,
+                                             Cfg<N>::TILE, &zc);
+    __syncthreads();  // the next layer refills the tile
+  }
 }
 
 template <int N, class V>

@@ -1,6 +1,7 @@
 // fe_apply_launch.cuh -- host launchers of the apply kernels for one arithmetic V.
 #pragma once
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "fe_recompute.cuh"
@@ -65,7 +66,12 @@ template <int N, class V, int OP, int GEOM, int MODE = MODE_CELLS>
 static fe_status launch_one(const ApplyArgs<N, V>& a, cudaStream_t st) {
   using C = Cfg<N>;
   const size_t smem = apply_smem_bytes<N, V>(OP);
-  auto kern = k_apply<N, V, OP, GEOM, MODE>;
+  auto kern = [] {
+    if constexpr (MODE == MODE_BRICKZ)
+      return k_apply_zcarry<N, V, OP, GEOM>;
+    else
+      return k_apply<N, V, OP, GEOM, MODE>;
+  }();
   static bool attr_done[64] = {};  // one attribute call per instantiation and device
   int dev = 0;
   FE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -79,6 +85,11 @@ static fe_status launch_one(const ApplyArgs<N, V>& a, cudaStream_t st) {
   if constexpr (MODE == MODE_BRICK) {
     constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
     blocks = (long long)((a.c.mx + BX - 1) / BX) * ((a.c.my + BY - 1) / BY) * a.c.mz;
+    threads = BX * BY * C::N2;
+  } else if constexpr (MODE == MODE_BRICKZ) {
+    constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
+    blocks = (long long)((a.c.mx + BX - 1) / BX) * ((a.c.my + BY - 1) / BY) *
+             ((a.c.mz + a.zchunk - 1) / a.zchunk);
     threads = BX * BY * C::N2;
   } else if constexpr (MODE == MODE_PACKED) {
     blocks = (a.c.ncells / 8 + Packed<N>::UPB - 1) / Packed<N>::UPB;
@@ -125,6 +136,65 @@ static fe_status launch_recompute(ApplyArgs<N, V> a, const ApplyLaunch& L,
 }
 
 // the kernel of (operator, geometry mode); 16-bit operand types have stored geometry only
+#ifndef FE_ZCARRY_MAXZ
+#define FE_ZCARRY_MAXZ 16
+#endif
+// Layers per CTA of a z-carry launch (< 2: use the one-layer brick kernel).  The CTAs run
+// zchunk layers each, so the grid's last wave decides the tail: the largest zchunk <=
+// FE_ZCARRY_MAXZ whose grid fills at least four waves of resident CTAs, the last one to 97%
+// (Q3 96^3, double-word: 15 layers for the Laplace kernel at 3 CTAs per SM, 9 for mass at 6).
+template <int N, class V, int OP, int GEOM>
+static fe_status zcarry_slots(int* slots) {
+  static int cached[64] = {};
+  int dev = 0;
+  FE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) {
+    *slots = cached[dev];
+    return FE_OK;
+  }
+  auto kern = k_apply_zcarry<N, V, OP, GEOM>;
+  const size_t smem = apply_smem_bytes<N, V>(OP);
+  FE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+          "apply smem attribute");
+  int per_sm = 0, sms = 0;
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &per_sm, kern, Brick<N>::BX * Brick<N>::BY * Cfg<N>::N2, smem),
+          "occupancy");
+  FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  *slots = per_sm * sms;
+  if (dev >= 0 && dev < 64) cached[dev] = *slots;
+  return FE_OK;
+}
+
+template <int N, class V>
+static fe_status zcarry_chunk(const fe_mesh* m, int op, bool affine, int* zc) {
+  int slots = 0;
+  if (affine)
+    FE_TRY((op == FE_LAPLACE ? zcarry_slots<N, V, FE_LAPLACE, GEOM_AFFINE_K>(&slots)
+                             : zcarry_slots<N, V, FE_MASS, GEOM_AFFINE_K>(&slots)));
+  else
+    FE_TRY((op == FE_LAPLACE ? zcarry_slots<N, V, FE_LAPLACE, GEOM_STORED_K>(&slots)
+                             : zcarry_slots<N, V, FE_MASS, GEOM_STORED_K>(&slots)));
+  *zc = 0;
+  // FE_ZCARRY_CHUNK=k in the environment forces k layers per CTA (0 or 1: the one-layer kernel)
+  if (const char* force = std::getenv("FE_ZCARRY_CHUNK")) {
+    const int k = std::atoi(force);
+    *zc = k < 2 ? 0 : (k < m->d.mz ? k : m->d.mz);
+    return FE_OK;
+  }
+  if (slots < 1) return FE_OK;
+  constexpr int BX = Brick<N>::BX, BY = Brick<N>::BY;
+  const double per_layer = (double)((m->d.mx + BX - 1) / BX) * ((m->d.my + BY - 1) / BY);
+  for (int z = FE_ZCARRY_MAXZ < m->d.mz ? FE_ZCARRY_MAXZ : m->d.mz; z >= 2; --z) {
+    const double waves = (double)((m->d.mz + z - 1) / z) * per_layer / slots;
+    if (waves >= 4.0 && waves / std::ceil(waves) >= 0.97) {
+      *zc = z;
+      break;
+    }
+  }
+  return FE_OK;
+}
+
 template <int N, class V, int MODE>
 static fe_status launch_geom(const ApplyArgs<N, V>& a, int op, bool affine, cudaStream_t st) {
   if constexpr (!NT<V>::LOWP) {
@@ -200,6 +270,20 @@ static fe_status launch_apply_n(const ApplyLaunch& L, const typename NT<V>::GV* 
 #define FE_FUSE_MAXN 4
 #endif
   const bool fuse = L.assemble && N <= FE_FUSE_MAXN;
+  // Fused assembled applies with the DSS passes left to this launcher also sum the z-interfaces
+  // in the kernel: a CTA walks zchunk layers of its brick column; only the interfaces between
+  // chunks remain for the z-pass.
+  if constexpr (N <= FE_FUSE_MAXN && N < FE_ROLL_MINN && !NT<V>::LOWP) {
+    if (fuse && !L.brick_out) {
+      int zc = 0;
+      FE_TRY((zcarry_chunk<N, V>(m, L.op, affine, &zc)));
+      if (zc >= 2) {
+        a.zchunk = zc;
+        FE_TRY((launch_geom<N, V, MODE_BRICKZ>(a, L.op, affine, L.st)));
+        return fe_launch_dss_strided3(m, PREC, L.y, Brick<N>::BX, Brick<N>::BY, zc, L.st);
+      }
+    }
+  }
   if (fuse)
     FE_TRY((launch_geom<N, V, MODE_BRICK>(a, L.op, affine, L.st)));
   else

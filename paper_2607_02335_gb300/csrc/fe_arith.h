@@ -188,6 +188,8 @@ struct NT<double> {
   __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ double load_stream(const double* p) { return __ldcs(p); }
   __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
+  __device__ static __forceinline__ double to_sv(double v) { return v; }
+  __device__ static __forceinline__ void store_sv(double* p, double v) { __stcs(p, v); }
   __device__ static __forceinline__ double geo(const double* p) { return __ldcs(p); }
 };
 
@@ -212,6 +214,8 @@ struct NT<float> {
   __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float load_stream(const float* p) { return __ldcs(p); }
   __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
+  __device__ static __forceinline__ float to_sv(float v) { return v; }
+  __device__ static __forceinline__ void store_sv(float* p, float v) { __stcs(p, v); }
   __device__ static __forceinline__ float geo(const float* p) { return __ldcs(p); }
 };
 
@@ -294,6 +298,9 @@ struct NT<dw> {
   __device__ static __forceinline__ dw load(const double* p) { return dw_from_double(__ldg(p)); }
   __device__ static __forceinline__ dw load_stream(const double* p) { return dw_from_double(__ldcs(p)); }
   __device__ static __forceinline__ void store(double* p, dw v) { __stcs(p, dw_to_double_int(v)); }
+  // the stored value (binary64) and its store, for sums formed on stored values
+  __device__ static __forceinline__ double to_sv(dw v) { return dw_to_double_int(v); }
+  __device__ static __forceinline__ void store_sv(double* p, double v) { __stcs(p, v); }
   __device__ static __forceinline__ dw geo(const float2* p) {
     float2 g = __ldcs(p);
     return {g.x, g.y};

@@ -161,6 +161,10 @@ fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st);
 // bx x by cells: all z-interfaces, then the y- and x-interfaces between bricks
 fe_status fe_launch_dss_strided(const fe_mesh* m, int prec, void* v, int bx, int by,
                                 cudaStream_t st);
+// fe_launch_dss_strided whose z-pass also visits only every bz-th z-interface (the boundaries of
+// the z-chunks of a z-carry apply)
+fe_status fe_launch_dss_strided3(const fe_mesh* m, int prec, void* v, int bx, int by, int bz,
+                                 cudaStream_t st);
 // the passes of axes axis_hi down to axis_lo (2 = z, 1 = y, 0 = x) of fe_launch_dss_strided
 fe_status fe_launch_dss_axes(const fe_mesh* m, int prec, void* v, int bx, int by, int axis_hi,
                              int axis_lo, cudaStream_t st);

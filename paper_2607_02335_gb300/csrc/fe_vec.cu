@@ -12,8 +12,8 @@
 // because each pass sees the partial sums of the previous one, edge and vertex copies are
 // assembled as a by-product.
 // ---------------------------------------------------------------------------------------------
-// stride s > 1 (x and y only): just the interfaces whose left cell index is s-1 mod s, the
-// boundaries between bricks of s cells along that axis (nb = (m-1)/s of them per line)
+// stride s > 1: just the interfaces whose left (lower) cell index is s-1 mod s, the boundaries
+// between bricks (x, y) or z-chunks (z) of s cells along that axis (nb = (m-1)/s per line)
 // the node pair of work item e of one axis pass (cells L, R and local nodes locL, locR)
 template <class S>
 __device__ __forceinline__ void dss_pair(S* __restrict__ v, int axis, int n, int mx, int my,
@@ -40,8 +40,9 @@ __device__ __forceinline__ void dss_pair(S* __restrict__ v, int axis, int n, int
     locL = (fb * n + p) * n + fa;
     locR = (fb * n + 0) * n + fa;
   } else {  // faces normal to z
-    L = q;  // q = (czL*my + cy)*mx + cx
-    R = L + (long long)mx * my;
+    const long long mxy = (long long)mx * my, u = q / mxy;
+    L = (u * stride + stride - 1) * mxy + (q - u * mxy);  // q = (u*my + cy)*mx + cx
+    R = L + mxy;
     locL = (p * n + fb) * n + fa;
     locR = (0 * n + fb) * n + fa;
   }
@@ -90,14 +91,14 @@ static unsigned grid_cap(long long n, int threads) {
 
 template <class S>
 static fe_status dss_t(const fe_mesh* m, S* v, int sx, int sy, cudaStream_t st, int axis_hi = 2,
-                       int axis_lo = 0) {
+                       int axis_lo = 0, int sz = 1) {
   // the storage grid: cells, or 2^3-packed units whose sides carry 2p+1 nodes
   const int n = m->sn, n2 = n * n;
   const int mx = m->sgx, my = m->sgy, mz = m->sgz;
-  const int stride[3] = {sx, sy, 1};
+  const int stride[3] = {sx, sy, sz};
   const long long work[3] = {(long long)((mx - 1) / sx) * my * mz * n2,
                              (long long)mx * ((my - 1) / sy) * mz * n2,
-                             (long long)mx * my * (mz - 1) * n2};
+                             (long long)mx * my * ((mz - 1) / sz) * n2};
   for (int axis = axis_hi; axis >= axis_lo; --axis) {  // z, y, x
     if (work[axis] <= 0) continue;
     k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, stride[axis],
@@ -126,6 +127,18 @@ fe_status fe_launch_dss_axes(const fe_mesh* m, int prec, void* v, int bx, int by
   }
   if (prec == FE_F64) return dss_t<double>(m, (double*)v, bx, by, st, axis_hi, axis_lo);
   if (prec == FE_F32) return dss_t<float>(m, (float*)v, bx, by, st, axis_hi, axis_lo);
+  fe_set_error("dss: unsupported precision %d", prec);
+  return FE_ERR_INVALID;
+}
+
+fe_status fe_launch_dss_strided3(const fe_mesh* m, int prec, void* v, int bx, int by, int bz,
+                                 cudaStream_t st) {
+  if (bx < 1 || by < 1 || bz < 1) {
+    fe_set_error("dss: bad brick %d x %d x %d", bx, by, bz);
+    return FE_ERR_INVALID;
+  }
+  if (prec == FE_F64) return dss_t<double>(m, (double*)v, bx, by, st, 2, 0, bz);
+  if (prec == FE_F32) return dss_t<float>(m, (float*)v, bx, by, st, 2, 0, bz);
   fe_set_error("dss: unsupported precision %d", prec);
   return FE_ERR_INVALID;
 }
