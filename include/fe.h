@@ -129,9 +129,11 @@ fe_status fe_gather(const fe_mesh* mesh, const double* x_unique_host, double* x_
  * vector (Sec. 2.1: G the gather, A_D the operator of fe_apply).  x_unique_host and each
  * y_unique_host[k] hold unique_dofs doubles in fe_gather's lexicographic order.  Only these
  * unique-node vectors cross the host link (cell-wise storage, 2.4x larger at Q3, stays on the
- * device): the call copies x in once, expands it to cell-wise form with a kernel, runs fe_apply
- * with FE_ASSEMBLE per operator, and copies one copy of every node back, each read-back
- * overlapping the next operator's apply.  Stream-ordered: it returns once the work is enqueued;
+ * device): the call copies x in once, expands it to cell-wise form with a kernel, runs the
+ * assembled apply per operator, and copies one copy of every node back.  Large meshes are
+ * pipelined in chunks of z-layers (uploads, applies and read-backs of different chunks overlap);
+ * the result is bitwise that of fe_apply with FE_ASSEMBLE.  The environment variable
+ * FE_HOST_CHUNKS sets the chunk count.  Stream-ordered: it returns once the work is enqueued;
  * with page-locked host buffers (cudaHostAlloc) the copies are asynchronous and the buffers must
  * stay untouched until `stream` has passed the call (synchronize it or wait on an event).  The
  * device staging (one unique and two cell-wise vectors, plus one unique vector per output) belongs

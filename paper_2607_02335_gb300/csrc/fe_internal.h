@@ -82,11 +82,12 @@ struct fe_mesh {
   double* red = nullptr;
   int red_len = 0;
   // host-vector applies (fe_host.cu): device staging of the unique-node input, its cell-wise
-  // expansion, the assembled cell-wise output and up to two unique-node outputs; a copy stream for
-  // the read-backs and events ordering it against the caller's stream
+  // expansion, the assembled cell-wise output and up to two unique-node outputs; streams for the
+  // uploads and the read-backs, and events ordering them against the caller's stream
   double *hs_xu = nullptr, *hs_xc = nullptr, *hs_yc = nullptr, *hs_yu[2] = {nullptr, nullptr};
-  cudaStream_t hs_copy = nullptr;
-  cudaEvent_t hs_ev[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t hs_copy = nullptr, hs_up = nullptr;
+  static constexpr int HS_EVENTS = 52;  // start, done, an upload and two read-backs per chunk
+  cudaEvent_t hs_ev[HS_EVENTS] = {};
   // conjugate-gradient workspace (fe_cg.cu), released through cg_free
   void* cg_work = nullptr;
   void (*cg_free)(void*, cudaStream_t) = nullptr;

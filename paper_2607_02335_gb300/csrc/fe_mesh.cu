@@ -391,6 +391,7 @@ static void free_mesh(fe_mesh* m, cudaStream_t st) {
   for (cudaEvent_t e : m->hs_ev)
     if (e) cudaEventDestroy(e);
   if (m->hs_copy) cudaStreamDestroy(m->hs_copy);
+  if (m->hs_up) cudaStreamDestroy(m->hs_up);
   if (m->st) cudaStreamDestroy(m->st);
   delete m;
 }

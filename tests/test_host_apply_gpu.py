@@ -54,6 +54,26 @@ def test_host_apply_matches_oracle_and_device_path(fe, m, p, dirichlet):
     assert np.array_equal(y1, ys[1])
 
 
+@pytest.mark.parametrize("chunks", [2, 3, 7])
+@pytest.mark.parametrize("m,p,dirichlet", [((5, 3, 7), 2, True), ((4, 4, 9), 3, False),
+                                           ((3, 3, 7), 7, True), ((5, 5, 8), 1, False)])
+def test_chunked_host_apply_is_bitwise_the_device_path(fe, monkeypatch, chunks, m, p, dirichlet):
+    """z-chunks forced through FE_HOST_CHUNKS: per chunk the apply, its z-pass and the one across the
+    chunk's lower interface, then the y/x passes of the layers whose z-sums are complete, and the
+    read-back of the node layers that are final (cell offsets of odd length included)."""
+    monkeypatch.setenv("FE_HOST_CHUNKS", str(chunks))
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=dirichlet)
+    xu = S.primal_unique(m, p, seed=6)
+    ys = [np.full(gm.unique_dofs, np.nan), np.full(gm.unique_dofs, np.nan)]
+    fe.fe_apply_host(gm.handle, [fe.FE_LAPLACE, fe.FE_MASS], xu, ys)
+    torch.cuda.synchronize()
+    own = owner_copies(m, p)
+    xc = gm.gather(xu)
+    for op, y in zip((fe.FE_LAPLACE, fe.FE_MASS), ys):
+        dev = gm.apply(xc, op=op, flags=fe.FE_ASSEMBLE).cpu().numpy()
+        assert np.array_equal(y, dev[own])
+
+
 def test_host_apply_pinned_buffers_on_streams(fe):
     """Stream-ordered calls with page-locked buffers, two meshes on two streams, repeated."""
     cases = [((8, 8, 8), 3), ((4, 4, 4), 7)]
