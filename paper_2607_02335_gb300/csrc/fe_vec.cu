@@ -82,6 +82,65 @@ __global__ void k_dss_pass_blocks(S* __restrict__ v, int axis, int n,
   }
 }
 
+// The passes on one structured grid: one CTA per row of interfaces, the row's cell offsets formed
+// once per CTA and the items of the row (interface along the row, face node) in 32-bit arithmetic
+// with compile-time divisors.  Rows and items: x-pass row (cz, cy), items (u, node); y-pass row
+// (cz, u), items (cx, node); z-pass row (u, cy), items (cx, node); u counts the interfaces visited
+// along the axis (nb per line), the left cell of interface u has index u*stride + stride - 1.
+// Each pair gets the sum of dss_pair.
+template <class S, int N>
+__global__ void __launch_bounds__(256) k_dss_row(S* __restrict__ v, int axis, int mx, int my,
+                                                 int stride, int nb) {
+  constexpr int P = N - 1, N2 = N * N, N3 = N2 * N;
+  const long long r = blockIdx.x;
+  long long first;  // left cell of the row's first item
+  int items, lstep;  // items in the row; left-cell step from one item group to the next
+  long long rstep;   // right cell - left cell
+  int locL0, locR0, sa, sb;  // local node of face node (fa, fb): loc0 + fa*sa + fb*sb
+  if (axis == 0) {
+    first = r * mx + stride - 1;
+    items = nb * N2;
+    lstep = stride;
+    rstep = 1;
+    locL0 = P, locR0 = 0, sa = N, sb = N2;
+  } else if (axis == 1) {
+    const long long cz = r / nb, u = r - cz * nb;
+    first = (cz * my + u * stride + stride - 1) * mx;
+    items = mx * N2;
+    lstep = 1;
+    rstep = mx;
+    locL0 = P * N, locR0 = 0, sa = 1, sb = N2;
+  } else {
+    const long long u = r / my, cy = r - u * my;
+    first = ((u * stride + stride - 1) * my + cy) * mx;
+    items = mx * N2;
+    lstep = 1;
+    rstep = (long long)mx * my;
+    locL0 = P * N2, locR0 = 0, sa = 1, sb = N;
+  }
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int g = it / N2, f = it - g * N2, fa = f % N, fb = f / N;
+    const long long L = first + (long long)g * lstep;
+    const int off = fa * sa + fb * sb;
+    S* pl = v + L * N3 + locL0 + off;
+    S* pr = v + (L + rstep) * N3 + locR0 + off;
+    const S s = *pl + *pr;
+    *pl = s;
+    *pr = s;
+  }
+}
+
+template <class S, int N>
+static void launch_dss_rows(S* v, int axis, int mx, int my, int mz, int stride, cudaStream_t st) {
+  const int nb = axis == 0 ? (mx - 1) / stride : axis == 1 ? (my - 1) / stride : (mz - 1) / stride;
+  const long long rows = axis == 0 ? (long long)my * mz : axis == 1 ? (long long)mz * nb
+                                                                    : (long long)nb * my;
+  const int items = (axis == 0 ? nb : mx) * N * N;
+  if (nb <= 0 || rows <= 0) return;
+  const int threads = items >= 256 ? 256 : (items + 31) / 32 * 32;
+  k_dss_row<S, N><<<(unsigned)rows, threads, 0, st>>>(v, axis, mx, my, stride, nb);
+}
+
 static unsigned grid_cap(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152LL * 32) b = 152LL * 32;
@@ -101,8 +160,18 @@ static fe_status dss_t(const fe_mesh* m, S* v, int sx, int sy, cudaStream_t st, 
                              (long long)mx * my * ((mz - 1) / sz) * n2};
   for (int axis = axis_hi; axis >= axis_lo; --axis) {  // z, y, x
     if (work[axis] <= 0) continue;
-    k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, stride[axis],
-                                                             work[axis]);
+    switch (n) {
+      case 2: launch_dss_rows<S, 2>(v, axis, mx, my, mz, stride[axis], st); break;
+      case 3: launch_dss_rows<S, 3>(v, axis, mx, my, mz, stride[axis], st); break;
+      case 4: launch_dss_rows<S, 4>(v, axis, mx, my, mz, stride[axis], st); break;
+      case 5: launch_dss_rows<S, 5>(v, axis, mx, my, mz, stride[axis], st); break;
+      case 6: launch_dss_rows<S, 6>(v, axis, mx, my, mz, stride[axis], st); break;
+      case 7: launch_dss_rows<S, 7>(v, axis, mx, my, mz, stride[axis], st); break;
+      case 8: launch_dss_rows<S, 8>(v, axis, mx, my, mz, stride[axis], st); break;
+      default:
+        k_dss_pass<S><<<grid_cap(work[axis], 256), 256, 0, st>>>(v, axis, n, mx, my, stride[axis],
+                                                                 work[axis]);
+    }
   }
   return fe_cuda_check(cudaGetLastError(), "dss launch");
 }
