@@ -94,7 +94,7 @@ struct Sm<dw> {  // hi and lo interleaved: one 64-bit shared-memory access per v
 // One 1D contraction of a line in even-odd form (the EO comment in fe_internal.h):
 // put(q, value) receives output q.  ROLLED: the output pairs are a run-time loop (outputs must
 // go to shared memory); otherwise everything unrolls and put may write a register array.
-template <int N, class V, int SIG, bool ROLLED, class Put>
+template <int N, class V, int SIG, int ROLLED, class Put>
 __device__ __forceinline__ void eo_line(const EO<N, V>& t, const V (&in)[N], Put put) {
   using T = NT<V>;
   constexpr int H = N / 2, MID = N / 2;
@@ -128,8 +128,9 @@ __device__ __forceinline__ void eo_line(const EO<N, V>& t, const V (&in)[N], Put
     put(q, T::addk(a, b));
     put(N - 1 - q, SIG > 0 ? T::subk(a, b) : T::subk(b, a));
   };
-  if constexpr (ROLLED) {
-#pragma unroll 1
+  if constexpr (ROLLED > 0) {
+    constexpr int kUnroll = ROLLED;  // output pairs per loop iteration
+#pragma unroll(kUnroll)
     for (int q = 0; q < H; ++q) pair(q);
   } else {
 #pragma unroll
@@ -140,7 +141,7 @@ __device__ __forceinline__ void eo_line(const EO<N, V>& t, const V (&in)[N], Put
 // register line -> register line
 template <int N, class V, int SIG>
 __device__ __forceinline__ void eo_regs(const EO<N, V>& t, const V (&in)[N], V (&out)[N]) {
-  eo_line<N, V, SIG, false>(t, in, [&](int q, V v) { out[q] = v; });
+  eo_line<N, V, SIG, 0>(t, in, [&](int q, V v) { out[q] = v; });
 }
 
 // line access in the padded tile: x-line (a=j, b=k), y-line (a=i, b=k), z-line (a=i, b=j)
@@ -159,7 +160,7 @@ __device__ __forceinline__ void tile_sweep(const Sm<V>& s, int cbase, int a, int
 #pragma unroll
   for (int r = 0; r < N; ++r)
     in[r] = s.get(cbase + (AX == 0 ? xl<N>(a, b, r) : yl<N>(a, b, r)));
-  eo_line<N, V, SIG, false>(M, in, [&](int q, V v) {
+  eo_line<N, V, SIG, 0>(M, in, [&](int q, V v) {
     s.put(cbase + (AX == 0 ? xl<N>(a, b, q) : yl<N>(a, b, q)), v);
   });
 }
@@ -313,17 +314,27 @@ __device__ __forceinline__ void brick_sums(const Sm<V>& s, int cb, int cl, int l
 #define FE_ROLL_MINN 5
 #endif
 
-// s[base + q * stride] = (M in)_q
-template <int N, class V, int SIG>
+// s[base + q * stride] = (M in)_q, R output pairs per loop iteration
+template <int N, class V, int SIG, int R>
 __device__ __forceinline__ void sweep_rolled(const EO<N, V>& M, const V (&in)[N], const Sm<V>& s,
                                              int base, int stride) {
-  eo_line<N, V, SIG, true>(M, in, [&](int q, V v) { s.put(base + q * stride, v); });
+  eo_line<N, V, SIG, R>(M, in, [&](int q, V v) { s.put(base + q * stride, v); });
+}
+
+// Output pairs per loop iteration of the run-time contraction loops (measured, double-word, GB300):
+// all of them (the loop unrolled) except the Laplace kernel at n = 6, where the unrolled loops ran
+// 7.5% slower; unrolled, the mass kernels gain 5-16% at n = 5..8 and the Laplace kernels 6% at
+// n = 5 and 7.
+template <int N, int OP>
+__host__ __device__ constexpr int roll_unroll() {
+  return (OP == FE_LAPLACE && N == 6) ? 1 : N / 2;
 }
 
 template <int N, class V, int OP, int GEOM, int MODE>
 __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
                                                    long long cell0, unsigned char* smraw,
                                                    int tile_stride) {
+  constexpr int RU = roll_unroll<N, OP>();
   using T = NT<V>;
   using C = Cfg<N>;
   constexpr int N2 = C::N2, N3 = C::N3, RS = C::RS, PS = C::PS;
@@ -372,24 +383,24 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
 #pragma unroll
     for (int k = 0; k < N; ++k) jpre[k] = active ? T::geo(g6 + k * N2) : T::zero();
   }
-  sweep_rolled<N, V, 1>(tab.eV, in, s0, bz, PS);  // z
+  sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, bz, PS);  // z
   __syncthreads();
   load_line(s0, bx, 1, in);
-  sweep_rolled<N, V, 1>(tab.eV, in, s0, bx, 1);  // x
+  sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, bx, 1);  // x
   __syncthreads();
   load_line(s0, by, RS, in);
-  sweep_rolled<N, V, 1>(tab.eV, in, s0, by, RS);  // y
+  sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, by, RS);  // y
   __syncthreads();
 
   if constexpr (OP == FE_LAPLACE) {
     V inz[N];
     load_line(s0, bz, PS, inz);
     load_line(s0, bx, 1, in);
-    sweep_rolled<N, V, -1>(tab.eD, in, s1, bx, 1);  // d/dx -> s1
+    sweep_rolled<N, V, -1, RU>(tab.eD, in, s1, bx, 1);  // d/dx -> s1
     load_line(s0, by, RS, in);
-    sweep_rolled<N, V, -1>(tab.eD, in, s2, by, RS);  // d/dy -> s2
+    sweep_rolled<N, V, -1, RU>(tab.eD, in, s2, by, RS);  // d/dy -> s2
     __syncthreads();
-    sweep_rolled<N, V, -1>(tab.eD, inz, s0, bz, PS);  // d/dz -> s0 (own z-line)
+    sweep_rolled<N, V, -1, RU>(tab.eD, inz, s0, bz, PS);  // d/dz -> s0 (own z-line)
     // pointwise metric on the own z-line: g = G grad u
     const typename NT<V>::GV* gp = a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + lt;
 #pragma unroll
@@ -424,11 +435,11 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
     __syncthreads();
     // transposed derivatives, each in place on its own array
     load_line(s1, bx, 1, in);
-    sweep_rolled<N, V, -1>(tab.eDT, in, s1, bx, 1);
+    sweep_rolled<N, V, -1, RU>(tab.eDT, in, s1, bx, 1);
     load_line(s2, by, RS, in);
-    sweep_rolled<N, V, -1>(tab.eDT, in, s2, by, RS);
+    sweep_rolled<N, V, -1, RU>(tab.eDT, in, s2, by, RS);
     load_line(s0, bz, PS, in);
-    sweep_rolled<N, V, -1>(tab.eDT, in, s0, bz, PS);
+    sweep_rolled<N, V, -1, RU>(tab.eDT, in, s0, bz, PS);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -454,13 +465,13 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
   }
 
   // transposed interpolation: z from registers, then x and y in place
-  sweep_rolled<N, V, 1>(tab.eVT, in, s0, bz, PS);
+  sweep_rolled<N, V, 1, RU>(tab.eVT, in, s0, bz, PS);
   __syncthreads();
   load_line(s0, bx, 1, in);
-  sweep_rolled<N, V, 1>(tab.eVT, in, s0, bx, 1);
+  sweep_rolled<N, V, 1, RU>(tab.eVT, in, s0, bx, 1);
   __syncthreads();
   load_line(s0, by, RS, in);
-  sweep_rolled<N, V, 1>(tab.eVT, in, s0, by, RS);
+  sweep_rolled<N, V, 1, RU>(tab.eVT, in, s0, by, RS);
   __syncthreads();
   if constexpr (MODE == MODE_BRICK) brick_sums<N, V>(s0, cb, cl, la, lb, a, cell0);
   if (active) {
