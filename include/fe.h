@@ -147,7 +147,10 @@ fe_status fe_apply_host(const fe_mesh* mesh, int nop, const fe_op* ops, const do
  * With FE_ASSEMBLE the structured DSS follows (Sec. 4.1): y = S(A x), continuous.  x and y must
  * not overlap.  x and y are float arrays for every prec but FE_F64.  FE_BF16_F32ACC /
  * FE_F16_F32ACC need FE_GEOM_STORED (else FE_ERR_INVALID); their first call on a mesh builds the
- * 16-bit metric from the FP64 one. */
+ * 16-bit metric from the FP64 one.  Assembled applies at degree <= 3 sum the x/y interfaces
+ * inside bricks of cells in the kernel, and on large meshes also the z-interfaces inside chunks
+ * of z-layers (the environment variable FE_ZCARRY_CHUNK=k forces k layers per chunk, 0 or 1
+ * none); the result is bitwise the same either way. */
 fe_status fe_apply(const fe_mesh* mesh, fe_op op, fe_prec prec, const void* x, void* y,
                    unsigned flags, void* stream);
 

@@ -217,8 +217,9 @@ extern "C" fe_status fe_apply_host(const fe_mesh* cm, int nop, const fe_op* ops,
       make_view(m, z0, z1, &view);
       const long long cell0 = (long long)z0 * m->d.mx * m->d.my * m->n3;
       int brick[2] = {1, 1};
-      ApplyLaunch L{&view, (int)ops[k], m->hs_xc + cell0, m->hs_yc + cell0, st, nullptr, true,
-                    brick};  // the kernels need 8-byte alignment only
+      // one chunk: the mesh itself (recompute-mode meshes keep their coordinates and scratch)
+      ApplyLaunch L{K == 1 ? m : &view, (int)ops[k], m->hs_xc + cell0, m->hs_yc + cell0, st,
+                    nullptr, true, brick};  // the kernels need 8-byte alignment only
       FE_TRY((flags & FE_NATIVE_F64) ? fe_launch_apply_f64native(L) : fe_launch_apply_f64dw(L));
       FE_TRY(fe_launch_dss_axes(&view, FE_F64, m->hs_yc + cell0, brick[0], brick[1], 2, 2, st));
       if (c > 0) {

@@ -31,10 +31,11 @@ def owner_copies(m, p):
     return ((cz * my + cy) * mx + cx) * n ** 3 + (k * n + j) * n + i
 
 
-@pytest.mark.parametrize("m,p,dirichlet", [((5, 4, 3), 1, False), ((4, 3, 5), 3, True),
-                                           ((3, 2, 2), 7, False), ((6, 5, 4), 2, True)])
-def test_host_apply_matches_oracle_and_device_path(fe, m, p, dirichlet):
-    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=dirichlet)
+@pytest.mark.parametrize("m,p,dirichlet,geom", [((5, 4, 3), 1, False, 0), ((4, 3, 5), 3, True, 0),
+                                                ((3, 2, 2), 7, False, 0), ((6, 5, 4), 2, True, 0),
+                                                ((4, 3, 5), 3, True, 1), ((3, 3, 3), 5, False, 1)])
+def test_host_apply_matches_oracle_and_device_path(fe, m, p, dirichlet, geom):
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=dirichlet, geom_mode=geom)
     om = oracle_mesh(m, p, amp=0.1, dirichlet=dirichlet)
     xu = S.primal_unique(m, p, seed=4)
     ys = [np.empty(gm.unique_dofs), np.empty(gm.unique_dofs)]
