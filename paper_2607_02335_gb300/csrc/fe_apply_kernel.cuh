@@ -322,12 +322,12 @@ __device__ __forceinline__ void sweep_rolled(const EO<N, V>& M, const V (&in)[N]
 }
 
 // Output pairs per loop iteration of the run-time contraction loops (measured, double-word, GB300):
-// all of them (the loop unrolled) except the Laplace kernel at n = 6, where the unrolled loops ran
-// 7.5% slower; unrolled, the mass kernels gain 5-16% at n = 5..8 and the Laplace kernels 6% at
-// n = 5 and 7.
+// all of them (the loop unrolled) except the Laplace kernels at n = 6 and 8, where the unrolled
+// loops ran 7.5% slower (n = 6) and no faster (n = 8: equal at 32^3 cells, 10% slower at 16^3);
+// unrolled, the mass kernels gain 5-16% at n = 5..8 and the Laplace kernels 6% at n = 5 and 7.
 template <int N, int OP>
 __host__ __device__ constexpr int roll_unroll() {
-  return (OP == FE_LAPLACE && N == 6) ? 1 : N / 2;
+  return (OP == FE_LAPLACE && (N == 6 || N == 8)) ? 1 : N / 2;
 }
 
 template <int N, class V, int OP, int GEOM, int MODE>
