@@ -60,7 +60,7 @@ typedef enum { FE_LAPLACE = 0, FE_MASS = 1 } fe_op;
  * preconditioner; stored geometry only). */
 typedef enum { FE_F64 = 0, FE_F32 = 1, FE_BF16_F32ACC = 2, FE_F16_F32ACC = 3 } fe_prec;
 
-/* Geometry representation (Sec. 2.3 and Sec. 5.3: "per-quadrature-point Jacobians"):
+/* Geometry representation (Sec. 2.3 and Sec. 6.2: "per-quadrature-point Jacobians"):
  *  STORED    -- w_q detJ J^{-1}J^{-T} (6 symmetric entries, Laplace) and w_q detJ (mass) per
  *               quadrature point, precomputed by fe_mesh_create;
  *  RECOMPUTE -- only the cell-wise nodal coordinates are stored (3 values per cell node, as
@@ -103,14 +103,14 @@ typedef struct {
   long long n_cells;        /* storage units: mx*my*mz cells (layout 0), mx*my*mz/8 units (1) */
   long long nodes_per_cell; /* values per storage unit: (p+1)^3, or (2p+1)^3 packed */
   long long cellwise_len;   /* n_cells * nodes_per_cell: the length of every mesh vector */
-  long long unique_dofs;    /* (mx p + 1)(my p + 1)(mz p + 1), Sec. 5 closed form */
+  long long unique_dofs;    /* (mx p + 1)(my p + 1)(mz p + 1), Sec. 6 closed form */
   int layout_id;            /* FE_LAYOUT_CELLS or FE_LAYOUT_PACKED2 */
 } fe_layout;
 
 typedef struct fe_mesh fe_mesh;
 typedef struct fe_server fe_server;
 
-/* Build a mesh: 1D tables, geometry kernel on `stream` (Sec. 2.3 geometry, Sec. 5.3).  The call
+/* Build a mesh: 1D tables, geometry kernel on `stream` (Sec. 2.3 geometry, Sec. 6.2).  The call
  * returns once the geometry is built (it synchronizes `stream`).  *out is library-owned; free it
  * with fe_mesh_destroy.  FE_ERR_INVALID for degree outside [1,7], non-positive cell counts,
  * geom_mode AFFINE with deform_amp != 0; FE_ERR_OOM if device memory runs out. */

@@ -119,7 +119,7 @@ double or_lagrange_deriv(const double* t, int n, int i, double s) {
 }
 
 /* ------------------------------------------------------------------------------------------
- * Counts (Sec. 5: unique count (n p + 1)^d on structured grids; cell-wise (p+1)^d per cell).
+ * Counts (Sec. 6: unique count (n p + 1)^d on structured grids; cell-wise (p+1)^d per cell).
  * ---------------------------------------------------------------------------------------- */
 long long or_n_cells(const or_mesh* m) { return (long long)m->mx * m->my * m->mz; }
 long long or_n_cellwise(const or_mesh* m) {

@@ -1,6 +1,6 @@
 // fe_mesh.cu -- mesh object, geometry set-up kernel, gather helper, error reporting.
 //
-// Geometry (Sec. 2.3 and Sec. 5.3 "per-quadrature-point Jacobians"): the map
+// Geometry (Sec. 2.3 and Sec. 6.2 "per-quadrature-point Jacobians"): the map
 // Phi(X) = X + amp sin(pi X) sin(pi Y) sin(pi Z) (1,1,1) is sampled at the GLL nodes of every
 // cell and interpolated isoparametrically with Q_p.  For every Gauss point q the kernel forms
 // J_ab = d x_a / d xi_b (xi in [0,1]^3) by sum factorization, then stores

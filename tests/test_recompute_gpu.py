@@ -1,5 +1,5 @@
 """Recomputed geometry (metric formed on the fly from cell-wise nodal coordinates, Sec. 2.3 and
-Sec. 5.3) against the FP64 CPU oracle and against the stored-metric mode of the same mesh.
+Sec. 6.2) against the FP64 CPU oracle and against the stored-metric mode of the same mesh.
 
 The two modes describe the same operator, so they must agree to the FP64 bar (1e-12 relative
 max-norm).  Meshes of the chunked sizes make the apply walk several L2-sized chunks of cells with
