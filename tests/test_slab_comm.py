@@ -148,3 +148,47 @@ def test_invalid_slab_descriptors_rejected_on_host():
     assert fe._lib.fe_slab_dss(None, 0, None, None, None, None) == fe.FE_ERR_INVALID
     assert fe._lib.fe_slab_cg_solve(None, None, None, None, None, None, None) == fe.FE_ERR_INVALID
     assert fe._lib.fe_slab_plane_len(None, None) == fe.FE_ERR_INVALID
+
+
+def test_single_reduction_recurrence_equals_the_two_reduction_pcg():
+    """The slab solver's recurrence (z = P r, s = A z; gamma = <r,z>, delta = <s,z>; beta =
+    gamma/gamma_old, alpha = gamma/(delta - beta gamma/alpha_old); p = z + beta p, q = s + beta q)
+    written out on the oracle's assembled Jacobi-PCG system: its alpha_k and beta_k are the
+    oracle's two-reduction PCG's (equal in exact arithmetic)."""
+    import scipy.sparse as sp
+    m, p = (4, 3, 5), 3
+    om = oracle.Mesh(m, p, amp=0.1, dirichlet=True)
+    rowptr, col, val = oracle.assemble_csr(om, oracle.LAPLACE)
+    A = sp.csr_matrix((val, col, rowptr))
+    free = ~oracle.boundary_global(om)
+    R = sp.diags(free.astype(float))
+    A = R @ A @ R
+    d = np.where(free, oracle.diag_global(om, oracle.LAPLACE), 1.0)
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal(A.shape[0]) * free
+    ref = oracle.cg(om, oracle.LAPLACE, b, rtol=1e-12, maxit=400)
+    x = np.zeros_like(b)
+    r = b.copy()
+    pv = np.zeros_like(b)
+    q = np.zeros_like(b)
+    alphas, betas = [], []
+    z = r * free / d
+    s = A @ z
+    gamma, delta = r @ z, s @ z
+    alpha, beta = gamma / delta, 0.0
+    for k in range(30):
+        pv = z + beta * pv
+        q = s + beta * q
+        x += alpha * pv
+        r -= alpha * q
+        alphas.append(alpha)
+        z = r * free / d
+        s = A @ z
+        g_new, delta = r @ z, s @ z
+        beta = g_new / gamma
+        betas.append(beta)
+        alpha = g_new / (delta - beta * g_new / alpha)
+        gamma = g_new
+    k = 25
+    assert np.allclose(alphas[:k], ref["alpha"][:k], rtol=1e-9, atol=0)
+    assert np.allclose(betas[:k - 1], ref["beta"][:k - 1], rtol=1e-8, atol=0)
