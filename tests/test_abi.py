@@ -62,6 +62,16 @@ def test_invalid_descriptors_rejected_on_host(lib):
     assert fe._lib.fe_pairing(None, 0, None, None, None, None) == fe.FE_ERR_INVALID
     assert fe._lib.fe_cg_solve(None, None, None, None, None, None) == fe.FE_ERR_INVALID
     assert fe._lib.fe_mesh_destroy(None) == fe.FE_OK
+    # host-vector apply: every argument is checked before the device is touched
+    y = (ctypes.c_void_p * 2)()
+    ops = (ctypes.c_int * 2)(0, 1)
+    assert fe._lib.fe_apply_host(None, 1, ops, None, y, 0, None) == fe.FE_ERR_INVALID
+    assert fe.fe_last_error()
+    for name, args in (("fe_mb_create", (None, None, None)), ("fe_amr_create", (None, None, None)),
+                       ("fe_slab_face_pack", (None, 0, None, 0, None, None)),
+                       ("fe_slab_face_add", (None, 0, None, 0, None, None)),
+                       ("fe_slab_apply", (None, 0, 0, None, None, 0, None, None))):
+        assert getattr(fe._lib, name)(*args) == fe.FE_ERR_INVALID, name
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
