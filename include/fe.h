@@ -20,8 +20,10 @@
  *    (cell = (cz*my + cy)*mx + cx), each cell's n^3 values contiguous with local node
  *    (i,j,k) at (k*n + j)*n + i.  Element e of a cell-wise vector is cell e / n^3, node e % n^3.
  *  - Vectors are caller-owned DEVICE memory of `cellwise_len` elements: double for FE_F64,
- *    float for the other precisions.  Pointers must be 16-byte aligned.  Library-owned state
- *    (geometry, tables, solver workspaces) lives inside the opaque fe_mesh / fe_server objects.
+ *    float for the other precisions.  Pointers must be 16-byte aligned.  HOST arrays appear only
+ *    where a declaration says so (fe_gather, fe_apply_host, the server, CG histories).
+ *    Library-owned state (geometry, tables, solver workspaces, staging buffers) lives inside the
+ *    opaque fe_mesh / fe_mbmesh / fe_amr / fe_server objects.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on it
  *    unless stated otherwise.
  *  - Errors: every call returns an fe_status; fe_last_error() gives a thread-local message.
