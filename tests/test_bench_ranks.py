@@ -1,5 +1,6 @@
-"""Host logic of the multi-GPU bench path (replicas, weak scaling) on CPU ranks: two gloo
-processes, the slowest rank's time sets the job time and the rate counts every rank's units."""
+"""Host logic of bench.py on CPU: the multi-GPU path (replicas, weak scaling) on two gloo
+processes, where the slowest rank's time sets the job time and the rate counts every rank's units;
+and the reference arm's JSON line."""
 import importlib.util
 import os
 import socket
@@ -59,3 +60,22 @@ def test_single_rank_needs_no_process_group():
     b = _bench()
     assert b.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert b.job_rate(10, 2, 1, 1.0) == pytest.approx(2e-8)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the CPU oracle and prints one JSON line with the keys the
+    contract names (no GPU involved)."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                       timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    for key in ("metric", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "config", "dtype"):
+        assert key in line, key
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
