@@ -37,6 +37,10 @@ GEO_BYTES = {0: 48, 1: 8}  # stored geometry bytes per cell-wise DoF: Laplace 6 
 FP64_PIPE_TFLOPS = 0.98   # FP64 FMA rate probed on a pool GB300 (0.49 T FMA/s), for context
 
 
+EXTRAS = ("geometry_recompute", "reduced_precision_apply", "block_structured_dss", "packed_storage",
+          "hanging_node_dss", "slab_decomposition", "solve_mixed_vs_fp64", "batched", "serving")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -59,7 +63,12 @@ def parse():
                          "serving")
     ap.add_argument("--profile-case", default=None,
                     help="p,m,op: only run K+W applies of one case (for profiler captures)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.extras != "all":
+        unknown = set(args.extras.split(",")) - set(EXTRAS)
+        if unknown:
+            ap.error(f"unknown extra blocks: {', '.join(sorted(unknown))}")
+    return args
 
 
 def load_peaks():
