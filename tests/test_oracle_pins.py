@@ -369,3 +369,53 @@ def test_cg_matches_direct_solve_and_fcg():
     assert np.allclose(r1["alpha"][:k], r2["alpha"][:k], rtol=1e-8)
     assert np.allclose(r1["beta"][:k], r2["beta"][:k], rtol=1e-6)
     assert np.all(np.diff(r1["relres"][:3]) < 1)
+
+
+# ---------------------------------------------------------------- element-matrix apply, L2 norm
+@pytest.mark.parametrize("p,dirichlet", [(2, True), (3, True), (4, False)])
+def test_apply_local_mats_equals_apply_local(p, dirichlet):
+    """The CPU baseline's apply (precomputed element matrices, a range of cells) is A_K x_K of
+    Sec. 3.1: bitwise the on-the-fly element apply on the same cells, and within rounding of a
+    numpy product with the masks applied by hand (Dirichlet rows and columns zeroed)."""
+    m = (3, 4, 2)
+    mesh = O.Mesh(m, p, amp=0.1, dirichlet=dirichlet)
+    n3 = (p + 1) ** 3
+    xc = S.dual_cellwise(m, p, seed=21)
+    yref = O.apply_local(mesh, O.LAPLACE, xc)
+    cell0, ncell = 5, 11
+    mats = O.element_matrices(mesh, O.LAPLACE, cell0, ncell)
+    sl = slice(cell0 * n3, (cell0 + ncell) * n3)
+    y = O.apply_local_mats(mesh, cell0, mats, xc[sl])
+    assert np.array_equal(y, yref[sl])
+    keep = np.ones(mesh.n_cellwise)
+    if dirichlet:
+        bnd = O.boundary_global(mesh)
+        gidx = O.gather(mesh, np.arange(mesh.n_unique, dtype=np.float64)).astype(np.int64)
+        keep = (~bnd[gidx]).astype(np.float64)
+    kx = (xc * keep)[sl].reshape(ncell, n3)
+    yn = np.einsum("cab,cb->ca", mats, kx).reshape(-1) * keep[sl]
+    assert np.abs(y - yn).max() <= 1e-14 * np.abs(yn).max()
+    if dirichlet:
+        assert np.all(y[keep[sl] == 0] == 0.0)
+
+
+def test_l2_error_closed_forms():
+    """||u_h - u||_{L2(unit cube)} against closed forms: u_h = 0 gives ||u|| = (1/30)^{3/2} for
+    u = prod x(1-x) and (1/8)^{1/2} for the sine; u_h = I u (p >= 2, affine) gives 0; u_h = 2 I u
+    gives ||u|| (a sign slip gives 3 ||u||); u_h = c gives sqrt(c^2 - 2c/216 + 1/27000) on a
+    deformed mesh (det J weighting, exact in physical space up to quadrature)."""
+    quad = (1.0 / 30.0) ** 1.5
+    for p in (2, 3):
+        mesh = O.Mesh(3, p)
+        zero = np.zeros(mesh.n_cellwise)
+        assert abs(O.l2_error(mesh, zero, O.RHS_QUADRATIC) - quad) <= 1e-14
+        uq = O.gather(mesh, O.exact_nodal(mesh, O.RHS_QUADRATIC))
+        assert O.l2_error(mesh, uq, O.RHS_QUADRATIC) <= 1e-14
+        assert abs(O.l2_error(mesh, 2.0 * uq, O.RHS_QUADRATIC) - quad) <= 1e-14
+    mesh = O.Mesh(4, 3)
+    assert abs(O.l2_error(mesh, np.zeros(mesh.n_cellwise), O.RHS_SINE) - math.sqrt(0.125)) <= 1e-9
+    c = 0.3
+    for amp in (0.0, 0.1):
+        mesh = O.Mesh(4, 3, amp=amp)
+        e = O.l2_error(mesh, np.full(mesh.n_cellwise, c), O.RHS_QUADRATIC)
+        assert abs(e - math.sqrt(c * c - 2 * c / 216 + 1 / 27000)) <= 1e-7, amp
