@@ -26,6 +26,8 @@
 // the output loop of each contraction stays a run-time loop (apply_cells_rolled), because the
 // fully unrolled double-word kernel no longer fits the instruction cache.
 #pragma once
+#include <type_traits>
+
 #include "fe_internal.h"
 
 template <int N>
@@ -136,6 +138,128 @@ __device__ __forceinline__ void eo_line(const EO<N, V>& t, const V (&in)[N], Put
 #pragma unroll
     for (int q = 0; q < H; ++q) pair(q);
   }
+}
+
+// Derivative at the n Gauss points of a line from the n-1 differences d_s = x_{s+1} - x_s of its
+// nodal values, in the even-odd form of B' (EOB in fe_arith.h); put(q, value) receives output q.
+template <int N, class V, int ROLLED, class Put>
+__device__ __forceinline__ void eob_line(const EOB<N, V>& t, const V (&d)[N - 1], Put put) {
+  using T = NT<V>;
+  using E = EOB<N, V>;
+  constexpr int NI = E::NI, HI = E::HI, HO = E::HO;
+  V e[E::HA], o[E::HA];
+#pragma unroll
+  for (int s = 0; s < HI; ++s) {
+    e[s] = T::addk(d[s], d[NI - 1 - s]);
+    o[s] = T::subk(d[s], d[NI - 1 - s]);
+  }
+  if constexpr (N & 1) {  // middle output (no middle difference for odd n)
+    V acc = T::prod(t.cr[0], e[0]);
+#pragma unroll
+    for (int s = 1; s < HI; ++s) acc = T::mac(acc, t.cr[s], e[s]);
+    put(N / 2, T::keep(acc));
+  }
+  auto pair = [&](int q) {
+    V a;
+    if constexpr (HI > 0) {
+      a = T::prod(t.A[q][0], e[0]);
+#pragma unroll
+      for (int s = 1; s < HI; ++s) a = T::mac(a, t.A[q][s], e[s]);
+      if constexpr (NI & 1) a = T::mac(a, t.cm[q], d[NI / 2]);
+      V b = T::prod(t.B[q][0], o[0]);
+#pragma unroll
+      for (int s = 1; s < HI; ++s) b = T::mac(b, t.B[q][s], o[s]);
+      put(q, T::addk(a, b));
+      put(N - 1 - q, T::subk(a, b));
+    } else {  // n = 2: one difference, a constant derivative
+      a = T::keep(T::prod(t.cm[q], d[0]));
+      put(q, a);
+      put(N - 1 - q, a);
+    }
+  };
+  if constexpr (ROLLED > 0) {
+    constexpr int kUnroll = ROLLED;
+#pragma unroll(kUnroll)
+    for (int q = 0; q < HO; ++q) pair(q);
+  } else {
+#pragma unroll
+    for (int q = 0; q < HO; ++q) pair(q);
+  }
+}
+
+// Exponent shift of the FP64 path: the CTA's inputs enter the double-word arithmetic scaled by
+// 2^-sh, sh = (binary exponent of the largest finite |x| of the CTA), and every output is scaled
+// back by 2^sh.  Powers of two are exact, so the result is the same operator applied to x; the
+// scaling keeps every intermediate double-word value (and its low part) inside the float range
+// whatever the magnitude of x.  Scaled values below 2^-74 (of the CTA's largest) are flushed to
+// zero.  All threads of the CTA call it; it holds a __syncthreads.
+template <int N>
+__device__ __forceinline__ int cta_exp_shift(const double (&xr)[N]) {
+  __shared__ unsigned s_wmax[32];
+  unsigned em = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    unsigned e = ((unsigned)__double2hiint(xr[k]) >> 20) & 0x7FFu;
+    em = max(em, e == 0x7FFu ? 0u : e);  // infinities and NaNs keep their own value
+  }
+  const unsigned warp = threadIdx.x >> 5;
+  const unsigned lanes = min(32u, blockDim.x - warp * 32u);
+  em = __reduce_max_sync(lanes == 32u ? 0xFFFFFFFFu : ((1u << lanes) - 1u), em);
+  if ((threadIdx.x & 31u) == 0u) s_wmax[warp] = em;
+  __syncthreads();
+  unsigned m = 0;
+  const unsigned nw = (blockDim.x + 31u) >> 5;
+  for (unsigned w = 0; w < nw; ++w) m = max(m, s_wmax[w]);
+  return (int)m - 1023;
+}
+
+// Reference gradient at the Gauss points for the FP64 path, from differences of the binary64
+// inputs: component a is B'_a (the derivative from the differences along axis a) followed by V
+// along the two other axes.  Every value the double-word arithmetic carries is of the size of a
+// difference of neighbouring nodal values, not of x itself, so the rounding of the sweeps does
+// not meet the cancellation of the derivative (a smooth field's Laplacian).  Three phases, each
+// the same contraction on three lines of the thread (an axis loop, not unrolled, which keeps the
+// kernel's code within the instruction cache):
+//   1  B' on the x-, y- and z-line of the inputs (raw tile)  -> s1, s2, s0
+//   2  V  along z of s1 and s2, along x of s0
+//   3  V  along y of s1, along x of s2, along y of s0
+// On return s1, s2, s0 hold d/dx, d/dy, d/dz of u at the Gauss points and sh the exponent shift.
+template <int N, int RU>
+__device__ __forceinline__ void dw_gradient(const double (&xr)[N], const Sm<double>& raw,
+                                            const Sm<dw>& s0, const Sm<dw>& s1, const Sm<dw>& s2,
+                                            int cb, int la, int lb, const Tab1D<N, dw>& tab,
+                                            int& sh) {
+  constexpr int RS = Cfg<N>::RS, PS = Cfg<N>::PS;
+  const int bx = cb + lb * PS + la * RS, by = cb + lb * PS + la, bz = cb + lb * RS + la;
+#pragma unroll
+  for (int k = 0; k < N; ++k) raw.put(bz + k * PS, xr[k]);
+  sh = cta_exp_shift<N>(xr);  // its barrier also publishes the raw tile
+#pragma unroll 1
+  for (int ax = 0; ax < 3; ++ax) {
+    const int base = ax == 0 ? bx : (ax == 1 ? by : bz);
+    const int st = ax == 0 ? 1 : (ax == 1 ? RS : PS);
+    const Sm<dw> o = ax == 0 ? s1 : (ax == 1 ? s2 : s0);
+    double dd[N - 1];
+#pragma unroll
+    for (int r = 0; r < N - 1; ++r) dd[r] = raw.get(base + (r + 1) * st) - raw.get(base + r * st);
+    dw d[N - 1];
+#pragma unroll
+    for (int r = 0; r < N - 1; ++r) d[r] = dw_from_double_ftz(dd[r], sh);
+    eob_line<N, dw, RU>(tab.eB, d, [&](int q, dw v) { o.put(base + q * st, v); });
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int ax = 0; ax < 6; ++ax) {
+    if (ax == 3) __syncthreads();
+    const Sm<dw> o = (ax == 0 || ax == 3) ? s1 : ((ax == 1 || ax == 4) ? s2 : s0);
+    const int base = ax < 2 ? bz : ((ax == 2 || ax == 4) ? bx : by);
+    const int st = ax < 2 ? PS : ((ax == 2 || ax == 4) ? 1 : RS);
+    dw in[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) in[r] = o.get(base + r * st);
+    eo_line<N, dw, 1, RU>(tab.eV, in, [&](int q, dw v) { o.put(base + q * st, v); });
+  }
+  __syncthreads();
 }
 
 // register line -> register line
@@ -330,6 +454,13 @@ __host__ __device__ constexpr int roll_unroll() {
   return (OP == FE_LAPLACE && (N == 6 || N == 8)) ? 1 : N / 2;
 }
 
+// Arrays of the shared-memory tile: Laplace 3 (the FP64 path a fourth for the binary64 inputs),
+// mass 1.
+template <class V>
+__host__ __device__ constexpr int apply_narr(int op) {
+  return op == FE_LAPLACE ? (std::is_same<V, dw>::value ? 4 : 3) : 1;
+}
+
 template <int N, class V, int OP, int GEOM, int MODE>
 __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, const Tab1D<N, V>& tab,
                                                    long long cell0, unsigned char* smraw,
@@ -369,11 +500,23 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
     for (int r = 0; r < N; ++r) v[r] = s.get(base + r * stride);
   };
 
+  // FP64 path: binary64 inputs until they are differenced, CTA exponent shift (as apply_cells)
+  constexpr bool DW = std::is_same<V, dw>::value;
+  int sh = 0;
   V in[N];
+  double xr[DW ? N : 1];
+  if constexpr (DW) {
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    V v = active ? T::load_stream(a.x + gbase + k * N2 + lt) : T::zero();
-    in[k] = masked(k) ? T::zero() : v;
+    for (int k = 0; k < N; ++k) {
+      const double v = active ? __ldcs(a.x + gbase + k * N2 + lt) : 0.0;
+      xr[k] = masked(k) ? 0.0 : v;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      V v = active ? T::load_stream(a.x + gbase + k * N2 + lt) : T::zero();
+      in[k] = masked(k) ? T::zero() : v;
+    }
   }
   constexpr bool PREF_M = (OP == FE_MASS) && (GEOM == GEOM_STORED_K) && (N <= FE_PREFETCH_MASS_MAXN);
   V jpre[PREF_M ? N : 1];
@@ -383,24 +526,35 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
 #pragma unroll
     for (int k = 0; k < N; ++k) jpre[k] = active ? T::geo(g6 + k * N2) : T::zero();
   }
-  sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, bz, PS);  // z
-  __syncthreads();
-  load_line(s0, bx, 1, in);
-  sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, bx, 1);  // x
-  __syncthreads();
-  load_line(s0, by, RS, in);
-  sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, by, RS);  // y
-  __syncthreads();
+  if constexpr (DW && OP == FE_LAPLACE) {
+    dw_gradient<N, RU>(xr, Sm<double>(smraw, 4, 3, tile_stride), s0, s1, s2, cb, la, lb, tab, sh);
+  } else {
+    if constexpr (DW) {
+      sh = cta_exp_shift<N>(xr);
+#pragma unroll
+      for (int k = 0; k < N; ++k) in[k] = dw_from_double_ftz(xr[k], sh);
+    }
+    sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, bz, PS);  // z
+    __syncthreads();
+    load_line(s0, bx, 1, in);
+    sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, bx, 1);  // x
+    __syncthreads();
+    load_line(s0, by, RS, in);
+    sweep_rolled<N, V, 1, RU>(tab.eV, in, s0, by, RS);  // y
+    __syncthreads();
+    if constexpr (OP == FE_LAPLACE) {
+      V inz[N];
+      load_line(s0, bz, PS, inz);
+      load_line(s0, bx, 1, in);
+      sweep_rolled<N, V, -1, RU>(tab.eD, in, s1, bx, 1);  // d/dx -> s1
+      load_line(s0, by, RS, in);
+      sweep_rolled<N, V, -1, RU>(tab.eD, in, s2, by, RS);  // d/dy -> s2
+      __syncthreads();
+      sweep_rolled<N, V, -1, RU>(tab.eD, inz, s0, bz, PS);  // d/dz -> s0 (own z-line)
+    }
+  }
 
   if constexpr (OP == FE_LAPLACE) {
-    V inz[N];
-    load_line(s0, bz, PS, inz);
-    load_line(s0, bx, 1, in);
-    sweep_rolled<N, V, -1, RU>(tab.eD, in, s1, bx, 1);  // d/dx -> s1
-    load_line(s0, by, RS, in);
-    sweep_rolled<N, V, -1, RU>(tab.eD, in, s2, by, RS);  // d/dy -> s2
-    __syncthreads();
-    sweep_rolled<N, V, -1, RU>(tab.eD, inz, s0, bz, PS);  // d/dz -> s0 (own z-line)
     // pointwise metric on the own z-line: g = G grad u
     const typename NT<V>::GV* gp = a.geo + (size_t)(cell - a.geo_cell0) * (FE_GEO_COMPS * N3) + lt;
 #pragma unroll
@@ -480,7 +634,7 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
       V v = s0.get(bz + k * PS);
       if (masked(k)) v = T::zero();
       if constexpr (T::LOWP) v.v *= a.oscale;
-      T::store(a.y + gbase + k * N2 + lt, v);
+      T::store(a.y + gbase + k * N2 + lt, v, sh);
     }
   }
 }
@@ -544,11 +698,24 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
       return gbase + k * N2 + lt;
     }
   };
+  // FP64 path (double-word values): the inputs stay binary64 until they are differenced, and the
+  // CTA's values are scaled by a power of two (cta_exp_shift)
+  constexpr bool DW = std::is_same<V, dw>::value;
+  int sh = 0;
   V u[N], w[N];
+  double xr[DW ? N : 1];
+  if constexpr (DW) {
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    V v = active ? T::load_stream(a.x + xaddr(k)) : T::zero();
-    u[k] = masked(k) ? T::zero() : v;
+    for (int k = 0; k < N; ++k) {
+      const double v = active ? __ldcs(a.x + xaddr(k)) : 0.0;
+      xr[k] = masked(k) ? 0.0 : v;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      V v = active ? T::load_stream(a.x + xaddr(k)) : T::zero();
+      u[k] = masked(k) ? T::zero() : v;
+    }
   }
   // low degrees: issue the metric loads now so that their latency hides behind the sweeps
 #ifndef FE_PREFETCH_MAXN
@@ -572,19 +739,28 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 #pragma unroll
       for (int c = 0; c < 6; ++c) gpre[c * N + k] = active ? T::geo(g0 + c * N3 + k * N2) : T::zero();
   }
-  eo_regs<N, V, 1>(tab.eV, u, w);
+  if constexpr (DW && OP == FE_LAPLACE) {
+    dw_gradient<N, 0>(xr, Sm<double>(smraw, 4, 3, tile_stride), s0, s1, s2, cb, la, lb, tab, sh);
+    // s1, s2, s0: d/dx, d/dy, d/dz of u at the Gauss points
 #pragma unroll
-  for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
-  __syncthreads();
-  tile_sweep<N, V, 0, 1>(s0, cb, la, lb, tab.eV);  // x
-  __syncthreads();
-  tile_sweep<N, V, 1, 1>(s0, cb, la, lb, tab.eV);  // y
-  __syncthreads();
-  // s0 now holds u at the Gauss points
-
-  if constexpr (OP == FE_LAPLACE) {
-    // ---- reference gradient at the Gauss points (collocation derivative)
-    {
+    for (int k = 0; k < N; ++k) u[k] = s0.get(cb + zl<N>(la, lb, k));
+  } else {
+    if constexpr (DW) {
+      sh = cta_exp_shift<N>(xr);
+#pragma unroll
+      for (int k = 0; k < N; ++k) u[k] = dw_from_double_ftz(xr[k], sh);
+    }
+    eo_regs<N, V, 1>(tab.eV, u, w);
+#pragma unroll
+    for (int k = 0; k < N; ++k) s0.put(cb + zl<N>(la, lb, k), w[k]);
+    __syncthreads();
+    tile_sweep<N, V, 0, 1>(s0, cb, la, lb, tab.eV);  // x
+    __syncthreads();
+    tile_sweep<N, V, 1, 1>(s0, cb, la, lb, tab.eV);  // y
+    __syncthreads();
+    // s0 now holds u at the Gauss points
+    if constexpr (OP == FE_LAPLACE) {
+      // ---- reference gradient at the Gauss points (collocation derivative)
       V in[N], out[N];
 #pragma unroll
       for (int r = 0; r < N; ++r) in[r] = s0.get(cb + xl<N>(la, lb, r));
@@ -599,8 +775,11 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 #pragma unroll
       for (int r = 0; r < N; ++r) in[r] = s0.get(cb + zl<N>(la, lb, r));
       eo_regs<N, V, -1>(tab.eD, in, u);  // u := d/dz along the z-line
+      __syncthreads();
     }
-    __syncthreads();
+  }
+
+  if constexpr (OP == FE_LAPLACE) {
     // ---- pointwise metric: g = G grad u (z-line owner)
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -693,7 +872,7 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
     // The x/y sums inside the brick came first, as they do before the pass.
     if (active) {
       using SV = typename NT<V>::SV;
-      SV bottom = T::to_sv(masked(0) ? T::zero() : s0.get(cb + zl<N>(la, lb, 0)));
+      SV bottom = T::to_sv(masked(0) ? T::zero() : s0.get(cb + zl<N>(la, lb, 0)), sh);
       if (zc->pending) {
         bottom = zc->top + bottom;
         T::store_sv(a.y + gbase - (long long)a.mx * a.my * N3 + (N - 1) * N2 + lt, bottom);
@@ -703,9 +882,9 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
       for (int k = 1; k < N - 1; ++k) {
         V v = s0.get(cb + zl<N>(la, lb, k));
         if (masked(k)) v = T::zero();
-        T::store(a.y + gbase + k * N2 + lt, v);
+        T::store(a.y + gbase + k * N2 + lt, v, sh);
       }
-      const SV top = T::to_sv(masked(N - 1) ? T::zero() : s0.get(cb + zl<N>(la, lb, N - 1)));
+      const SV top = T::to_sv(masked(N - 1) ? T::zero() : s0.get(cb + zl<N>(la, lb, N - 1)), sh);
       if (zc->last) {
         T::store_sv(a.y + gbase + (N - 1) * N2 + lt, top);
         zc->pending = false;
@@ -745,7 +924,7 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
         V v = s0.get(cb + zl<N>(la, lb, k));
         if (masked(k)) v = T::zero();
         if constexpr (T::LOWP) v.v *= a.oscale;
-        T::store(yu + (long long)(sz * P + k) * NU * NU, v);
+        T::store(yu + (long long)(sz * P + k) * NU * NU, v, sh);
       }
     }
     return;
@@ -756,15 +935,22 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
       V v = s0.get(cb + zl<N>(la, lb, k));
       if (masked(k)) v = T::zero();
       if constexpr (T::LOWP) v.v *= a.oscale;
-      T::store(a.y + gbase + k * N2 + lt, v);
+      T::store(a.y + gbase + k * N2 + lt, v, sh);
     }
   }
 }
 
+// Resident CTAs per SM the one-layer kernels are compiled for: the double-word kernels are held
+// to the register budget of 3 (Laplace, unrolled degrees: 80 registers), 4 (Laplace, rolled: 64)
+// or 6 (mass: 40) CTAs per SM; the rest are left to the compiler.
+template <int N, class V, int OP>
+__host__ __device__ constexpr int apply_minb() {
+  return std::is_same<V, dw>::value ? (OP == FE_LAPLACE ? (N < FE_ROLL_MINN ? 3 : 4) : 6) : 1;
+}
 #ifdef FE_MINB
 #define FE_APPLY_BOUNDS __launch_bounds__(Cfg<N>::THREADS, FE_MINB)
 #else
-#define FE_APPLY_BOUNDS __launch_bounds__(Cfg<N>::THREADS)
+#define FE_APPLY_BOUNDS __launch_bounds__(Cfg<N>::THREADS, (apply_minb<N, V, OP>()))
 #endif
 // z-carry bricks: held to a register budget for 3 CTAs per SM (Laplace, as the one-layer brick
 // kernel; left to itself the compiler gives the layer loop 98 registers, 2 CTAs per SM) or 6
@@ -815,5 +1001,5 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS,
 
 template <int N, class V>
 inline size_t apply_smem_bytes(int op) {
-  return (size_t)((op == FE_LAPLACE) ? 3 : 1) * Cfg<N>::TILE * Sm<V>::BYTES;
+  return (size_t)apply_narr<V>(op) * Cfg<N>::TILE * Sm<V>::BYTES;
 }

@@ -45,6 +45,29 @@ void fill_eo(EO<N, V>& e, const double (&M0)[FE_MAXN][FE_MAXN], bool tr) {
   if (N & 1) e.mm = fe_cast<V>(M(mid, mid));
 }
 
+// even-odd form of B' (EOB in fe_arith.h) from B = Dh: B'[q][s] = sum_{r > s} Dh[q][r]
+template <int N, class V>
+void fill_eob(EOB<N, V>& e, const HostTab& h) {
+  using E = EOB<N, V>;
+  double Bp[FE_MAXN][FE_MAXN] = {};
+  for (int q = 0; q < N; ++q)
+    for (int s = 0; s < N - 1; ++s) {
+      double acc = 0.0;
+      for (int r = s + 1; r < N; ++r) acc += h.Dh[q][r];
+      Bp[q][s] = acc;
+    }
+  std::memset(&e, 0, sizeof(e));
+  for (int q = 0; q < E::HO; ++q) {
+    for (int s = 0; s < E::HI; ++s) {
+      e.A[q][s] = fe_cast<V>(0.5 * (Bp[q][s] + Bp[q][E::NI - 1 - s]));
+      e.B[q][s] = fe_cast<V>(0.5 * (Bp[q][s] - Bp[q][E::NI - 1 - s]));
+    }
+    if (E::NI & 1) e.cm[q] = fe_cast<V>(Bp[q][E::NI / 2]);
+  }
+  if (N & 1)
+    for (int s = 0; s < E::HI; ++s) e.cr[s] = fe_cast<V>(Bp[N / 2][s]);
+}
+
 template <int N, class V>
 Tab1D<N, V> make_tab(const HostTab& h) {
   Tab1D<N, V> t;
@@ -59,6 +82,7 @@ Tab1D<N, V> make_tab(const HostTab& h) {
   fill_eo<N, V>(t.eVT, h.V, true);
   fill_eo<N, V>(t.eD, h.D, false);
   fill_eo<N, V>(t.eDT, h.D, true);
+  fill_eob<N, V>(t.eB, h);
   return t;
 }
 

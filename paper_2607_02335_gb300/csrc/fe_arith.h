@@ -117,6 +117,51 @@ __device__ __forceinline__ dw dw_from_double(double x) {
   }
   return dw_from_double_slow(x);
 }
+// x * 2^-sh as a double-word: dw_from_double on the scaled exponent (sh from the CTA's largest
+// input, see cta_exp_shift in fe_apply_kernel.cuh).  Zero and subnormal x give 0; values that
+// the scaling leaves outside the exact range take the FP64 path (out of line).
+static __device__ __noinline__ dw dw_from_double_sh_slow(double x, int sh) {
+  const double v = scalbn(x, -sh);
+  const float hi = __double2float_rn(v);
+  return {hi, __double2float_rn(v - (double)hi)};
+}
+__device__ __forceinline__ dw dw_from_double_sh(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned e0 = (unsigned)(b >> 52) & 0x7FFu;
+  const unsigned e = e0 - (unsigned)sh;
+  if (e - 949u <= 201u && e0 - 1u < 2046u) {  // finite, normal, in range after the shift
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+    const unsigned m = (unsigned)b & 0x1FFFFFFFu;
+    const float flo = __fsub_rn(__uint_as_float(0x4B000000u | (m & 0x7FFFFFu)), 8388608.0f);
+    const float fhi = __fsub_rn(__uint_as_float(0x4B000000u | (m >> 23)), 8388608.0f);
+    float lo = __fmul_rn(__fmaf_rn(fhi, 8388608.0f, flo), __uint_as_float((e - 948u) << 23));
+    lo = __uint_as_float(__float_as_uint(lo) | sign);
+    return {hi, lo};
+  }
+  if (e0 == 0u) return {0.0f, 0.0f};
+  return dw_from_double_sh_slow(x, sh);
+}
+
+// x * 2^-sh as a double-word without a branch: exact (as dw_from_double) for
+// 2^-74 <= |x| 2^-sh < 2^128; smaller values, zero and subnormals give 0; infinities and NaN give
+// NaN.  The callers choose sh so that no scaled value reaches 2^128.
+__device__ __forceinline__ dw dw_from_double_ftz(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned e0 = (unsigned)(b >> 52) & 0x7FFu;
+  const unsigned e = e0 - (unsigned)sh;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | (((e - 896u) & 0xFFu) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+  const unsigned m = (unsigned)b & 0x1FFFFFFFu;
+  const float flo = __fsub_rn(__uint_as_float(0x4B000000u | (m & 0x7FFFFFu)), 8388608.0f);
+  const float fhi = __fsub_rn(__uint_as_float(0x4B000000u | (m >> 23)), 8388608.0f);
+  float lo = __fmul_rn(__fmaf_rn(fhi, 8388608.0f, flo), __uint_as_float(((e - 948u) & 0xFFu) << 23));
+  lo = __uint_as_float(__float_as_uint(lo) | sign);
+  const bool in = e - 949u <= 201u && e0 != 0u;
+  const float nan = __uint_as_float(0x7FC00000u);
+  return e0 == 0x7FFu ? dw{nan, nan} : (in ? dw{hi, lo} : dw{0.0f, 0.0f});
+}
+
 // float -> binary64 exactly for normal floats by bit manipulation; zero and subnormal -> 0.
 __device__ __forceinline__ double f2d_bits(float f) {
   unsigned u = __float_as_uint(f);
@@ -161,6 +206,19 @@ __device__ __forceinline__ double dw_to_double_int(dw a) {
   return __longlong_as_double((long long)out);
 }
 
+// (h + l) * 2^sh as binary64: dw_to_double_int, then sh added to the exponent field; results
+// that leave the normal binary64 range take the FP64 path (out of line).
+static __device__ __noinline__ double dw_to_double_sh_slow(double v, int sh) { return scalbn(v, sh); }
+__device__ __forceinline__ double dw_to_double_sh(dw a, int sh) {
+  const double v = dw_to_double_int(a);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+  if (e == 0u || sh == 0) return v;
+  if (e != 0x7FFu && (e + (unsigned)sh) - 1u < 2046u)
+    return __longlong_as_double((long long)(b + ((unsigned long long)(long long)sh << 52)));
+  return dw_to_double_sh_slow(v, sh);
+}
+
 // ---------------------------------------------------------------------------------------------
 // number traits: value type V, storage type of vectors (SV) and of geometry (GV)
 // ---------------------------------------------------------------------------------------------
@@ -187,8 +245,8 @@ struct NT<double> {
   __device__ static __forceinline__ double neg(double a) { return -a; }
   __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ double load_stream(const double* p) { return __ldcs(p); }
-  __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
-  __device__ static __forceinline__ double to_sv(double v) { return v; }
+  __device__ static __forceinline__ void store(double* p, double v, int = 0) { __stcs(p, v); }
+  __device__ static __forceinline__ double to_sv(double v, int = 0) { return v; }
   __device__ static __forceinline__ void store_sv(double* p, double v) { __stcs(p, v); }
   __device__ static __forceinline__ double geo(const double* p) { return __ldcs(p); }
 };
@@ -213,8 +271,8 @@ struct NT<float> {
   __device__ static __forceinline__ float neg(float a) { return -a; }
   __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float load_stream(const float* p) { return __ldcs(p); }
-  __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
-  __device__ static __forceinline__ float to_sv(float v) { return v; }
+  __device__ static __forceinline__ void store(float* p, float v, int = 0) { __stcs(p, v); }
+  __device__ static __forceinline__ float to_sv(float v, int = 0) { return v; }
   __device__ static __forceinline__ void store_sv(float* p, float v) { __stcs(p, v); }
   __device__ static __forceinline__ float geo(const float* p) { return __ldcs(p); }
 };
@@ -257,7 +315,7 @@ struct NT16 {
   __device__ static __forceinline__ W neg(W a) { return {-a.v}; }
   __device__ static __forceinline__ W load(const float* p) { return {rnd(__ldg(p))}; }
   __device__ static __forceinline__ W load_stream(const float* p) { return {rnd(__ldcs(p))}; }
-  __device__ static __forceinline__ void store(float* p, W x) { __stcs(p, x.v); }
+  __device__ static __forceinline__ void store(float* p, W x, int = 0) { __stcs(p, x.v); }
   __device__ static __forceinline__ W geo(const unsigned short* p) {
     const unsigned short b = __ldcs(p);
     if constexpr (W::BF)
@@ -297,9 +355,12 @@ struct NT<dw> {
   __device__ static __forceinline__ dw neg(dw a) { return {-a.h, -a.l}; }
   __device__ static __forceinline__ dw load(const double* p) { return dw_from_double(__ldg(p)); }
   __device__ static __forceinline__ dw load_stream(const double* p) { return dw_from_double(__ldcs(p)); }
-  __device__ static __forceinline__ void store(double* p, dw v) { __stcs(p, dw_to_double_int(v)); }
+  // stores of values computed on inputs scaled by 2^-sh (the CTA's exponent shift)
+  __device__ static __forceinline__ void store(double* p, dw v, int sh = 0) {
+    __stcs(p, dw_to_double_sh(v, sh));
+  }
   // the stored value (binary64) and its store, for sums formed on stored values
-  __device__ static __forceinline__ double to_sv(dw v) { return dw_to_double_int(v); }
+  __device__ static __forceinline__ double to_sv(dw v, int sh = 0) { return dw_to_double_sh(v, sh); }
   __device__ static __forceinline__ void store_sv(double* p, double v) { __stcs(p, v); }
   __device__ static __forceinline__ dw geo(const float2* p) {
     float2 g = __ldcs(p);
@@ -331,10 +392,27 @@ struct EO {
   V mm;       // M[mid][mid] (odd n, sig = +1)
 };
 
+// Even-odd form of the n x (n-1) matrix B' that maps the n-1 differences d_s = x_{s+1} - x_s of a
+// line's nodal values to the derivative at the n Gauss points: B'[q][s] = sum_{r > s} B[q][r],
+// B[q][r] = l_r'(s_q) (B x = B' d because the rows of B sum to zero).  B' is even under the
+// reflection (q, s) -> (n-1-q, n-2-s); with e_s = d_s + d_{n-2-s}, o_s = d_s - d_{n-2-s}
+// (s < (n-1)/2), a = sum_s A[q][s] e_s (+ cm[q] d_mid for even n), b = sum_s B[q][s] o_s:
+// output q is a + b and output n-1-q is a - b; for odd n the middle output is sum_s cr[s] e_s.
+template <int N, class V>
+struct EOB {
+  static constexpr int NI = N - 1, HI = NI / 2, HO = N / 2;
+  static constexpr int HA = HI > 0 ? HI : 1;
+  V A[HO][HA];
+  V B[HO][HA];
+  V cm[HO];  // B'[q][(n-2)/2]   (even n: the middle difference)
+  V cr[HA];  // B'[(n-1)/2][s]   (odd n: the middle output)
+};
+
 template <int N, class V>
 struct Tab1D {
   V V_[N][N];  // V[q][i]  = l_i(s_q): GLL-node Lagrange basis at Gauss point q      (Sec. 2.3 "V")
   V D_[N][N];  // D[q][r]  = derivative of the Gauss-point Lagrange basis r at s_q (collocation)
   V W_[N];     // Gauss weights on [0,1]
   EO<N, V> eV, eVT, eD, eDT;  // even-odd forms of V, V^T, D, D^T
+  EOB<N, V> eB;               // even-odd form of B' (derivative from nodal differences)
 };

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(BT)
 
 template <int N, class V>
 constexpr size_t tile_bytes() {
-  return (size_t)3 * (Cfg<N>::TILE + Cfg<N>::CS) * Sm<V>::BYTES;
+  return (size_t)apply_narr<V>(FE_LAPLACE) * (Cfg<N>::TILE + Cfg<N>::CS) * Sm<V>::BYTES;
 }
 template <class V>
 size_t max_tile_bytes() {
