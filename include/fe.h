@@ -202,22 +202,28 @@ fe_status fe_l2_error(const fe_mesh* mesh, int kind, const double* u, double* er
  * Jacobi preconditioner P = D_cell^{-1} S.  Convergence (unspecified in the paper; reading):
  * ||G^T r||_2 / ||G^T b||_2 <= rtol over free nodes, evaluated on the device as
  * sum_e (S r)_e^2 / mult_e.  mixed = 0: FP64 throughout; flexible = 1 uses the FCG beta.
- * mixed = FE_F32, flexible = 0: FP64 iterative refinement (r = b - A x in FP64, x += d in FP64)
- * around an FP32 inner PCG solved to inner_rtol.  mixed = FE_F32, flexible = 1: FP64 FCG whose
- * (variable) preconditioner is the FP32 inner PCG solve, the reduced-precision preconditioner
- * that motivates FCG in Sec. 3.2.  mixed = FE_BF16_F32ACC or FE_F16_F32ACC: the same schemes with
- * the inner operator in 16-bit operands and FP32 accumulation (stored geometry only; inner
- * vectors stay FP32).  The FP32 inner solve receives the residual assembled in FP64
- * and split evenly over the copies of each node.  b (dual) and x (primal, in/out) are device
- * arrays of cellwise_len doubles.  Synchronous: returns after the solve. */
+ * mixed = FE_F32, flexible = 0: FP32 PCG (FP32 vectors and operator, pairings accumulated in
+ * double-word arithmetic) with FP64 reliable updates: whenever the recursive residual has dropped
+ * by inner_rtol since the last update, the FP32 correction is added to the FP64 solution x, the
+ * true residual b - A x is formed with the FP64 operator and replaces the recursive one, and the
+ * search direction is kept (iterative refinement that keeps the Krylov space).
+ * mixed = FE_F32, flexible = 1: FP64 FCG whose (variable) preconditioner is an FP32 PCG solve to
+ * inner_rtol, the reduced-precision preconditioner that motivates FCG in Sec. 3.2.
+ * mixed = FE_BF16_F32ACC or FE_F16_F32ACC: the FCG scheme (whatever `flexible` says) with the
+ * inner operator in 16-bit operands and FP32 accumulation (stored geometry only; inner vectors
+ * stay FP32).  The FP32 iteration receives the residual assembled in FP64 and split evenly over
+ * the copies of each node.  The FP64 residual of the returned x decides convergence.  b (dual)
+ * and x (primal, in/out) are device arrays of cellwise_len doubles.  Synchronous: returns after
+ * the solve. */
 typedef struct {
   double rtol;       /* relative residual target */
   int maxit;         /* iteration cap (inner iterations in total for mixed) */
   int mixed;         /* 0 = FP64; FE_F32, FE_BF16_F32ACC, FE_F16_F32ACC = inner solve in that
                         arithmetic under FP64 refinement */
   int flexible;      /* 1 = FCG beta */
-  double inner_rtol; /* mixed only: relative reduction per inner solve (<= 0: 1e-2); an inner
-                        solve also stops after 20 iterations without a 10% residual drop */
+  double inner_rtol; /* mixed only: residual reduction between two reliable updates (<= 0: 0.1),
+                        or per inner FCG solve (<= 0: 1e-2; an inner FCG solve also stops after
+                        20 iterations without a 10% residual drop) */
   double* history;   /* nullable HOST array of 3*maxit doubles; FP64 solves write, for iteration
                         k, alpha_k, beta_k and the relative residual after the update */
 } fe_cg_opts;
@@ -231,8 +237,8 @@ fe_status fe_cg_solve(const fe_mesh* mesh, const double* b, double* x, const fe_
                       fe_cg_result* res, void* stream);
 
 /* Batched solve of nprob independent problems (each its own mesh, degree and right-hand side)
- * with the options of fe_cg_solve (mixed = 0: FP64 PCG; mixed = FE_F32: FP64 FCG preconditioned by
- * an FP32 PCG solve, whatever `flexible` says).  Every CG iteration applies the operators of all
+ * with the options of fe_cg_solve (mixed = 0: FP64 PCG; mixed = FE_F32: FP32 PCG with FP64 reliable
+ * updates, whatever `flexible` says).  Every CG iteration applies the operators of all
  * unconverged problems in one persistent launch over (problem, cell-tile) work items; vector
  * kernels run over (problem, chunk) items and every problem's scalars are reduced in a fixed
  * order, so each result is bitwise the same alone and in any mix.  meshes must be distinct and on
@@ -255,7 +261,7 @@ fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes, const dou
  *  fe_serve_submit: desc describes the mesh (geom_mode STORED or AFFINE, device = the server's);
  *    b_host is a HOST cell-wise dual right-hand side of the mesh's cellwise_len doubles, copied at
  *    submission, or NULL for the manufactured sine load (FE_RHS_SINE); opts as in fe_cg_solve
- *    (mixed = FE_F32 runs FP64 FCG preconditioned by an FP32 PCG solve).  *ticket identifies the
+ *    (mixed = FE_F32 runs FP32 PCG with FP64 reliable updates).  *ticket identifies the
  *    request.  FE_ERR_OOM if the request alone exceeds the budget.
  *  fe_serve_poll: FE_ERR_BUSY while pending; FE_OK fills *res and, if x_host is not NULL, copies
  *    the solution (cellwise_len doubles) and forgets the ticket.  Non-blocking.

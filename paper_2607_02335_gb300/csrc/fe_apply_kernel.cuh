@@ -213,51 +213,62 @@ __device__ __forceinline__ int cta_exp_shift(const double (&xr)[N]) {
   return (int)m - 1023;
 }
 
-// Reference gradient at the Gauss points for the FP64 path, from differences of the binary64
-// inputs: component a is B'_a (the derivative from the differences along axis a) followed by V
-// along the two other axes.  Every value the double-word arithmetic carries is of the size of a
-// difference of neighbouring nodal values, not of x itself, so the rounding of the sweeps does
-// not meet the cancellation of the derivative (a smooth field's Laplacian).  Three phases, each
-// the same contraction on three lines of the thread (an axis loop, not unrolled, which keeps the
-// kernel's code within the instruction cache):
+// Reference gradient at the Gauss points from differences of the stored inputs (the FP64 path:
+// binary64 inputs into double-word differences; the FP32 path: float differences): component a is
+// B'_a (the derivative from the differences along axis a) followed by V along the two other axes.
+// Every value the sweeps carry is of the size of a difference of neighbouring nodal values, not of
+// x itself, so the rounding of the sweeps does not meet the cancellation of the derivative (a
+// smooth field's Laplacian).  Three phases, each the same contraction on three lines of the thread
+// (an axis loop, not unrolled, which keeps the kernel's code within the instruction cache):
 //   1  B' on the x-, y- and z-line of the inputs (raw tile)  -> s1, s2, s0
 //   2  V  along z of s1 and s2, along x of s0
 //   3  V  along y of s1, along x of s2, along y of s0
-// On return s1, s2, s0 hold d/dx, d/dy, d/dz of u at the Gauss points and sh the exponent shift.
-template <int N, int RU>
-__device__ __forceinline__ void dw_gradient(const double (&xr)[N], const Sm<double>& raw,
-                                            const Sm<dw>& s0, const Sm<dw>& s1, const Sm<dw>& s2,
-                                            int cb, int la, int lb, const Tab1D<N, dw>& tab,
-                                            int& sh) {
+// On return s1, s2, s0 hold d/dx, d/dy, d/dz of u at the Gauss points and sh the exponent shift
+// (FP64 path; 0 otherwise).
+template <int N, class V, int RU>
+__device__ __forceinline__ void diff_gradient(const typename NT<V>::SV (&xr)[N],
+                                              const Sm<typename NT<V>::SV>& raw, const Sm<V>& s0,
+                                              const Sm<V>& s1, const Sm<V>& s2, int cb, int la,
+                                              int lb, const Tab1D<N, V>& tab, int& sh) {
+  constexpr bool DW = std::is_same<V, dw>::value;
+  using SV = typename NT<V>::SV;
   constexpr int RS = Cfg<N>::RS, PS = Cfg<N>::PS;
   const int bx = cb + lb * PS + la * RS, by = cb + lb * PS + la, bz = cb + lb * RS + la;
 #pragma unroll
   for (int k = 0; k < N; ++k) raw.put(bz + k * PS, xr[k]);
-  sh = cta_exp_shift<N>(xr);  // its barrier also publishes the raw tile
+  if constexpr (DW)
+    sh = cta_exp_shift<N>(xr);  // its barrier also publishes the raw tile
+  else
+    __syncthreads();
 #pragma unroll 1
   for (int ax = 0; ax < 3; ++ax) {
     const int base = ax == 0 ? bx : (ax == 1 ? by : bz);
     const int st = ax == 0 ? 1 : (ax == 1 ? RS : PS);
-    const Sm<dw> o = ax == 0 ? s1 : (ax == 1 ? s2 : s0);
-    double dd[N - 1];
+    const Sm<V> o = ax == 0 ? s1 : (ax == 1 ? s2 : s0);
+    SV dd[N - 1];
 #pragma unroll
     for (int r = 0; r < N - 1; ++r) dd[r] = raw.get(base + (r + 1) * st) - raw.get(base + r * st);
-    dw d[N - 1];
+    V d[N - 1];
 #pragma unroll
-    for (int r = 0; r < N - 1; ++r) d[r] = dw_from_double_ftz(dd[r], sh);
-    eob_line<N, dw, RU>(tab.eB, d, [&](int q, dw v) { o.put(base + q * st, v); });
+    for (int r = 0; r < N - 1; ++r) {
+      if constexpr (DW)
+        d[r] = dw_from_double_ftz(dd[r], sh);
+      else
+        d[r] = dd[r];
+    }
+    eob_line<N, V, RU>(tab.eB, d, [&](int q, V v) { o.put(base + q * st, v); });
   }
   __syncthreads();
 #pragma unroll 1
   for (int ax = 0; ax < 6; ++ax) {
     if (ax == 3) __syncthreads();
-    const Sm<dw> o = (ax == 0 || ax == 3) ? s1 : ((ax == 1 || ax == 4) ? s2 : s0);
+    const Sm<V> o = (ax == 0 || ax == 3) ? s1 : ((ax == 1 || ax == 4) ? s2 : s0);
     const int base = ax < 2 ? bz : ((ax == 2 || ax == 4) ? bx : by);
     const int st = ax < 2 ? PS : ((ax == 2 || ax == 4) ? 1 : RS);
-    dw in[N];
+    V in[N];
 #pragma unroll
     for (int r = 0; r < N; ++r) in[r] = o.get(base + r * st);
-    eo_line<N, dw, 1, RU>(tab.eV, in, [&](int q, dw v) { o.put(base + q * st, v); });
+    eo_line<N, V, 1, RU>(tab.eV, in, [&](int q, V v) { o.put(base + q * st, v); });
   }
   __syncthreads();
 }
@@ -454,11 +465,12 @@ __host__ __device__ constexpr int roll_unroll() {
   return (OP == FE_LAPLACE && (N == 6 || N == 8)) ? 1 : N / 2;
 }
 
-// Arrays of the shared-memory tile: Laplace 3 (the FP64 path a fourth for the binary64 inputs),
-// mass 1.
+// Arrays of the shared-memory tile: Laplace 3 (the FP64 and FP32 paths a fourth for the inputs
+// that are differenced), mass 1.
 template <class V>
 __host__ __device__ constexpr int apply_narr(int op) {
-  return op == FE_LAPLACE ? (std::is_same<V, dw>::value ? 4 : 3) : 1;
+  return op == FE_LAPLACE ? ((std::is_same<V, dw>::value || std::is_same<V, float>::value) ? 4 : 3)
+                          : 1;
 }
 
 template <int N, class V, int OP, int GEOM, int MODE>
@@ -502,14 +514,17 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
 
   // FP64 path: binary64 inputs until they are differenced, CTA exponent shift (as apply_cells)
   constexpr bool DW = std::is_same<V, dw>::value;
+  // Laplace gradient from differences of the stored inputs (FP64 and FP32 paths)
+  constexpr bool DIFF = (DW || std::is_same<V, float>::value) && OP == FE_LAPLACE;
+  using SV = typename NT<V>::SV;
   int sh = 0;
   V in[N];
-  double xr[DW ? N : 1];
-  if constexpr (DW) {
+  SV xr[(DW || DIFF) ? N : 1];
+  if constexpr (DW || DIFF) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      const double v = active ? __ldcs(a.x + gbase + k * N2 + lt) : 0.0;
-      xr[k] = masked(k) ? 0.0 : v;
+      const SV v = active ? __ldcs(a.x + gbase + k * N2 + lt) : SV(0);
+      xr[k] = masked(k) ? SV(0) : v;
     }
   } else {
 #pragma unroll
@@ -526,8 +541,8 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
 #pragma unroll
     for (int k = 0; k < N; ++k) jpre[k] = active ? T::geo(g6 + k * N2) : T::zero();
   }
-  if constexpr (DW && OP == FE_LAPLACE) {
-    dw_gradient<N, RU>(xr, Sm<double>(smraw, 4, 3, tile_stride), s0, s1, s2, cb, la, lb, tab, sh);
+  if constexpr (DIFF) {
+    diff_gradient<N, V, RU>(xr, Sm<SV>(smraw, 4, 3, tile_stride), s0, s1, s2, cb, la, lb, tab, sh);
   } else {
     if constexpr (DW) {
       sh = cta_exp_shift<N>(xr);
@@ -701,14 +716,17 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   // FP64 path (double-word values): the inputs stay binary64 until they are differenced, and the
   // CTA's values are scaled by a power of two (cta_exp_shift)
   constexpr bool DW = std::is_same<V, dw>::value;
+  // Laplace gradient from differences of the stored inputs (FP64 and FP32 paths)
+  constexpr bool DIFF = (DW || std::is_same<V, float>::value) && OP == FE_LAPLACE;
+  using SV = typename NT<V>::SV;
   int sh = 0;
   V u[N], w[N];
-  double xr[DW ? N : 1];
-  if constexpr (DW) {
+  SV xr[(DW || DIFF) ? N : 1];
+  if constexpr (DW || DIFF) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      const double v = active ? __ldcs(a.x + xaddr(k)) : 0.0;
-      xr[k] = masked(k) ? 0.0 : v;
+      const SV v = active ? __ldcs(a.x + xaddr(k)) : SV(0);
+      xr[k] = masked(k) ? SV(0) : v;
     }
   } else {
 #pragma unroll
@@ -739,8 +757,8 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 #pragma unroll
       for (int c = 0; c < 6; ++c) gpre[c * N + k] = active ? T::geo(g0 + c * N3 + k * N2) : T::zero();
   }
-  if constexpr (DW && OP == FE_LAPLACE) {
-    dw_gradient<N, 0>(xr, Sm<double>(smraw, 4, 3, tile_stride), s0, s1, s2, cb, la, lb, tab, sh);
+  if constexpr (DIFF) {
+    diff_gradient<N, V, 0>(xr, Sm<SV>(smraw, 4, 3, tile_stride), s0, s1, s2, cb, la, lb, tab, sh);
     // s1, s2, s0: d/dx, d/dy, d/dz of u at the Gauss points
 #pragma unroll
     for (int k = 0; k < N; ++k) u[k] = s0.get(cb + zl<N>(la, lb, k));

@@ -10,9 +10,11 @@
 // problems share the launch: its result is bitwise the same alone and in a mix.
 //
 // Precisions: FP64 Jacobi-PCG (double-word apply), or the mixed scheme of fe_cg_solve with
-// mixed = FE_F32, flexible = 1: FP64 FCG whose preconditioner is an FP32 Jacobi-PCG solve.  The
-// phases (outer FP64 step, inner FP32 iterations) are global: a problem whose inner solve ends
-// early waits for the others, which changes nothing in its own sequence of operations.
+// mixed = FE_F32: FP32 Jacobi-PCG with FP64 reliable updates (every run of FP32 iterations ends
+// with the FP32 correction added to the FP64 solution, the true residual b - A x formed in FP64
+// and put in place of the recursive one, and the search direction kept).  The phases (FP64
+// replacement, FP32 iterations) are global: a problem whose FP32 run ends early waits for the
+// others, which changes nothing in its own sequence of operations.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -406,29 +408,34 @@ __global__ void __launch_bounds__(BT)
   }
 }
 
-// z64 = d32 / s ; partials slot 1 <r64, z64>, slot 2 <q64, z64> (with_q)
+// reliable update: x64 += d32 / s (s = 1/||G^T r|| of the run's residual)
 __global__ void __launch_bounds__(BT)
-    kb_from_inner(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks,
-                  int with_q, double* __restrict__ partials) {
-  __shared__ dw sh[32];
+    kb_correct(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks) {
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const Chunk C = chunks[c];
     const BProb& P = probs[C.prob];
     if (*(volatile const int*)&P.sc[0].done) continue;
     const double inv_s = sqrt(P.sc[0].rnorm2);
-    dw a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
-    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
-      const double ze = inv_s * (double)P.d32[e];
-      P.z64[e] = ze;
-      a1 = dw_add(a1, prod2<double>(P.r64[e], ze));
-      if (with_q) a2 = dw_add(a2, prod2<double>(P.q64[e], ze));
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) P.x64[e] += inv_s * (double)P.d32[e];
+  }
+}
+
+// start of a run: p32 = z32 (a problem's first run) or p32 = z32 + c p32, the direction of the
+// previous run kept in the new scale: c = beta (s/s_old) with beta = <r', z'> / (rz_old
+// (s/s_old)^2), rz_old = <r_{k-1}, z_{k-1}> in the old scale (sc[0].rz_new), s_old in sc[0].qz
+__global__ void __launch_bounds__(BT)
+    kb_keep_direction(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Chunk C = chunks[c];
+    const BProb& P = probs[C.prob];
+    if (*(volatile const int*)&P.sc[0].done) continue;
+    if (P.sc[0].pad) {  // first run: p = z (the buffer's old contents are not read)
+      for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) P.p32[e] = P.z32[e];
+      continue;
     }
-    a1 = block_reduce_dw(a1, sh);
-    if (threadIdx.x == 0) partials[(size_t)c * 4 + 1] = dw_to_double(a1);
-    if (with_q) {
-      a2 = block_reduce_dw(a2, sh);
-      if (threadIdx.x == 0) partials[(size_t)c * 4 + 2] = dw_to_double(a2);
-    }
+    const double ratio = (1.0 / sqrt(P.sc[0].rnorm2)) / P.sc[0].qz;
+    const float cf = (float)(P.sc[1].rz / (P.sc[0].rz_new * ratio));
+    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) P.p32[e] = fmaf(cf, P.p32[e], P.z32[e]);
   }
 }
 
@@ -467,45 +474,12 @@ __global__ void __launch_bounds__(BT)
   CgScal* sc = &P.sc[slot];
   if (*(volatile int*)&sc->done) return;
   const int flexible = slot == 0 ? P.flexible : 0;
-  const double rtol = slot == 0 ? P.rtol : P.irtol;
+  const double rtol = slot == 0 ? P.rtol : sc->rtol;
   const double rn2 = sum_chunks(partials, P.chunk0, P.chunk1, 0, sh);
   const double rz = (mode == FIN_INIT_R || mode == FIN_ITER) ? sum_chunks(partials, P.chunk0, P.chunk1, 1, sh) : 0.0;
   const double qz = (mode == FIN_ITER && flexible) ? sum_chunks(partials, P.chunk0, P.chunk1, 2, sh) : 0.0;
   if (threadIdx.x != 0) return;
   fin_scalars(sc, rn2, rz, qz, rtol, mode, flexible);
-}
-
-// outer FCG scalars: a problem's first preconditioned residual (sc[0].pad set) only records
-// rz = <r,z>; later ones give beta = -<q,z>/<q,p> and rz
-__global__ void __launch_bounds__(BT)
-    kb_fin_fcg(BProb* __restrict__ probs, const double* __restrict__ partials) {
-  __shared__ dw sh[32];
-  BProb& P = probs[blockIdx.x];
-  CgScal* sc = &P.sc[0];
-  if (*(volatile int*)&sc->done) return;
-  const int init = sc->pad;
-  const double rz = sum_chunks(partials, P.chunk0, P.chunk1, 1, sh);
-  const double qz = init ? 0.0 : sum_chunks(partials, P.chunk0, P.chunk1, 2, sh);
-  if (threadIdx.x != 0) return;
-  if (!init) sc->beta = -qz / sc->qp;
-  sc->rz = rz;
-}
-
-// p = z (first direction of a problem) or p = z + beta p
-__global__ void __launch_bounds__(BT)
-    kb_update_p_fcg(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks) {
-  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    const Chunk C = chunks[c];
-    const BProb& P = probs[C.prob];
-    if (*(volatile const int*)&P.sc[0].done) continue;
-    const double b = P.sc[0].pad ? 0.0 : P.sc[0].beta;
-    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) P.p64[e] = P.z64[e] + b * P.p64[e];
-  }
-}
-
-__global__ void kb_clear_first(BProb* __restrict__ probs, int nprob) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nprob) probs[i].sc[0].pad = 0;
 }
 
 // reset the inner scalars for a new inner solve (done mirrors the outer state)
@@ -523,10 +497,22 @@ __global__ void kb_reset_inner(BProb* __restrict__ probs, int nprob) {
   CgScal s;
   memset(&s, 0, sizeof(s));
   s.maxit = maxit - spent > 0 ? maxit - spent : 1;
-  s.stall_limit = 20;
   s.stall_total = spent;
   s.done = o->done;
+  // run the FP32 iterations down to delta, or to just below the outer target
+  s.rtol = fmax(probs[i].irtol, 0.5 * probs[i].rtol / o->relres);
   *in = s;
+}
+
+// end of a run: keep <r_{k-1}, z_{k-1}> (the run stopped before its last beta) and the scale
+__global__ void kb_save_run(BProb* __restrict__ probs, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  CgScal* o = &probs[i].sc[0];
+  if (o->done) return;
+  o->rz_new = probs[i].sc[1].rz;
+  o->qz = 1.0 / sqrt(o->rnorm2);
+  o->pad = 0;
 }
 
 // accumulate the finished inner iteration count
@@ -725,38 +711,36 @@ fe_status fe_batch_read(FeBatch* B) {
   return fe_cuda_check(cudaStreamSynchronize(B->st), "batch synchronize");
 }
 
+// start of an FP32 run for every unconverged problem: r32 = s (S r)/mult, z32 = P r32, <r32, z32>,
+// and the direction (first run: p = z; later: the previous direction kept, kb_keep_direction)
 fe_status fe_batch_inner_start(FeBatch* B) {
-  const int np = (int)B->hp.size();
-  kb_reset_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
-  kb_to_inner<<<grid_chunks(B->nvch), BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch);
-  FE_TRY(fe_batch_norm<float>(B, 1, 1, FIN_INIT_B, 0));
-  return fe_batch_norm<float>(B, 1, 1, FIN_INIT_R, 1);
-}
-
-fe_status fe_batch_inner_finish(FeBatch* B) {
-  const int np = (int)B->hp.size();
-  const unsigned g = grid_chunks(B->nvch);
-  kb_count_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
-  kb_from_inner<<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch, 1, B->d_partials);
-  kb_fin_fcg<<<np, BT, 0, B->st>>>(B->d_probs, B->d_partials);
-  kb_update_p_fcg<<<g, BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_vch, B->nvch);
-  kb_clear_first<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
-  return fe_cuda_check(cudaGetLastError(), "batch inner finish");
-}
-
-// outer FCG step A: q = A p, alpha, x += alpha p, r -= alpha q, ||G^T r||, convergence
-fe_status fe_batch_outer_step(FeBatch* B) {
   const int np = (int)B->hp.size();
   const unsigned g = grid_chunks(B->nvch);
   const Chunk* ch = (const Chunk*)B->d_vch;
-  FE_TRY(launch_apply_batched<double>(B, 0));
-  kb_qp<double><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 0, B->d_partials);
-  kb_fin_alpha<<<np, BT, 0, B->st>>>(B->d_probs, 0, B->d_partials);
-  kb_update_ur<double><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 0);
-  FE_TRY(launch_dss_batched<double>(B, 0));
-  kb_precond<double><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 0, 0, B->d_partials);
+  kb_reset_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
+  kb_to_inner<<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch);
+  FE_TRY(fe_batch_norm<float>(B, 1, 1, FIN_INIT_B, 0));
+  kb_copy<float><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 1, 5, 1);
+  FE_TRY(launch_dss_batched<float>(B, 1));
+  kb_precond<float><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, 1, 1 | 2, B->d_partials);
+  kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, 1, FIN_INIT_R, B->d_partials);
+  kb_keep_direction<<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch);
+  return fe_cuda_check(cudaGetLastError(), "batch run start");
+}
+
+// end of an FP32 run (the reliable update): x += d / s, r = b - A x in FP64, ||G^T r||, convergence
+fe_status fe_batch_inner_finish(FeBatch* B) {
+  const int np = (int)B->hp.size();
+  const unsigned g = grid_chunks(B->nvch);
+  const Chunk* ch = (const Chunk*)B->d_vch;
+  kb_count_inner<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
+  kb_save_run<<<(np + 127) / 128, 128, 0, B->st>>>(B->d_probs, np);
+  kb_correct<<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch);
+  FE_TRY(launch_apply_batched<double>(B, 0, 1));  // q = A x
+  kb_residual<<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch);
+  FE_TRY(fe_batch_norm<double>(B, 0, 1, FIN_NORM, 0));
   kb_fin_beta<<<np, BT, 0, B->st>>>(B->d_probs, 0, FIN_OUTER, B->d_partials);
-  return fe_cuda_check(cudaGetLastError(), "batch outer step");
+  return fe_cuda_check(cudaGetLastError(), "batch reliable update");
 }
 
 fe_status fe_batch_prepare() {
@@ -784,7 +768,7 @@ fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const do
   BProb& P = B->hp[i];
   std::memset(&P, 0, sizeof(P));
   P.rtol = opts->rtol;
-  P.irtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 1e-2;
+  P.irtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 0.1;
   P.maxit = opts->maxit;
   P.flexible = (opts->mixed == 0 && opts->flexible) ? 1 : 0;
   P.n = m->n;
@@ -860,7 +844,7 @@ fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts) {
     }
     return FE_OK;
   }
-  // mixed: FP64 FCG, preconditioner = FP32 PCG solve
+  // mixed: FP32 PCG runs between FP64 reliable updates
   for (;;) {
     FE_TRY(fe_batch_read(B));
     if (fe_batch_all_done(B, 0)) break;
@@ -871,7 +855,6 @@ fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts) {
       FE_TRY(fe_batch_read(B));
     }
     FE_TRY(fe_batch_inner_finish(B));
-    FE_TRY(fe_batch_outer_step(B));
   }
   return FE_OK;
 }

@@ -61,13 +61,13 @@ template <class S>
 fe_status fe_batch_iteration(FeBatch* B, int slot, int redistribute);
 template <class S>
 fe_status fe_batch_norm(FeBatch* B, int slot, int src, int mode, int redistribute);
+// mixed solves: start of an FP32 run, and its end with the FP64 reliable update
 fe_status fe_batch_inner_start(FeBatch* B);
 fe_status fe_batch_inner_finish(FeBatch* B);
-fe_status fe_batch_outer_step(FeBatch* B);
 fe_status fe_batch_fill(FeBatch* B, int i, const fe_mesh* m, CgWork* w, const double* b,
                         const fe_cg_opts* opts);
 // first steps of a solve for every problem of B: fresh scalars, ||G^T b||, r = b - A x, and the
 // initial preconditioned direction (FP64) or the initial residual check (mixed)
 fe_status fe_batch_start(FeBatch* B, bool mixed);
-// run a full solve of every active problem (FP64 PCG or the mixed FCG scheme)
+// run a full solve of every active problem (FP64 PCG or the mixed reliable-update scheme)
 fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts);

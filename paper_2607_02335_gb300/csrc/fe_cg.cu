@@ -15,8 +15,8 @@
 // Convergence (unspecified in the paper): ||G^T r||_2 / ||G^T b||_2 <= rtol over free nodes, with
 // ||G^T r||^2 = sum_e (S r)_e^2 / mult_e.
 //
-// Mixed precision: FP64 iterative refinement.  r = b - A x with the FP64 apply, an FP32 PCG solves
-// A d = r (FP32 vectors and operator, FP64-accumulated pairings) to inner_rtol, x += d in FP64.
+// Mixed precision: FP32 PCG with FP64 reliable updates (solve_reliable), or FP64 FCG whose variable
+// preconditioner is an FP32 PCG solve (solve_fcg_outer).
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -123,6 +123,14 @@ __global__ void k_update_ur<float, float>(float* __restrict__ u, float* __restri
     r[e] = re;
     w[e] = re;
   }
+}
+
+// p = z + c p (host scalar): the search direction kept across a reliable update
+__global__ void k_keep_direction(float* __restrict__ p, const float* __restrict__ z, float c,
+                                 long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    p[e] = fmaf(c, p[e], z[e]);
 }
 
 // p = z + beta p
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   const double qz = (mode == FIN_ITER && flexible) ? sum_slot(partials, 2, sh) : 0.0;
   if (threadIdx.x != 0) return;
   const int k = sc->iter;
-  fin_scalars(sc, rn2, rz, qz, rtol, mode, flexible);
+  fin_scalars(sc, rn2, rz, qz, rtol < 0.0 ? sc->rtol : rtol, mode, flexible);
   if (hist && mode == FIN_ITER) {
     hist[3 * k + 2] = sc->relres;
     if (!sc->done) hist[3 * k + 1] = sc->beta;
@@ -372,9 +380,8 @@ fe_status launch_inner_apply(const ApplyLaunch& L, const CgWork* w) {
 
 // one PCG iteration on vectors of type S, solution of type U, scalars sc
 template <class S, class U>
-fe_status enqueue_iteration(const fe_mesh* m, CgWork* w, int op, bool flexible, double rtol,
-                            U* u, S* r, S* z, S* p, S* q, S* wv, const S* invdiag, CgScal* sc,
-                            double* hist) {
+fe_status enqueue_iteration(const fe_mesh* m, CgWork* w, int op, bool flexible, U* u, S* r, S* z,
+                            S* p, S* q, S* wv, const S* invdiag, CgScal* sc, double* hist) {
   const long long n = w->n;
   ApplyLaunch L{m, op, p, q, w->st, &sc->done};
   if (sizeof(S) == 8)
@@ -388,14 +395,15 @@ fe_status enqueue_iteration(const fe_mesh* m, CgWork* w, int op, bool flexible, 
   k_precond<S><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(wv, r, flexible ? q : nullptr, invdiag,
                                                       w->invmult, z, w->partials, sc, n, 1,
                                                       sizeof(S) == 4 ? 1 : 0);
-  k_fin_beta<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, rtol, FIN_ITER, flexible ? 1 : 0, hist);
+  k_fin_beta<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, -1.0, FIN_ITER, flexible ? 1 : 0, hist);
   k_update_p<S><<<grid_for(n), 256, 0, w->st>>>(p, z, sc, n);
   return fe_cuda_check(cudaGetLastError(), "cg iteration launch");
 }
 
+// the iteration graph; its stopping tolerance is read from sc->rtol at every replay
 template <class S, class U>
-fe_status build_graph(const fe_mesh* m, CgWork* w, int op, bool flexible, double rtol, U* u, S* r,
-                      S* z, S* p, S* q, S* wv, const S* invdiag, CgScal* sc, double* hist,
+fe_status build_graph(const fe_mesh* m, CgWork* w, int op, bool flexible, U* u, S* r, S* z, S* p,
+                      S* q, S* wv, const S* invdiag, CgScal* sc, double* hist,
                       cudaGraphExec_t* exec) {
   cudaGraph_t g = nullptr;
   {  // one uncaptured apply first, so that per-kernel attributes are set outside the capture
@@ -403,7 +411,7 @@ fe_status build_graph(const fe_mesh* m, CgWork* w, int op, bool flexible, double
     FE_TRY(sizeof(S) == 8 ? fe_launch_apply_f64dw(L) : launch_inner_apply(L, w));
   }
   FE_CUDA(cudaStreamBeginCapture(w->st, cudaStreamCaptureModeThreadLocal), "begin capture");
-  fe_status s = enqueue_iteration<S, U>(m, w, op, flexible, rtol, u, r, z, p, q, wv, invdiag, sc, hist);
+  fe_status s = enqueue_iteration<S, U>(m, w, op, flexible, u, r, z, p, q, wv, invdiag, sc, hist);
   cudaError_t e = cudaStreamEndCapture(w->st, &g);
   if (s != FE_OK) {
     if (g) cudaGraphDestroy(g);
@@ -430,11 +438,13 @@ fe_status run_until_done(CgWork* w, cudaGraphExec_t exec, int slot, CgScal* out)
   return FE_OK;
 }
 
-fe_status set_scal(CgWork* w, int slot, int maxit, int stall_limit = 0) {
+// fresh scalars of a run; rtol is the stopping tolerance the replayed iteration graphs read
+fe_status set_scal(CgWork* w, int slot, int maxit, int stall_limit, double rtol) {
   CgScal s;
   std::memset(&s, 0, sizeof(s));
   s.maxit = maxit;
   s.stall_limit = stall_limit;
+  s.rtol = rtol;
   w->hsc[slot] = s;
   return fe_cuda_check(
       cudaMemcpyAsync(&w->sc[slot], &w->hsc[slot], sizeof(CgScal), cudaMemcpyHostToDevice, w->st),
@@ -480,14 +490,14 @@ fe_status inner_solve(const fe_mesh* m, CgWork* w, int op, int flex, double rnor
   const long long n = w->n;
   const double s = 1.0 / sqrt(rnorm2);
   k_to_inner<<<grid_for(n), 256, 0, w->st>>>(w->w, w->invmult, w->r32, w->d32, s, n);
-  FE_TRY(set_scal(w, 1, maxit, 20));
+  FE_TRY(set_scal(w, 1, maxit, 20, irtol));
   FE_TRY(residual_norm<float>(m, w, w->r32, w->w32, &w->sc[1], FIN_INIT_B));
   FE_TRY(init_direction<float>(m, w, w->r32, w->z32, w->p32, w->w32, w->invdiag32, &w->sc[1], irtol));
   CgScal h;
   FE_TRY(read_scal(w, 1, &h));
   if (!h.done) {
     if (!w->g32[flex])
-      FE_TRY((build_graph<float, float>(m, w, op, flex, irtol, w->d32, w->r32, w->z32, w->p32, w->q32,
+      FE_TRY((build_graph<float, float>(m, w, op, flex, w->d32, w->r32, w->z32, w->p32, w->q32,
                                         w->w32, w->invdiag32, &w->sc[1], nullptr, &w->g32[flex])));
     FE_TRY(run_until_done(w, w->g32[flex], 1, &h));
   }
@@ -561,6 +571,97 @@ fe_status solve_fcg_outer(const fe_mesh* m, CgWork* w, int op, const double* b, 
     k_fin_fcg<<<1, RED_THREADS, 0, w->st>>>(w->partials, &w->sc[0], 0);
     k_update_p<double><<<grid_for(n), 256, 0, w->st>>>(w->p, w->z, &w->sc[0], n);
     FE_CUDA(cudaGetLastError(), "fcg launch");
+  }
+  res->iters = total;
+  res->outer_iters = outer;
+  return FE_OK;
+}
+
+// FP32 PCG with FP64 reliable updates (residual replacement; Sleijpen & van der Vorst 1996, the
+// mixed-precision form of Clark et al. 2010): the iteration runs on FP32 vectors and the FP32
+// operator; whenever its recursive residual has dropped by the factor delta since the last
+// replacement, the correction accumulated in FP32 is added to the FP64 solution, the true residual
+// b - A x is formed with the FP64 operator and replaces the recursive one (assembled in FP64 and
+// split evenly over the copies of each node, scaled to unit norm), and the search direction is
+// kept: p = P r' + beta p with beta = <r', P r'> / <r_{k-1}, z_{k-1}>.  Keeping p keeps the
+// Krylov space, so the iteration count stays near that of FP64 PCG, while every step but the few
+// replacements runs in FP32.  The FP64 residual of the final iterate decides convergence.
+fe_status solve_reliable(const fe_mesh* m, CgWork* w, int op, const double* b, double bnorm2,
+                         const fe_cg_opts* opts, fe_cg_result* res, fe_status* status) {
+  const long long n = w->n;
+  const double delta = opts->inner_rtol > 0.0 ? opts->inner_rtol : 0.1;
+  int total = 0, outer = 0;
+  double s_old = 0.0, rz_old = 0.0;  // scale and <r, z> (scaled units) when the FP32 run stopped
+  bool have_p = false;
+  CgScal h;
+  for (;;) {
+    // true FP64 residual of the current iterate; w = S r for the inner right-hand side
+    ApplyLaunch L{m, op, w->x, w->q, w->st, nullptr};
+    FE_TRY(fe_launch_apply_f64dw(L));
+    k_residual<<<grid_for(n), 256, 0, w->st>>>(b, w->q, w->r, n);
+    FE_TRY(residual_norm<double>(m, w, w->r, w->w, &w->sc[0], FIN_NORM));
+    FE_TRY(read_scal(w, 0, &h));
+    const double rel = sqrt(h.rnorm2 / bnorm2);
+    res->rel_res = rel;
+    if (rel <= opts->rtol) {
+      *status = FE_OK;
+      break;
+    }
+    if (!std::isfinite(rel)) {
+      *status = FE_ERR_BREAKDOWN;
+      break;
+    }
+    if (total >= opts->maxit) {
+      *status = FE_ERR_NOT_CONVERGED;
+      break;
+    }
+    // run the FP32 iteration down to delta, or to just below the outer target
+    const double irtol = std::max(delta, 0.5 * opts->rtol / rel);
+    FE_TRY(set_scal(w, 1, opts->maxit - total, 0, irtol));
+    // r32 = s (S r) / mult, d32 = 0
+    const double s = 1.0 / sqrt(h.rnorm2);
+    k_to_inner<<<grid_for(n), 256, 0, w->st>>>(w->w, w->invmult, w->r32, w->d32, s, n);
+    FE_TRY(residual_norm<float>(m, w, w->r32, w->w32, &w->sc[1], FIN_INIT_B));
+    if (!have_p) {
+      FE_TRY(init_direction<float>(m, w, w->r32, w->z32, w->p32, w->w32, w->invdiag32, &w->sc[1],
+                                   irtol));
+      FE_TRY(read_scal(w, 1, &h));
+    } else {
+      // z = P r', <r', z>; p = z + beta p in the new scale (p and rz_old were in units of s_old)
+      FE_CUDA(cudaMemcpyAsync(w->w32, w->r32, n * sizeof(float), cudaMemcpyDeviceToDevice, w->st),
+              "cg copy");
+      FE_TRY(fe_launch_dss(m, FE_F32, w->w32, w->st));
+      k_precond<float><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(w->w32, w->r32, nullptr, w->invdiag32,
+                                                              w->invmult, w->z32, w->partials,
+                                                              &w->sc[1], n, 0, 1);
+      k_fin_beta<<<1, RED_THREADS, 0, w->st>>>(w->partials, &w->sc[1], irtol, FIN_INIT_R, 0, nullptr);
+      FE_TRY(read_scal(w, 1, &h));
+      const double ratio = s / s_old;
+      const double beta = h.rz / (rz_old * ratio * ratio);
+      k_keep_direction<<<grid_for(n), 256, 0, w->st>>>(w->p32, w->z32, (float)(beta * ratio), n);
+      FE_CUDA(cudaGetLastError(), "keep direction launch");
+    }
+    if (!h.done) {
+      if (!w->g32[0])
+        FE_TRY((build_graph<float, float>(m, w, op, false, w->d32, w->r32, w->z32, w->p32, w->q32,
+                                          w->w32, w->invdiag32, &w->sc[1], nullptr, &w->g32[0])));
+      FE_TRY(run_until_done(w, w->g32[0], 1, &h));
+    }
+    if (h.status == FE_ERR_BREAKDOWN) {
+      *status = FE_ERR_BREAKDOWN;
+      break;
+    }
+    total += h.iter;
+    ++outer;
+    s_old = s;
+    rz_old = h.rz;  // <r_{k-1}, z_{k-1}>: the run stopped before its last beta
+    have_p = h.iter > 0 || have_p;
+    if (h.iter == 0 && !have_p) {  // converged in FP32 before any step: nothing to add
+      *status = FE_ERR_NOT_CONVERGED;
+      break;
+    }
+    k_correct<<<grid_for(n), 256, 0, w->st>>>(w->x, w->d32, 1.0 / s, n);
+    FE_CUDA(cudaGetLastError(), "correction launch");
   }
   res->iters = total;
   res->outer_iters = outer;
@@ -641,7 +742,7 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
 
   // u := x, ||G^T b||
   FE_CUDA(cudaMemcpyAsync(w->x, x, n * sizeof(double), cudaMemcpyDeviceToDevice, w->st), "cg copy");
-  FE_TRY(set_scal(w, 0, opts->maxit));
+  FE_TRY(set_scal(w, 0, opts->maxit, 0, opts->rtol));
   FE_TRY(residual_norm<double>(m, w, b, w->w, &w->sc[0], FIN_INIT_B));
   CgScal h;
   FE_TRY(read_scal(w, 0, &h));
@@ -666,7 +767,7 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
     FE_TRY(read_scal(w, 0, &h));
     if (!h.done) {
       if (!w->g64[flex])
-        FE_TRY((build_graph<double, double>(m, w, op, flex, opts->rtol, w->x, w->r, w->z, w->p, w->q,
+        FE_TRY((build_graph<double, double>(m, w, op, flex, w->x, w->r, w->z, w->p, w->q,
                                             w->w, w->invdiag64, &w->sc[0], hist, &w->g64[flex])));
       FE_TRY(run_until_done(w, w->g64[flex], 0, &h));
     }
@@ -678,62 +779,10 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
       FE_CUDA(cudaMemcpy(opts->history, hist, 3 * (size_t)h.iter * sizeof(double),
                          cudaMemcpyDeviceToHost),
               "history readback");
-  } else if (flex) {
+  } else if (flex || lowp) {  // 16-bit inner operators: too coarse to keep a direction across updates
     FE_TRY(solve_fcg_outer(m, w, op, b, bnorm2, opts, res, &status));
   } else {
-    int total = 0, outer = 0;
-    for (;;) {
-      // FP64 residual of the current iterate
-      ApplyLaunch L{m, op, w->x, w->q, w->st, nullptr};
-      FE_TRY(fe_launch_apply_f64dw(L));
-      k_residual<<<grid_for(n), 256, 0, w->st>>>(b, w->q, w->r, n);
-      FE_TRY(residual_norm<double>(m, w, w->r, w->w, &w->sc[0], FIN_INIT_R));
-      FE_TRY(read_scal(w, 0, &h));
-      const double rel = sqrt(h.rnorm2 / bnorm2);
-      res->rel_res = rel;
-      if (rel <= opts->rtol) {
-        status = FE_OK;
-        break;
-      }
-      if (!std::isfinite(rel)) {
-        status = FE_ERR_BREAKDOWN;
-        break;
-      }
-      if (total >= opts->maxit) {
-        status = FE_ERR_NOT_CONVERGED;
-        break;
-      }
-      // inner FP32 PCG on A d = s r
-      const double s = 1.0 / sqrt(h.rnorm2);
-      k_to_inner<<<grid_for(n), 256, 0, w->st>>>(w->w, w->invmult, w->r32, w->d32, s, n);
-      FE_TRY(set_scal(w, 1, opts->maxit - total, 20));
-      FE_TRY(residual_norm<float>(m, w, w->r32, w->w32, &w->sc[1], FIN_INIT_B));
-      const double irtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 1e-2;
-      FE_TRY(init_direction<float>(m, w, w->r32, w->z32, w->p32, w->w32, w->invdiag32, &w->sc[1],
-                                   irtol));
-      FE_TRY(read_scal(w, 1, &h));
-      if (!h.done) {
-        if (!w->g32[flex])
-          FE_TRY((build_graph<float, float>(m, w, op, flex, irtol, w->d32, w->r32, w->z32, w->p32,
-                                            w->q32, w->w32, w->invdiag32, &w->sc[1], nullptr,
-                                            &w->g32[flex])));
-        FE_TRY(run_until_done(w, w->g32[flex], 1, &h));
-      }
-      if (h.status == FE_ERR_BREAKDOWN && h.iter == 0) {
-        status = FE_ERR_BREAKDOWN;
-        break;
-      }
-      total += h.iter;
-      ++outer;
-      k_correct<<<grid_for(n), 256, 0, w->st>>>(w->x, w->d32, 1.0 / s, n);
-      FE_CUDA(cudaGetLastError(), "correction launch");
-      if (outer > 200) {
-        status = FE_ERR_NOT_CONVERGED;
-        break;
-      }
-    }
-    res->iters = total;
-    res->outer_iters = outer;
+    FE_TRY(solve_reliable(m, w, op, b, bnorm2, opts, res, &status));
   }
   FE_CUDA(cudaMemcpyAsync(x, w->x, n * sizeof(double), cudaMemcpyDeviceToDevice, w->st), "cg copy");
   FE_CUDA(cudaStreamSynchronize(w->st), "cg synchronize");

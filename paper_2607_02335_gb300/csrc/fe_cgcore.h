@@ -13,6 +13,7 @@ struct CgScal {
   int stall_limit;  // stop after this many iterations without progress (0 = never)
   int stall_total;  // batched mixed solves: inner iterations accumulated over outer steps
   int pad;
+  double rtol;      // stopping tolerance of graph-replayed iterations (set by the host per run)
 };
 
 // FIN_INIT_B: ||G^T b||^2.  FIN_INIT_R: initial residual, <r,z>.  FIN_ITER: residual, convergence,

@@ -225,7 +225,6 @@ fe_status step_mixed(fe_server* S) {
   FE_TRY(fe_batch_read(&S->b32));
   if (!fe_batch_all_done(&S->b32, 1)) return FE_OK;
   FE_TRY(fe_batch_inner_finish(&S->b32));
-  FE_TRY(fe_batch_outer_step(&S->b32));
   FE_TRY(fe_batch_read(&S->b32));
   S->inner_phase = false;
   return retire(S, S->b32, S->run32);

@@ -167,3 +167,33 @@ def test_rhs_and_l2_error_vs_oracle(fe, p, m, amp):
         uc = O.gather(om, u)
         e = gm.l2_error(torch.from_numpy(uc).cuda(), kind)
         assert abs(e - O.l2_error(om, uc, kind)) <= 1e-12 * abs(e)
+
+
+def test_reliable_update_solve_at_48cubed(fe):
+    """FP32 PCG with FP64 reliable updates on the deformed Q3 48^3 mesh (sine load): the FP64
+    residual of the returned x (formed with the FP64 operator, itself parity-tested against the
+    oracle) is below 1e-10, the solution agrees with FP64 PCG's to the solve's accuracy, and the
+    FP32 iteration count stays within 1.5x of FP64 PCG's (the kept search direction)."""
+    gm = fe.Mesh(48, 3, deform_amp=0.1, dirichlet=True)
+    b = gm.rhs(fe.FE_RHS_SINE)
+    x64 = torch.zeros_like(b)
+    r64 = gm.cg_solve(b, x64, rtol=1e-10, maxit=5000)
+    x32 = torch.zeros_like(b)
+    r32 = gm.cg_solve(b, x32, rtol=1e-10, maxit=5000, mixed=fe.FE_F32, inner_rtol=0.1)
+    assert r64.status == fe.FE_OK and r32.status == fe.FE_OK
+    assert r32.rel_res <= 1e-10 and r32.outer_iters >= 2
+    assert r32.iters <= 1.5 * r64.iters
+    # FP64 residual of the mixed solution, recomputed here: ||G^T (b - A x)|| / ||G^T b|| over the
+    # free nodes (the assembled mass of ones vanishes exactly on the Dirichlet nodes)
+    free = gm.apply(torch.ones_like(b), op=fe.FE_MASS, flags=fe.FE_ASSEMBLE) != 0
+    inv_mult = free / gm.dss(torch.ones_like(b))
+
+    def gnorm(v):
+        w = gm.dss(v)
+        return float(torch.sqrt((w * w * inv_mult).sum()))
+
+    res = b - gm.apply(x32, op=fe.FE_LAPLACE)
+    assert gnorm(res) / gnorm(b) <= 1.05e-10
+    assert float((x32 - x64).abs().max()) <= 1e-8 * float(x64.abs().max())
+    e64, e32 = gm.l2_error(x64), gm.l2_error(x32)
+    assert abs(e64 - e32) <= 1e-6 * e64
