@@ -29,7 +29,7 @@
 namespace {
 
 constexpr int BT = 256;            // threads of every batched CTA
-constexpr long long CHUNK = 16384;  // elements (or DSS pairs) per work item
+constexpr long long CHUNK = 4096;  // elements per vector work item (small batches still fill the GPU)
 
 // ---- 1D tables of every degree, in constant memory -------------------------------------------
 template <class V>
@@ -107,6 +107,9 @@ struct Chunk {
   int pad;
   long long lo, hi;
 };
+struct DssRow {  // one row of interfaces of one problem (see kb_dss)
+  int prob, row;
+};
 
 // ---- persistent apply ------------------------------------------------------------------------
 template <int N, class V>
@@ -142,30 +145,24 @@ __device__ __forceinline__ void apply_item(const BProb& P, int prec, int src, lo
     apply_cells<N, V, FE_LAPLACE, GEOM_STORED_K>(a, tab_of<N, V>(), cell0, sm, stride);
 }
 
-template <class V>
-__global__ void __launch_bounds__(BT)
-    kb_apply(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, long long ntiles,
-             int slot, int prec, int src, unsigned long long* counter) {
+// persistent apply over the tiles [lo, hi) of one degree (tiles are grouped by degree), each kernel
+// compiled for its own degree: registers and shared memory of that degree, not of the largest
+template <int N, class V>
+__global__ void __launch_bounds__(BT, (apply_minb<N, V, FE_LAPLACE>()))
+    kb_apply_n(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, long long lo,
+               long long hi, int slot, int prec, int src, unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ long long item;
   for (;;) {
-    if (threadIdx.x == 0) item = (long long)atomicAdd(counter, 1ULL);
+    if (threadIdx.x == 0) item = lo + (long long)atomicAdd(counter, 1ULL);
     __syncthreads();
     const long long it = item;
     __syncthreads();
-    if (it >= ntiles) break;
+    if (it >= hi) break;
     const Tile T = tiles[it];
     const BProb& P = probs[T.prob];
     if (*(volatile const int*)&P.sc[slot].done) continue;  // uniform over the CTA
-    switch (P.n) {
-      case 2: apply_item<2, V>(P, prec, src, T.cell0, sm); break;
-      case 3: apply_item<3, V>(P, prec, src, T.cell0, sm); break;
-      case 4: apply_item<4, V>(P, prec, src, T.cell0, sm); break;
-      case 5: apply_item<5, V>(P, prec, src, T.cell0, sm); break;
-      case 6: apply_item<6, V>(P, prec, src, T.cell0, sm); break;
-      case 7: apply_item<7, V>(P, prec, src, T.cell0, sm); break;
-      case 8: apply_item<8, V>(P, prec, src, T.cell0, sm); break;
-    }
+    apply_item<N, V>(P, prec, src, T.cell0, sm);
     __syncthreads();  // the next tile reuses the shared-memory tile
   }
 }
@@ -173,17 +170,6 @@ __global__ void __launch_bounds__(BT)
 template <int N, class V>
 constexpr size_t tile_bytes() {
   return (size_t)apply_narr<V>(FE_LAPLACE) * (Cfg<N>::TILE + Cfg<N>::CS) * Sm<V>::BYTES;
-}
-template <class V>
-size_t max_tile_bytes() {
-  size_t b = tile_bytes<2, V>();
-  b = std::max(b, tile_bytes<3, V>());
-  b = std::max(b, tile_bytes<4, V>());
-  b = std::max(b, tile_bytes<5, V>());
-  b = std::max(b, tile_bytes<6, V>());
-  b = std::max(b, tile_bytes<7, V>());
-  b = std::max(b, tile_bytes<8, V>());
-  return b;
 }
 
 // ---- vector kernels over chunks ----------------------------------------------------------------
@@ -260,55 +246,87 @@ __global__ void __launch_bounds__(BT)
     const S* p = vec<S>(P, 3);
     const S* q = vec<S>(P, 4);
     S* w = vec<S>(P, 5);
-    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
-      u[e] = (S)((double)u[e] + a * (double)p[e]);
-      const S re = (S)((double)r[e] - a * (double)q[e]);
-      r[e] = re;
-      w[e] = re;
+    if constexpr (sizeof(S) == 4) {  // FP32 state: FP32 arithmetic (the FP64 pipe is slow)
+      const float af = (float)a;
+      for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
+        u[e] = fmaf(af, p[e], u[e]);
+        const float re = fmaf(-af, q[e], r[e]);
+        r[e] = re;
+        w[e] = re;
+      }
+    } else {
+      for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
+        u[e] = fma(a, p[e], u[e]);
+        const double re = fma(-a, q[e], r[e]);
+        r[e] = re;
+        w[e] = re;
+      }
     }
   }
 }
 
-// structured DSS pass over every problem's interface node pairs of one axis
+// structured DSS pass of one axis over rows of interfaces of every problem, one warp per row:
+// x-pass row (cz, cy) with items (interface, face node), y-pass row (cz, interface) and z-pass row
+// (interface, cy) with items (cx, face node); node counts are compile-time, so the index
+// arithmetic inside a row is multiplications and shifts.  Pairs of one pass are disjoint.
+template <class S, int N>
+__device__ __forceinline__ void dss_row(S* __restrict__ v, int axis, int row, int mx, int my,
+                                        int lane) {
+  constexpr int P = N - 1, N2 = N * N, N3 = N2 * N;
+  long long first, rstep;
+  int items, lstep, locL0, locR0, sa, sb;
+  if (axis == 0) {
+    first = (long long)row * mx;
+    items = (mx - 1) * N2;
+    lstep = 1;
+    rstep = 1;
+    locL0 = P, locR0 = 0, sa = N, sb = N2;
+  } else if (axis == 1) {
+    const int cz = row / (my - 1), u = row - cz * (my - 1);
+    first = ((long long)cz * my + u) * mx;
+    items = mx * N2;
+    lstep = 1;
+    rstep = mx;
+    locL0 = P * N, locR0 = 0, sa = 1, sb = N2;
+  } else {
+    const int u = row / my, cy = row - u * my;
+    first = ((long long)u * my + cy) * mx;
+    items = mx * N2;
+    lstep = 1;
+    rstep = (long long)mx * my;
+    locL0 = P * N2, locR0 = 0, sa = 1, sb = N;
+  }
+  for (int it = lane; it < items; it += 32) {
+    const int g = it / N2, f = it - g * N2, fb = f / N, fa = f - fb * N;
+    const long long L = first + (long long)g * lstep;
+    const int off = fa * sa + fb * sb;
+    S* pl = v + L * N3 + locL0 + off;
+    S* pr = v + (L + rstep) * N3 + locR0 + off;
+    const S sum = *pl + *pr;
+    *pl = sum;
+    *pr = sum;
+  }
+}
+
 template <class S>
 __global__ void __launch_bounds__(BT)
-    kb_dss(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks, int slot,
+    kb_dss(const BProb* __restrict__ probs, const DssRow* __restrict__ rows, int nrows, int slot,
            int axis) {
-  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    const Chunk C = chunks[c];
-    const BProb& P = probs[C.prob];
-    if (*(volatile const int*)&P.sc[slot].done) continue;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (BT / 32);
+  for (int w = blockIdx.x * (BT / 32) + (threadIdx.x >> 5); w < nrows; w += warps) {
+    const DssRow R = rows[w];
+    const BProb& P = probs[R.prob];
+    if (*(volatile const int*)&P.sc[slot].done) continue;  // uniform over the warp
     S* v = vec<S>(P, 5);
-    const int n = P.n, p = n - 1, n2 = n * n, n3 = n2 * n, mx = P.mx, my = P.my;
-    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
-      const int f = (int)(e % n2);
-      const long long q = e / n2;
-      const int fa = f % n, fb = f / n;
-      long long L, R;
-      int locL, locR;
-      if (axis == 0) {
-        const long long cxL = q % (mx - 1), r = q / (mx - 1);
-        L = r * mx + cxL;
-        R = L + 1;
-        locL = (fb * n + fa) * n + p;
-        locR = (fb * n + fa) * n;
-      } else if (axis == 1) {
-        const long long cx = q % mx, r = q / mx, cyL = r % (my - 1), cz = r / (my - 1);
-        L = (cz * my + cyL) * mx + cx;
-        R = L + mx;
-        locL = (fb * n + p) * n + fa;
-        locR = (fb * n) * n + fa;
-      } else {
-        L = q;
-        R = L + (long long)mx * my;
-        locL = (p * n + fb) * n + fa;
-        locR = fb * n + fa;
-      }
-      S* pl = v + L * n3 + locL;
-      S* pr = v + R * n3 + locR;
-      const S s = *pl + *pr;
-      *pl = s;
-      *pr = s;
+    switch (P.n) {
+      case 2: dss_row<S, 2>(v, axis, R.row, P.mx, P.my, lane); break;
+      case 3: dss_row<S, 3>(v, axis, R.row, P.mx, P.my, lane); break;
+      case 4: dss_row<S, 4>(v, axis, R.row, P.mx, P.my, lane); break;
+      case 5: dss_row<S, 5>(v, axis, R.row, P.mx, P.my, lane); break;
+      case 6: dss_row<S, 6>(v, axis, R.row, P.mx, P.my, lane); break;
+      case 7: dss_row<S, 7>(v, axis, R.row, P.mx, P.my, lane); break;
+      case 8: dss_row<S, 8>(v, axis, R.row, P.mx, P.my, lane); break;
     }
   }
 }
@@ -564,9 +582,9 @@ unsigned grid_chunks(int n) { return (unsigned)std::max(1, std::min(n, 152 * 8))
 // ---------------------------------------------------------------------------------------------
 fe_status fe_batch_build(FeBatch* B) {
   const int np = (int)B->hp.size();
-  std::vector<Tile> tiles;
+  std::vector<Tile> tiles_n[FE_MAXN + 1];
   std::vector<Chunk> vch;
-  std::vector<Chunk> dch[3];
+  std::vector<DssRow> dch[3];
   for (int i = 0; i < np; ++i) {
     BProb& P = B->hp[i];
     const int n = P.n;
@@ -584,18 +602,22 @@ fe_status fe_batch_build(FeBatch* B) {
       P.chunk0 = P.chunk1 = (int)vch.size();
       continue;
     }
-    for (long long c = 0; c < P.ncells; c += cpb) tiles.push_back({i, 0, c});
+    for (long long c = 0; c < P.ncells; c += cpb) tiles_n[n].push_back({i, 0, c});
     P.chunk0 = (int)vch.size();
     for (long long e = 0; e < P.ncw; e += CHUNK) vch.push_back({i, 0, e, std::min(P.ncw, e + CHUNK)});
     P.chunk1 = (int)vch.size();
-    const long long n2 = (long long)n * n;
-    const long long work[3] = {(long long)(P.mx - 1) * P.my * P.mz * n2,
-                               (long long)P.mx * (P.my - 1) * P.mz * n2,
-                               (long long)P.mx * P.my * (P.mz - 1) * n2};
+    // rows of interfaces per axis: x (cz, cy) if mx > 1; y (cz, interface); z (interface, cy)
+    const int rows[3] = {P.mx > 1 ? P.my * P.mz : 0, P.mz * (P.my - 1), (P.mz - 1) * P.my};
     for (int a = 0; a < 3; ++a)
-      for (long long e = 0; e < work[a]; e += CHUNK) dch[a].push_back({i, 0, e, std::min(work[a], e + CHUNK)});
+      for (int r = 0; r < rows[a]; ++r) dch[a].push_back({i, r});
   }
-  // interleave tiles of different problems so that neighbouring items spread over the mix
+  // tiles grouped by degree: one persistent apply launch per degree present
+  std::vector<Tile> tiles;
+  for (int nn = 0; nn <= FE_MAXN; ++nn) {
+    B->tile_lo[nn] = (long long)tiles.size();
+    tiles.insert(tiles.end(), tiles_n[nn].begin(), tiles_n[nn].end());
+    B->tile_hi[nn] = (long long)tiles.size();
+  }
   B->ntiles = (long long)tiles.size();
   B->nvch = (int)vch.size();
   for (int a = 0; a < 3; ++a) B->ndch[a] = (int)dch[a].size();
@@ -613,7 +635,7 @@ fe_status fe_batch_build(FeBatch* B) {
   FE_TRY(up(&B->d_tiles, &B->cap_tiles, tiles.data(), tiles.size() * sizeof(Tile)));
   FE_TRY(up(&B->d_vch, &B->cap_vch, vch.data(), vch.size() * sizeof(Chunk)));
   for (int a = 0; a < 3; ++a)
-    FE_TRY(up(&B->d_dch[a], &B->cap_dch[a], dch[a].data(), dch[a].size() * sizeof(Chunk)));
+    FE_TRY(up(&B->d_dch[a], &B->cap_dch[a], dch[a].data(), dch[a].size() * sizeof(DssRow)));
   FE_TRY(up((void**)&B->d_probs, &B->cap_probs, B->hp.data(), np * sizeof(BProb)));
   const size_t pbytes = std::max<size_t>(1, vch.size()) * 4 * sizeof(double);
   if (pbytes > B->cap_partials) {
@@ -634,33 +656,51 @@ fe_status fe_batch_build(FeBatch* B) {
   return FE_OK;
 }
 
+template <int N, class V>
+static fe_status launch_apply_degree(FeBatch* B, int slot, int src) {
+  const long long lo = B->tile_lo[N], hi = B->tile_hi[N];
+  if (hi <= lo) return FE_OK;
+  const size_t smem = tile_bytes<N, V>();
+  static int per_sm_dev[64] = {};  // resident CTAs per SM, per device (attribute set once)
+  int dev = 0;
+  FE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  int per_sm = (dev >= 0 && dev < 64) ? per_sm_dev[dev] : 0;
+  if (per_sm == 0) {
+    FE_CUDA(cudaFuncSetAttribute(kb_apply_n<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem),
+            "batch apply attribute");
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_apply_n<N, V>, BT, smem),
+            "occupancy");
+    per_sm = std::max(1, per_sm);
+    if (dev >= 0 && dev < 64) per_sm_dev[dev] = per_sm;
+  }
+  const long long grid = std::min<long long>(hi - lo, 152LL * per_sm);
+  kb_apply_n<N, V><<<(unsigned)grid, BT, smem, B->st>>>(
+      B->d_probs, (const Tile*)B->d_tiles, lo, hi, slot, std::is_same<V, dw>::value ? FE_F64 : FE_F32,
+      src, B->d_counter + N);
+  return fe_cuda_check(cudaGetLastError(), "batch apply launch");
+}
+
 template <class S>
 static fe_status launch_apply_batched(FeBatch* B, int slot, int src = 0) {
   using V = typename std::conditional<sizeof(S) == 8, dw, float>::type;
-  const size_t smem = max_tile_bytes<V>();
-  static bool attr[2] = {false, false};
-  if (!attr[sizeof(S) == 8]) {
-    FE_CUDA(cudaFuncSetAttribute(kb_apply<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-            "batch apply attribute");
-    attr[sizeof(S) == 8] = true;
-  }
-  FE_CUDA(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), B->st), "counter reset");
-  int per_sm = 0;
-  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_apply<V>, BT, smem), "occupancy");
-  const long long grid = std::max(1LL, std::min<long long>(B->ntiles, 152LL * std::max(1, per_sm)));
-  if (B->ntiles > 0)
-    kb_apply<V><<<(unsigned)grid, BT, smem, B->st>>>(B->d_probs, (const Tile*)B->d_tiles, B->ntiles, slot,
-                                                     sizeof(S) == 8 ? FE_F64 : FE_F32, src,
-                                                     B->d_counter);
-  return fe_cuda_check(cudaGetLastError(), "batch apply launch");
+  FE_CUDA(cudaMemsetAsync(B->d_counter, 0, (FE_MAXN + 1) * sizeof(unsigned long long), B->st),
+          "counter reset");
+  FE_TRY((launch_apply_degree<2, V>(B, slot, src)));
+  FE_TRY((launch_apply_degree<3, V>(B, slot, src)));
+  FE_TRY((launch_apply_degree<4, V>(B, slot, src)));
+  FE_TRY((launch_apply_degree<5, V>(B, slot, src)));
+  FE_TRY((launch_apply_degree<6, V>(B, slot, src)));
+  FE_TRY((launch_apply_degree<7, V>(B, slot, src)));
+  return launch_apply_degree<8, V>(B, slot, src);
 }
 
 template <class S>
 static fe_status launch_dss_batched(FeBatch* B, int slot) {
   for (int axis = 2; axis >= 0; --axis)
     if (B->ndch[axis] > 0)
-      kb_dss<S><<<grid_chunks(B->ndch[axis]), BT, 0, B->st>>>(B->d_probs, (const Chunk*)B->d_dch[axis],
-                                                              B->ndch[axis], slot, axis);
+      kb_dss<S><<<grid_chunks((B->ndch[axis] + BT / 32 - 1) / (BT / 32)), BT, 0, B->st>>>(
+          B->d_probs, (const DssRow*)B->d_dch[axis], B->ndch[axis], slot, axis);
   return fe_cuda_check(cudaGetLastError(), "batch dss launch");
 }
 
@@ -832,6 +872,18 @@ fe_status fe_batch_start(FeBatch* B, bool mixed) {
   return fe_cuda_check(cudaGetLastError(), "batch start");
 }
 
+// after a read-back: converged problems leave the work lists, so the launches of the following
+// iterations walk the unconverged problems' tiles and chunks only
+static fe_status drop_converged(FeBatch* B) {
+  bool changed = false;
+  for (size_t i = 0; i < B->hp.size(); ++i)
+    if (B->active[i] && B->hsc[2 * i].done) {
+      B->active[i] = 0;
+      changed = true;
+    }
+  return changed ? fe_batch_build(B) : FE_OK;
+}
+
 fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts) {
   const int batch = 8;
   const bool mixed = opts->mixed == FE_F32;
@@ -839,6 +891,7 @@ fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts) {
   if (!mixed) {
     FE_TRY(fe_batch_read(B));
     while (!fe_batch_all_done(B, 0)) {
+      FE_TRY(drop_converged(B));
       for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<double>(B, 0, 0));
       FE_TRY(fe_batch_read(B));
     }
@@ -848,6 +901,7 @@ fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts) {
   for (;;) {
     FE_TRY(fe_batch_read(B));
     if (fe_batch_all_done(B, 0)) break;
+    FE_TRY(drop_converged(B));
     FE_TRY(fe_batch_inner_start(B));
     FE_TRY(fe_batch_read(B));
     while (!fe_batch_all_done(B, 1)) {

@@ -33,6 +33,7 @@ struct FeBatch {
   void* d_tiles = nullptr;
   size_t cap_tiles = 0;
   long long ntiles = 0;
+  long long tile_lo[FE_MAXN + 1] = {}, tile_hi[FE_MAXN + 1] = {};  // tiles of each degree n
   void* d_vch = nullptr;
   size_t cap_vch = 0;
   int nvch = 0;
