@@ -214,7 +214,7 @@ __device__ __forceinline__ int cta_exp_shift(const double (&xr)[N]) {
 }
 
 // Reference gradient at the Gauss points from differences of the stored inputs (the FP64 path:
-// binary64 inputs into double-word differences; the FP32 path: float differences): component a is
+// binary64 inputs into double-word differences; also written for float values): component a is
 // B'_a (the derivative from the differences along axis a) followed by V along the two other axes.
 // Every value the sweeps carry is of the size of a difference of neighbouring nodal values, not of
 // x itself, so the rounding of the sweeps does not meet the cancellation of the derivative (a
@@ -465,12 +465,11 @@ __host__ __device__ constexpr int roll_unroll() {
   return (OP == FE_LAPLACE && (N == 6 || N == 8)) ? 1 : N / 2;
 }
 
-// Arrays of the shared-memory tile: Laplace 3 (the FP64 and FP32 paths a fourth for the inputs
+// Arrays of the shared-memory tile: Laplace 3 (the FP64 path a fourth for the binary64 inputs
 // that are differenced), mass 1.
 template <class V>
 __host__ __device__ constexpr int apply_narr(int op) {
-  return op == FE_LAPLACE ? ((std::is_same<V, dw>::value || std::is_same<V, float>::value) ? 4 : 3)
-                          : 1;
+  return op == FE_LAPLACE ? (std::is_same<V, dw>::value ? 4 : 3) : 1;
 }
 
 template <int N, class V, int OP, int GEOM, int MODE>
@@ -514,8 +513,8 @@ __device__ __forceinline__ void apply_cells_rolled(const CellArgs<N, V>& a, cons
 
   // FP64 path: binary64 inputs until they are differenced, CTA exponent shift (as apply_cells)
   constexpr bool DW = std::is_same<V, dw>::value;
-  // Laplace gradient from differences of the stored inputs (FP64 and FP32 paths)
-  constexpr bool DIFF = (DW || std::is_same<V, float>::value) && OP == FE_LAPLACE;
+  // FP64 path: Laplace gradient from differences of the binary64 inputs (diff_gradient)
+  constexpr bool DIFF = DW && OP == FE_LAPLACE;
   using SV = typename NT<V>::SV;
   int sh = 0;
   V in[N];
@@ -716,8 +715,8 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
   // FP64 path (double-word values): the inputs stay binary64 until they are differenced, and the
   // CTA's values are scaled by a power of two (cta_exp_shift)
   constexpr bool DW = std::is_same<V, dw>::value;
-  // Laplace gradient from differences of the stored inputs (FP64 and FP32 paths)
-  constexpr bool DIFF = (DW || std::is_same<V, float>::value) && OP == FE_LAPLACE;
+  // FP64 path: Laplace gradient from differences of the binary64 inputs (diff_gradient)
+  constexpr bool DIFF = DW && OP == FE_LAPLACE;
   using SV = typename NT<V>::SV;
   int sh = 0;
   V u[N], w[N];
