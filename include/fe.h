@@ -167,8 +167,10 @@ fe_status fe_diag(const fe_mesh* mesh, fe_op op, double* d_cell, void* stream);
 
 /* Duality pairing <a, b> = sum_e a_e b_e over all cell-wise entries (Lemma "Duality Pairing
  * Identity": pairing a dual with a continuous primal vector gives the assembled inner
- * product).  FP64 accumulation, fixed reduction order (bitwise reproducible).  result_dev is a
- * device pointer to one double.  prec FE_F64 (double inputs) or FE_F32 (float inputs). */
+ * product).  Products and sums in binary64 (the FP64 pipe; the whole binary64 range, rounding
+ * error below (n / 155,648 + 20) units of 2^-53 of sum |a_e b_e|), fixed reduction order
+ * (bitwise reproducible).  result_dev is a device pointer to one double.  prec FE_F64 (double
+ * inputs) or FE_F32 (float inputs). */
 fe_status fe_pairing(const fe_mesh* mesh, fe_prec prec, const void* a, const void* b,
                      double* result_dev, void* stream);
 
@@ -181,8 +183,10 @@ fe_status fe_pairing(const fe_mesh* mesh, fe_prec prec, const void* a, const voi
  * process exits); one CTA reduces 8192 consecutive entries per scratch slot, so meshes with more
  * than 67,108,864 cell-wise entries are rejected with FE_ERR_INVALID.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) and should come before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race.  Each call rewrites
- * every slot it reads, so no clearing is needed.  Same arguments and errors as fe_pairing. */
+ * capture; the address is kept for the life of the process, so the entry point must not be
+ * called after a reset of that device (cudaDeviceReset).  All calls share the array: calls that
+ * overlap on the GPU race.  Each call rewrites every slot it reads, so no clearing is needed.
+ * Same arguments, arithmetic and errors as fe_pairing. */
 fe_status fe_pairing_noalloc(const fe_mesh* mesh, fe_prec prec, const void* a, const void* b,
                              double* result_dev, void* stream);
 

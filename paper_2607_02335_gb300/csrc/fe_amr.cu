@@ -260,7 +260,8 @@ extern "C" fe_status fe_amr_create(const fe_amr_desc* d, void* stream, fe_amr** 
       cc[3 * c + a] = bit;
       fc[3 * c + a] = (double)(bit ? d->hi[a] : d->lo[a]) / mc;
     }
-  FE_CUDA(cudaSetDevice(d->device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(d->device), "cudaSetDevice");
   fe_status s = fe_mesh_create_impl(&cd, cc, stream, &A->coarse);
   if (s == FE_OK) {
     fe_mesh_desc fdsc = cd;
@@ -345,7 +346,8 @@ static fe_status amr_check(const fe_amr* A, fe_prec prec, const void* a, const v
 extern "C" fe_status fe_amr_dss(const fe_amr* A, fe_prec prec, const void* r, void* z,
                                 void* stream) {
   FE_TRY(amr_check(A, prec, r, z, "fe_amr_dss"));
-  FE_CUDA(cudaSetDevice(A->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(A->d.device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = prec == FE_F64 ? sizeof(double) : sizeof(float);
   if (r != z)
@@ -370,7 +372,8 @@ extern "C" fe_status fe_amr_apply(const fe_amr* A, fe_op op, fe_prec prec, const
     fe_set_error("fe_amr_apply: x and y overlap");
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(A->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(A->d.device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   const bool native = (flags & FE_NATIVE_F64) && prec == FE_F64;
   const fe_mesh* lv[2] = {A->coarse, A->fine};

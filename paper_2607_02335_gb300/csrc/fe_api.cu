@@ -49,7 +49,8 @@ fe_status fe_apply_impl(const fe_mesh* m, fe_op op, fe_prec prec, const void* x,
     fe_set_error("fe_apply: x and y overlap");
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   const bool native = (flags & FE_NATIVE_F64) && prec == FE_F64;
   FE_TRY(fe_ensure_geometry(m, prec, native));
   ApplyLaunch L{m, (int)op, x, y, (cudaStream_t)stream, nullptr, (flags & FE_ASSEMBLE) != 0,
@@ -79,7 +80,8 @@ extern "C" fe_status fe_dss(const fe_mesh* m, fe_prec prec, const void* r, void*
     fe_set_error("fe_dss: precision %d not provided", (int)prec);
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   if (r != z)
     FE_CUDA(cudaMemcpyAsync(z, r, (size_t)m->ncw * elem_size(prec), cudaMemcpyDeviceToDevice, st),
@@ -101,7 +103,8 @@ extern "C" fe_status fe_diag(const fe_mesh* m, fe_op op, double* d, void* stream
     fe_set_error("fe_diag: unknown operator %d", (int)op);
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   return fe_launch_diag(m, (int)op, d, (cudaStream_t)stream);
 }
 
@@ -113,6 +116,7 @@ extern "C" fe_status fe_pairing(const fe_mesh* m, fe_prec prec, const void* a, c
   }
   FE_TRY(check_vec(m, a, "fe_pairing a"));
   FE_TRY(check_vec(m, b, "fe_pairing b"));
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   return fe_launch_pairing(m, (int)prec, a, b, result_dev, (cudaStream_t)stream);
 }

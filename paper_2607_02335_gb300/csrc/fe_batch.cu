@@ -941,7 +941,8 @@ extern "C" fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes
         return FE_ERR_INVALID;
       }
   }
-  FE_CUDA(cudaSetDevice(meshes[0]->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(meshes[0]->d.device), "cudaSetDevice");
   FE_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "caller stream");
   const bool mixed = opts->mixed == FE_F32;
   FE_TRY(fe_batch_prepare());

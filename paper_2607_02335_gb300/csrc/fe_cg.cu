@@ -696,7 +696,8 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
     return FE_ERR_INVALID;
   }
   std::memset(res, 0, sizeof(*res));
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   const bool mixed = opts->mixed != 0;
   const int op = FE_LAPLACE;
   CgWork* w = nullptr;

@@ -182,7 +182,8 @@ extern "C" fe_status fe_apply_host(const fe_mesh* cm, int nop, const fe_op* ops,
     return FE_ERR_INVALID;
   }
   fe_mesh* m = const_cast<fe_mesh*>(cm);
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   FE_TRY(ensure_staging(m, nop));
   FE_TRY(fe_ensure_geometry(m, FE_F64, (flags & FE_NATIVE_F64) != 0));
   cudaStream_t st = (cudaStream_t)stream;

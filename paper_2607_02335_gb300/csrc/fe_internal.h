@@ -181,3 +181,16 @@ fe_status fe_launch_pairing(const fe_mesh* m, int prec, const void* a, const voi
                             double* out, cudaStream_t st);
 
 static inline bool fe_aligned(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Switches the calling thread to a mesh's device for the duration of an entry point and restores
+// the caller's current device when the entry point returns.
+struct FeDeviceGuard {
+  int prev = -1;
+  cudaError_t set(int dev) {
+    if (prev < 0 && cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    return cudaSetDevice(dev);
+  }
+  ~FeDeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};

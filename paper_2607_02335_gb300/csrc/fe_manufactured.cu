@@ -309,7 +309,8 @@ extern "C" fe_status fe_rhs(const fe_mesh* m, int kind, double* b, void* stream)
     fe_set_error("fe_rhs: FE_LAYOUT_CELLS meshes only");
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   return dispatch<false>(m, kind, nullptr, b, (cudaStream_t)stream);
 }
 
@@ -327,7 +328,8 @@ extern "C" fe_status fe_l2_error(const fe_mesh* m, int kind, const double* u, do
     fe_set_error("fe_l2_error: FE_LAYOUT_CELLS meshes only");
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   double* tmp = nullptr;
   FE_CUDA(cudaMallocAsync(&tmp, (m->ncells + 1) * sizeof(double), st), "fe_l2_error scratch");

@@ -224,7 +224,8 @@ extern "C" fe_status fe_mb_create(const fe_mb_desc* d, void* stream, fe_mbmesh**
       return FE_ERR_INVALID;
     }
   }
-  FE_CUDA(cudaSetDevice(d->device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(d->device), "cudaSetDevice");
   fe_mbmesh* M = new (std::nothrow) fe_mbmesh();
   if (!M) {
     fe_set_error("fe_mb_create: host allocation failed");
@@ -521,7 +522,8 @@ extern "C" fe_status fe_mb_create(const fe_mb_desc* d, void* stream, fe_mbmesh**
 
 extern "C" fe_status fe_mb_destroy(fe_mbmesh* M) {
   if (!M) return FE_OK;
-  cudaSetDevice(M->device);
+  FeDeviceGuard device_guard;
+  device_guard.set(M->device);
   cudaDeviceSynchronize();
   free_mb(M);
   return FE_OK;
@@ -587,7 +589,8 @@ static fe_status mb_check(const fe_mbmesh* M, fe_prec prec, const void* a, const
 extern "C" fe_status fe_mb_dss(const fe_mbmesh* M, fe_prec prec, const void* r, void* z,
                                void* stream) {
   FE_TRY(mb_check(M, prec, r, z, "fe_mb_dss"));
-  FE_CUDA(cudaSetDevice(M->device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(M->device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = prec == FE_F64 ? sizeof(double) : sizeof(float);
   if (r != z)
@@ -613,7 +616,8 @@ extern "C" fe_status fe_mb_apply(const fe_mbmesh* M, fe_op op, fe_prec prec, con
     fe_set_error("fe_mb_apply: x and y overlap");
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(M->device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(M->device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   const bool native = (flags & FE_NATIVE_F64) && prec == FE_F64;
   const long long n3 = (long long)M->n * M->n * M->n;

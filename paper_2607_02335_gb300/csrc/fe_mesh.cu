@@ -458,7 +458,8 @@ fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void
     fe_set_error("fe_mesh_create: mesh too large");
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(d->device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(d->device), "cudaSetDevice");
   fe_mesh* m = new (std::nothrow) fe_mesh();
   if (!m) {
     fe_set_error("fe_mesh_create: host allocation failed");
@@ -549,7 +550,8 @@ fe_status fe_mesh_create_impl(const fe_mesh_desc* d, const double* corners, void
 
 extern "C" fe_status fe_mesh_destroy(fe_mesh* m) {
   if (!m) return FE_OK;
-  cudaSetDevice(m->d.device);
+  FeDeviceGuard device_guard;
+  device_guard.set(m->d.device);
   cudaDeviceSynchronize();  // the mesh may have been used on any stream
   free_mesh(m, nullptr);
   cudaDeviceSynchronize();

@@ -419,7 +419,8 @@ extern "C" fe_status fe_serve_destroy(fe_server* S) {
     S->cv.notify_all();
   }
   if (S->worker.joinable()) S->worker.join();
-  cudaSetDevice(S->device);
+  FeDeviceGuard device_guard;
+  device_guard.set(S->device);
   for (auto& kv : S->reqs) {
     if (kv.second->mesh) release_request(S, kv.second);
     delete kv.second;

@@ -366,7 +366,8 @@ static fe_status face_call(const fe_mesh* m, fe_prec prec, const void* v, int si
                  what);
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   return face_op(m, (int)prec, const_cast<void*>(v), side, const_cast<void*>(plane), add,
                  (cudaStream_t)stream);
 }
@@ -389,7 +390,8 @@ extern "C" fe_status fe_slab_dss(const fe_mesh* m, fe_prec prec, const void* r, 
     fe_set_error("fe_slab_dss: null or misaligned vector, or precision not FE_F64/FE_F32");
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   if (r != z)
     FE_CUDA(cudaMemcpyAsync(z, r, (size_t)m->ncw * (prec == FE_F64 ? 8 : 4),
@@ -424,7 +426,8 @@ extern "C" fe_status fe_slab_cg_solve(const fe_mesh* m, const double* b, double*
   }
   FE_TRY(check_comm(m, comm, true, "fe_slab_cg_solve"));
   std::memset(res, 0, sizeof(*res));
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   FE_TRY(fe_ensure_geometry(m, FE_F64, false));
   const long long n = m->ncw;
   SlabWork W;

@@ -26,32 +26,31 @@
 
 static __device__ __align__(256) double g_pairing_partials[FE_PAIRING_NOALLOC_MAX_PARTIALS];
 
-// one partial per CTA over its chunk [blockIdx.x * CHUNK, min(n, (blockIdx.x + 1) * CHUNK))
+// one partial per CTA over its chunk [blockIdx.x * CHUNK, min(n, (blockIdx.x + 1) * CHUNK)),
+// binary64 products and sums as in fe_pairing
 template <class S>
 __global__ void __launch_bounds__(RED_THREADS)
     k_pairing_chunk(const S* __restrict__ a, const S* __restrict__ b, long long n,
                     double* __restrict__ partials) {
-  __shared__ dw sh[32];
+  __shared__ double sh[32];
   const long long lo = (long long)blockIdx.x * FE_PAIRING_NOALLOC_CHUNK;
   long long hi = lo + FE_PAIRING_NOALLOC_CHUNK;
   if (hi > n) hi = n;
-  dw acc = {0.0f, 0.0f};
+  double acc = 0.0;
   for (long long e = lo + threadIdx.x; e < hi; e += RED_THREADS)
-    acc = dw_mac(acc, to_dw<S>(__ldg(a + e)), to_dw<S>(__ldg(b + e)));
-  acc = dw_norm(acc);
-  acc = block_reduce_dw(acc, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = dw_to_double(acc);
+    acc = fma((double)__ldg(a + e), (double)__ldg(b + e), acc);
+  acc = block_reduce_f64(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
 // sum of the first nparts partials in a fixed order
 __global__ void __launch_bounds__(RED_THREADS)
     k_pairing_chunk_sum(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
-  __shared__ dw sh[32];
-  dw acc = {0.0f, 0.0f};
-  for (int i = threadIdx.x; i < nparts; i += RED_THREADS)
-    acc = dw_add(acc, dw_from_double(partials[i]));
-  acc = block_reduce_dw(acc, sh);
-  if (threadIdx.x == 0) out[0] = dw_to_double(acc);
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += RED_THREADS) acc += partials[i];
+  acc = block_reduce_f64(acc, sh);
+  if (threadIdx.x == 0) out[0] = acc;
 }
 
 // device address of the static array, looked up once per device with that device current
@@ -94,7 +93,8 @@ extern "C" fe_status fe_pairing_noalloc(const fe_mesh* m, fe_prec prec, const vo
                  n, (long long)FE_PAIRING_NOALLOC_MAX_PARTIALS * FE_PAIRING_NOALLOC_CHUNK);
     return FE_ERR_INVALID;
   }
-  FE_CUDA(cudaSetDevice(m->d.device), "cudaSetDevice");
+  FeDeviceGuard device_guard;
+  FE_CUDA(device_guard.set(m->d.device), "cudaSetDevice");
   double* scratch = nullptr;
   FE_TRY(scratch_for_device(m->d.device, &scratch));
   cudaStream_t st = (cudaStream_t)stream;

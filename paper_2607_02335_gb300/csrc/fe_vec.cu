@@ -490,37 +490,34 @@ fe_status fe_launch_diag(const fe_mesh* m, int op, double* d, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Deterministic reductions.  A fixed grid of RED_BLOCKS CTAs strides over the vector; each
-// thread accumulates in double-word arithmetic, the CTA reduces in a fixed shuffle tree and
-// writes one FP64 partial per CTA; a one-CTA kernel sums the partials in a fixed order.  The
-// result depends only on the data, never on timing.
+// Deterministic reductions.  A fixed grid of RED_BLOCKS CTAs strides over the vector; each thread
+// accumulates its products in binary64 (the FP64 pipe: one fma per entry, the whole binary64
+// range), the CTA reduces in a fixed shuffle tree and writes one partial per CTA, and a one-CTA
+// kernel sums the partials in a fixed order.  The result depends only on the data, never on
+// timing.
 // ---------------------------------------------------------------------------------------------
-// partials[slot * RED_BLOCKS + block] = sum over the CTA's stride of a_e * b_e
+// partials[block] = sum over the CTA's stride of a_e * b_e
 template <class S>
 __global__ void __launch_bounds__(RED_THREADS)
     k_pairing_partial(const S* __restrict__ a, const S* __restrict__ b, long long n,
                       double* __restrict__ partials) {
-  __shared__ dw sh[32];
-  dw acc = {0.0f, 0.0f};
+  __shared__ double sh[32];
+  double acc = 0.0;
   for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n;
        e += (long long)RED_BLOCKS * RED_THREADS)
-    acc = dw_mac(acc, to_dw<S>(__ldg(a + e)), to_dw<S>(__ldg(b + e)));
-  acc = dw_norm(acc);
-  acc = block_reduce_dw(acc, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = dw_to_double(acc);
+    acc = fma((double)__ldg(a + e), (double)__ldg(b + e), acc);
+  acc = block_reduce_f64(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// sum of RED_BLOCKS partials of each of `nslots` slots, in a fixed order
+// out[0] = sum of the nparts partials in a fixed order
 __global__ void __launch_bounds__(RED_THREADS)
-    k_partials_sum(const double* __restrict__ partials, int nslots, double* __restrict__ out) {
-  __shared__ dw sh[32];
-  for (int s = 0; s < nslots; ++s) {
-    dw acc = {0.0f, 0.0f};
-    for (int b = threadIdx.x; b < RED_BLOCKS; b += RED_THREADS)
-      acc = dw_add(acc, dw_from_double(partials[s * RED_BLOCKS + b]));
-    acc = block_reduce_dw(acc, sh);
-    if (threadIdx.x == 0) out[s] = dw_to_double(acc);
-  }
+    k_partials_sum64(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += RED_THREADS) acc += partials[b];
+  acc = block_reduce_f64(acc, sh);
+  if (threadIdx.x == 0) out[0] = acc;
 }
 
 fe_status fe_ensure_reduction(const fe_mesh* cm) {
@@ -547,6 +544,6 @@ fe_status fe_launch_pairing(const fe_mesh* m, int prec, const void* a, const voi
     fe_set_error("pairing: unsupported precision %d", prec);
     return FE_ERR_INVALID;
   }
-  k_partials_sum<<<1, RED_THREADS, 0, st>>>(m->red, 1, out);
+  k_partials_sum64<<<1, RED_THREADS, 0, st>>>(m->red, RED_BLOCKS, out);
   return fe_cuda_check(cudaGetLastError(), "pairing launch");
 }

@@ -35,3 +35,20 @@ template <>
 __device__ __forceinline__ dw to_dw<double>(double v) { return dw_from_double(v); }
 template <>
 __device__ __forceinline__ dw to_dw<float>(float v) { return {v, 0.0f}; }
+
+// CTA-wide binary64 sum in a fixed shuffle tree; result valid in thread 0
+__device__ __forceinline__ double block_reduce_f64(double v, double* sh /* [32] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (wid == 0) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  }
+  __syncthreads();
+  return v;
+}

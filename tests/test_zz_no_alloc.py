@@ -3,6 +3,8 @@ device memory (their memory is all in their own pool, or an allocation's possibl
 synchronization is not acceptable on their path).  It must agree with fe_pairing, the entry point
 whose partial sums live in library-allocated scratch, on consecutive calls that share the static
 scratch array.  This file is collected last so that a failure here comes after every other test."""
+import math
+
 import numpy as np
 import pytest
 
@@ -47,4 +49,33 @@ def test_noalloc_pairing_rejects_meshes_beyond_its_scratch():
     with pytest.raises(fe.FeError) as e:
         fe.fe_pairing_noalloc(gm.handle, fe.FE_F64, small, small, out)
     assert e.value.status == fe.FE_ERR_INVALID and "static scratch limit" in str(e.value)
+    gm.close()
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-18, 1e18])
+def test_noalloc_pairing_against_host_fp64_sum_without_allocating(scale):
+    """Both pairings against an exactly rounded host sum (math.fsum) of the FP64 products, with
+    the inputs scaled far outside the float range; the device's free memory and the caching
+    allocator's reservation are the same before and after the no-allocation calls."""
+    from paper_2607_02335_gb300 import fe
+
+    m, p = (5, 4, 3), 3
+    gm = fe.Mesh(m, p, geom_mode=fe.FE_GEOM_AFFINE)
+    an = S.dual_cellwise(m, p, seed=21) * scale
+    bn = S.dual_cellwise(m, p, seed=22) * scale
+    ref = math.fsum((an * bn).tolist())
+    mag = math.fsum(np.abs(an * bn).tolist())
+    a = torch.from_numpy(an).cuda()
+    b = torch.from_numpy(bn).cuda()
+    _pair(fe, gm, fe.FE_F64, a, b, fe.fe_pairing_noalloc)  # first call on the device: set-up
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    for _ in range(2):
+        fe.fe_pairing_noalloc(gm.handle, fe.FE_F64, a, b, out)
+        torch.cuda.synchronize()
+        assert abs(out.item() - ref) <= 1e-14 * mag, scale
+    assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_reserved() == reserved0
+    got = _pair(fe, gm, fe.FE_F64, a, b, fe.fe_pairing)
+    assert abs(got - ref) <= 1e-14 * mag, scale
     gm.close()
