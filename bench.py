@@ -65,7 +65,8 @@ def parse():
                          "hanging_node_dss, slab_decomposition, solve_mixed_vs_fp64, batched, "
                          "serving")
     ap.add_argument("--profile-case", default=None,
-                    help="p,m,op: only run K+W applies of one case (for profiler captures)")
+                    help="p,m,op[,vol[,f64|f32|bf16|fp16]]: only run K+W applies of one case "
+                         "(for profiler captures)")
     args = ap.parse_args()
     if args.extras != "all":
         unknown = set(args.extras.split(",")) - set(EXTRAS)
@@ -739,7 +740,8 @@ def multiblock_dss(fe, torch, flush, stream, m=32, p=3, reps=20):
 
 def reduced_precision_apply(fe, torch, flush, stream, m=96, p=3, reps=10):
     """Volumetric apply of the Q3 96^3 deformed mesh in the reduced-precision arithmetics of the
-    inner solves: FP32, and 16-bit operands with FP32 accumulation (16-bit metric)."""
+    inner solves: FP32 (FMA pipe), and 16-bit operands with FP32 accumulation (16-bit metric) on
+    the tensor cores (mma.sync, the default for n <= 4) and on the FMA pipe (FE_LOWP_FMA=1)."""
     from paper_2607_02335_gb300 import synth as S
 
     peak, _ = load_peaks()
@@ -747,25 +749,38 @@ def reduced_precision_apply(fe, torch, flush, stream, m=96, p=3, reps=10):
     x = gm.gather(S.primal_unique(m, p, seed=0)).float()
     y = gm.empty(fe.FE_F32)
     out = []
-    for name, prec, gbytes in (("fp32", fe.FE_F32, 4), ("bf16_f32acc", fe.FE_BF16_F32ACC, 2),
-                               ("fp16_f32acc", fe.FE_F16_F32ACC, 2)):
-        for op in (fe.FE_LAPLACE, fe.FE_MASS):
-            fe.fe_apply(gm.handle, op, prec, x, y, 0, stream)
-            ts = []
-            for _ in range(reps):
-                flush.fill_(1.0)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
+    cases = (("fp32", fe.FE_F32, 4, "fma_pipe"),
+             ("bf16_f32acc", fe.FE_BF16_F32ACC, 2, "tensor_cores_mma_sync"),
+             ("bf16_f32acc", fe.FE_BF16_F32ACC, 2, "fma_pipe"),
+             ("fp16_f32acc", fe.FE_F16_F32ACC, 2, "tensor_cores_mma_sync"),
+             ("fp16_f32acc", fe.FE_F16_F32ACC, 2, "fma_pipe"))
+    for name, prec, gbytes, engine in cases:
+        force_fma = engine == "fma_pipe" and prec != fe.FE_F32
+        if force_fma:
+            os.environ["FE_LOWP_FMA"] = "1"
+        try:
+            for op in (fe.FE_LAPLACE, fe.FE_MASS):
                 fe.fe_apply(gm.handle, op, prec, x, y, 0, stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            ms = float(np.median(ts))
-            alg = gm.cellwise_len * (8 + (6 if op == fe.FE_LAPLACE else 1) * gbytes)
-            out.append({"arith": name, "op": "laplace" if op == fe.FE_LAPLACE else "mass",
-                        "case": f"Q{p} {m}^3", "volumetric_ms": round(ms, 4),
-                        "alg_bytes_per_cellwise_dof": alg // gm.cellwise_len,
-                        "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)})
+                ts = []
+                for _ in range(reps):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fe.fe_apply(gm.handle, op, prec, x, y, 0, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = float(np.median(ts))
+                alg = gm.cellwise_len * (8 + (6 if op == fe.FE_LAPLACE else 1) * gbytes)
+                out.append({"arith": name, "engine": engine,
+                            "op": "laplace" if op == fe.FE_LAPLACE else "mass",
+                            "case": f"Q{p} {m}^3", "volumetric_ms": round(ms, 4),
+                            "alg_bytes_per_cellwise_dof": alg // gm.cellwise_len,
+                            "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)})
+        finally:
+            if force_fma:
+                del os.environ["FE_LOWP_FMA"]
     del x, y
     gm.close()
     return out
@@ -937,8 +952,8 @@ def serving_run(fe, mixed, n_req, rate, budget_gb, slots, cap_s, seed=0):
 
 
 def run_profile_case(args):
-    """One (degree, cells, operator[, vol]) case applied W+K times with FE_ASSEMBLE (vol: the
-    volumetric apply alone); no timing."""
+    """One (degree, cells, operator[, vol[, arithmetic]]) case applied W+K times with FE_ASSEMBLE
+    (vol: the volumetric apply alone; arithmetic f64 (default), f32, bf16 or fp16); no timing."""
     import torch
 
     from paper_2607_02335_gb300 import fe
@@ -947,12 +962,17 @@ def run_profile_case(args):
     parts = args.profile_case.split(",")
     p, m, opname = int(parts[0]), int(parts[1]), parts[2]
     flags = 0 if len(parts) > 3 and parts[3] == "vol" else fe.FE_ASSEMBLE
+    arith = parts[4] if len(parts) > 4 else "f64"
+    prec = {"f64": fe.FE_F64, "f32": fe.FE_F32, "bf16": fe.FE_BF16_F32ACC,
+            "fp16": fe.FE_F16_F32ACC}[arith]
     op = fe.FE_LAPLACE if opname == "laplace" else fe.FE_MASS
     gm = fe.Mesh(m, p, deform_amp=AMP)
     x = gm.gather(S.primal_unique(m, p, seed=0))
-    y = gm.empty()
+    if prec != fe.FE_F64:
+        x = x.float()
+    y = gm.empty(fe.FE_F64 if prec == fe.FE_F64 else fe.FE_F32)
     for _ in range(args.warmup + args.steps):
-        fe.fe_apply(gm.handle, op, fe.FE_F64, x, y, flags)
+        fe.fe_apply(gm.handle, op, prec, x, y, flags)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile_case, "launches": args.warmup + args.steps}))
 

@@ -56,10 +56,13 @@ typedef enum { FE_LAPLACE = 0, FE_MASS = 1 } fe_op;
 
 /* Arithmetic of a call.  FE_F64: double storage, FP64-accurate arithmetic (see FE_NATIVE_F64).
  * FE_F32: float storage and float arithmetic.  FE_BF16_F32ACC / FE_F16_F32ACC: float vectors, but
- * every operand of a product in the contractions (the input, intermediate sweep values, the 1D
- * matrices and the stored metric, kept in the 16-bit format scaled by a power of two) is rounded
- * to bf16 / fp16 and the products accumulate in FP32 (Sec. 3.2's reduced-precision
- * preconditioner; stored geometry only). */
+ * every operand of a product in the contractions is rounded to bf16 / fp16 and the products
+ * accumulate in FP32 (Sec. 3.2's reduced-precision preconditioner; stored geometry only; the
+ * stored metric is kept in the 16-bit format scaled by a power of two).  For n = p+1 = 2..4 on
+ * FE_LAYOUT_CELLS meshes the contractions run on the tensor cores as two dense products per cell
+ * (the 3n^3 x n^3 Kronecker gradient matrix, or the n^3 x n^3 interpolation matrix for mass,
+ * entries rounded once; the metric product in FP32); otherwise, or with FE_LOWP_FMA=1 in the
+ * environment, as sum-factorized sweeps on the FMA pipe with every sweep value rounded. */
 typedef enum { FE_F64 = 0, FE_F32 = 1, FE_BF16_F32ACC = 2, FE_F16_F32ACC = 3 } fe_prec;
 
 /* Geometry representation (Sec. 2.3 and Sec. 6.2: "per-quadrature-point Jacobians"):
@@ -149,7 +152,8 @@ fe_status fe_apply_host(const fe_mesh* mesh, int nop, const fe_op* ops, const do
  * With FE_ASSEMBLE the structured DSS follows (Sec. 4.1): y = S(A x), continuous.  x and y must
  * not overlap.  x and y are float arrays for every prec but FE_F64.  FE_BF16_F32ACC /
  * FE_F16_F32ACC need FE_GEOM_STORED (else FE_ERR_INVALID); their first call on a mesh builds the
- * 16-bit metric from the FP64 one.  Assembled applies at degree <= 3 sum the x/y interfaces
+ * 16-bit metric from the FP64 one (and, for n <= 4, the operand tables of the tensor-core
+ * kernels).  Assembled applies at degree <= 3 (but the tensor-core ones) sum the x/y interfaces
  * inside bricks of cells in the kernel, and on large meshes also the z-interfaces inside chunks
  * of z-layers (the environment variable FE_ZCARRY_CHUNK=k forces k layers per chunk, 0 or 1
  * none); the result is bitwise the same either way. */

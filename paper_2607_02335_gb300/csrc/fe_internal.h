@@ -55,6 +55,8 @@ struct fe_mesh {
   float* geo32 = nullptr;
   unsigned short* geo16[2] = {nullptr, nullptr};  // bf16 / fp16 metric, scaled by gscale[op]
   float gscale[2] = {1.0f, 1.0f};                 // powers of two: Laplace terms, w detJ
+  // fragment tables of the tensor-core 16-bit kernels [bf16, fp16][Laplace, mass] (n = 2..4)
+  unsigned* kron_tab[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool tri = false;  // a block of a block-structured mesh (trilinear map of its corners)
   // slab of a larger structured mesh (fe_slab_create): d.mz is the slab's own layer count, the
   // slab starts at global layer zoff of mzg, and has neighbouring slabs below / above when
@@ -155,6 +157,12 @@ fe_status fe_launch_apply_f64native(const ApplyLaunch& a);
 fe_status fe_launch_apply_f32(const ApplyLaunch& a);
 // FE_BF16_F32ACC / FE_F16_F32ACC: float vectors, 16-bit operands, stored geometry only
 fe_status fe_launch_apply_lowp(const ApplyLaunch& a, int prec);
+// the same on the tensor cores (mma.sync, fe_apply_kron.cu) for unpacked stored-geometry meshes
+// of n = 2..4; FE_LOWP_FMA=1 in the environment selects the FMA-pipe kernels instead
+bool fe_kron_eligible(const fe_mesh* m);
+bool fe_kron_supported(const fe_mesh* m);
+fe_status fe_kron_build_tables(fe_mesh* m, int prec);  // with the 16-bit metric, on m->st
+fe_status fe_launch_apply_kron(const ApplyLaunch& a, int prec);
 
 // dss / vectors (fe_dss.cu)
 fe_status fe_launch_dss(const fe_mesh* m, int prec, void* v, cudaStream_t st);

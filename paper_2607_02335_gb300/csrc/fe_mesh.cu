@@ -322,7 +322,7 @@ fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
   const long long n = m->ncells * FE_GEO_COMPS * m->n3;
   if (prec == FE_BF16_F32ACC || prec == FE_F16_F32ACC) {
     const int k = prec == FE_BF16_F32ACC ? 0 : 1;
-    if (m->geo16[k]) return FE_OK;
+    if (m->geo16[k]) return fe_kron_build_tables(m, prec);
     if (!m->geo64) {
       fe_set_error("16-bit metric: the FP64 metric of this mesh has been released");
       return FE_ERR_INVALID;
@@ -350,7 +350,7 @@ fe_status fe_ensure_geometry(const fe_mesh* cm, int prec, bool native) {
       k_to_h16<false><<<grid_for(n, 256), 256, 0, m->st>>>(m->geo64, m->geo16[k], n, (int)m->n3,
                                                            m->gscale[0], m->gscale[1]);
     FE_CUDA(cudaStreamSynchronize(m->st), "metric (16-bit) copy");
-    return FE_OK;
+    return fe_kron_build_tables(m, prec);
   }
   if ((prec == FE_F64 && !native && !m->geodw) || (prec == FE_F32 && !m->geo32) ||
       (prec == FE_F64 && native && !m->geo64)) {
@@ -386,7 +386,8 @@ static void free_mesh(fe_mesh* m, cudaStream_t st) {
                   m->rc_scratch[1], m->rc_scratch[2], m->diag64[0],
                   m->diag64[1], m->invdiag32[0], m->invdiag32[1], m->invdiag64[0],
                   m->invdiag64[1], m->invmult64, m->red, m->hs_xu, m->hs_xc, m->hs_yc,
-                  m->hs_yu[0], m->hs_yu[1]};
+                  m->hs_yu[0], m->hs_yu[1], m->kron_tab[0][0], m->kron_tab[0][1],
+                  m->kron_tab[1][0], m->kron_tab[1][1]};
   for (void* b : bufs) fe_dfree(b, st);
   for (cudaEvent_t e : m->hs_ev)
     if (e) cudaEventDestroy(e);
