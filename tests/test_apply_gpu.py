@@ -257,6 +257,31 @@ def test_smooth_input_accuracy(fe, p):
         assert rel_max_err(to_host(gm.apply(x, op=op, flags=fe.FE_ASSEMBLE)), ya) <= TOL64, (p, op)
 
 
+@pytest.mark.parametrize("p,m", [(3, 48), (7, 16)])
+def test_smooth_input_at_larger_sizes(fe, p, m):
+    """At finer meshes the local Laplacian of a smooth field amplifies input rounding by about
+    p^4/h, and FP64 evaluations in different orders (native sum factorization, the oracle's
+    element matrices) drift apart towards 1e-12.  The double-word path must stay as close to the
+    oracle as native FP64 is (sampled cells against the oracle's element matrices)."""
+    om = oracle_mesh(m, p, amp=0.1)
+    gm = fe.Mesh(m, p, deform_amp=0.1)
+    xc = O.gather(om, O.exact_nodal(om, O.RHS_SINE))
+    n3, nc = (p + 1) ** 3, m ** 3
+    x = torch.from_numpy(xc).cuda()
+    for op in (fe.FE_LAPLACE, fe.FE_MASS):
+        y = to_host(gm.apply(x, op=op))
+        yn = to_host(gm.apply(x, op=op, flags=fe.FE_NATIVE_F64))
+        den = np.abs(y).max()
+        e_dw = e_nat = 0.0
+        for c0 in (0, nc // 3, nc // 2 + m * m // 2 + m // 2, nc - 8):
+            yr = O.apply_local_mats(om, c0, O.element_matrices(om, op, c0, 8),
+                                    xc[c0 * n3:(c0 + 8) * n3])
+            e_dw = max(e_dw, np.abs(y[c0 * n3:(c0 + 8) * n3] - yr).max() / den)
+            e_nat = max(e_nat, np.abs(yn[c0 * n3:(c0 + 8) * n3] - yr).max() / den)
+        assert e_nat <= 3e-12, (p, m, op, e_nat)
+        assert e_dw <= max(1.5 * e_nat, TOL64), (p, m, op, e_dw, e_nat)
+
+
 @pytest.mark.parametrize("scale", [1e-300, 1e-30, 1e30, 1e300])
 def test_extreme_magnitudes(fe, scale):
     """The FP64 path scales each CTA's inputs by a power of two before the double-word arithmetic,
