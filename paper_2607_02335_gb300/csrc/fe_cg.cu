@@ -164,9 +164,20 @@ __global__ void __launch_bounds__(RED_THREADS)
   if (*(volatile const int*)&sc->done) return;
   __shared__ dw sh[32];
   dw acc = {0.0f, 0.0f};
-  for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n;
-       e += (long long)RED_BLOCKS * RED_THREADS)
-    acc = dw_add(acc, prod_dw<S>(q[e], p[e]));
+  constexpr long long STRIDE = (long long)RED_BLOCKS * RED_THREADS;
+  long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
+  // RED_U elements' loads in flight before their products join the accumulator, in the same order
+  for (; e + (RED_U - 1) * STRIDE < n; e += RED_U * STRIDE) {
+    S qv[RED_U], pv[RED_U];
+#pragma unroll
+    for (int u = 0; u < RED_U; ++u) {
+      qv[u] = q[e + u * STRIDE];
+      pv[u] = p[e + u * STRIDE];
+    }
+#pragma unroll
+    for (int u = 0; u < RED_U; ++u) acc = dw_add(acc, prod_dw<S>(qv[u], pv[u]));
+  }
+  for (; e < n; e += STRIDE) acc = dw_add(acc, prod_dw<S>(q[e], p[e]));
   acc = block_reduce_dw(acc, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = dw_to_double(acc);
 }
@@ -184,26 +195,44 @@ __global__ void __launch_bounds__(RED_THREADS)
   if (check_done && *(volatile const int*)&sc->done) return;
   __shared__ dw sh[32];
   dw a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
-  for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n;
-       e += (long long)RED_BLOCKS * RED_THREADS) {
-    const S we = w[e];
+  auto body = [&](long long e, S we, float im, S idg, S rv, S qv) {
     const dw w2 = prod_dw<S>(we, we);
-    const float im = invmult[e];  // a power of two or zero: exact scaling
-    a0 = dw_add(a0, {w2.h * im, w2.l * im});
+    a0 = dw_add(a0, {w2.h * im, w2.l * im});  // im: a power of two or zero, exact scaling
     if (z) {
-      const S ze = we * invdiag[e];
+      const S ze = we * idg;
       z[e] = ze;
       S re;
       if (redistribute) {
         re = we * (S)im;
         r[e] = re;
       } else {
-        re = r[e];
+        re = rv;
       }
       a1 = dw_add(a1, prod_dw<S>(re, ze));
-      if (q) a2 = dw_add(a2, prod_dw<S>(q[e], ze));
+      if (q) a2 = dw_add(a2, prod_dw<S>(qv, ze));
     }
+  };
+  constexpr long long STRIDE = (long long)RED_BLOCKS * RED_THREADS;
+  long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
+  // RED_U elements' loads in flight before they join the accumulators, in the same order
+  for (; e + (RED_U - 1) * STRIDE < n; e += RED_U * STRIDE) {
+    S wv[RED_U], idg[RED_U], rv[RED_U], qv[RED_U];
+    float im[RED_U];
+#pragma unroll
+    for (int u = 0; u < RED_U; ++u) {
+      const long long f = e + u * STRIDE;
+      wv[u] = w[f];
+      im[u] = invmult[f];
+      idg[u] = z ? invdiag[f] : S(0);
+      rv[u] = (z && !redistribute) ? r[f] : S(0);
+      qv[u] = (z && q) ? q[f] : S(0);
+    }
+#pragma unroll
+    for (int u = 0; u < RED_U; ++u) body(e + u * STRIDE, wv[u], im[u], idg[u], rv[u], qv[u]);
   }
+  for (; e < n; e += STRIDE)
+    body(e, w[e], invmult[e], z ? invdiag[e] : S(0), (z && !redistribute) ? r[e] : S(0),
+         (z && q) ? q[e] : S(0));
   a0 = block_reduce_dw(a0, sh);
   if (threadIdx.x == 0) partials[0 * RED_BLOCKS + blockIdx.x] = dw_to_double(a0);
   if (z) {

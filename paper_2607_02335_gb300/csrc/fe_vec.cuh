@@ -5,6 +5,7 @@
 #define RED_BLOCKS 608  // 4 CTAs per SM on 152 SMs; fixed, so reductions are reproducible
 #define RED_THREADS 256
 #define RED_SLOTS 8
+#define RED_U 4  // elements per thread whose loads are issued together in the reduction loops
 
 fe_status fe_ensure_reduction(const fe_mesh* m);
 
