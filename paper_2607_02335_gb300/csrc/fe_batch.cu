@@ -225,7 +225,15 @@ __global__ void __launch_bounds__(BT)
     const S* q = vec<S>(P, 4);
     const S* p = vec<S>(P, 3);
     dw acc = {0.0f, 0.0f};
-    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) acc = dw_add(acc, prod2<S>(q[e], p[e]));
+    long long e = C.lo + threadIdx.x;
+    for (; e + (RED_U - 1) * BT < C.hi; e += RED_U * BT) {  // loads first, same order
+      S qv[RED_U], pv[RED_U];
+#pragma unroll
+      for (int u = 0; u < RED_U; ++u) qv[u] = q[e + u * BT], pv[u] = p[e + u * BT];
+#pragma unroll
+      for (int u = 0; u < RED_U; ++u) acc = dw_add(acc, prod2<S>(qv[u], pv[u]));
+    }
+    for (; e < C.hi; e += BT) acc = dw_add(acc, prod2<S>(q[e], p[e]));
     acc = block_reduce_dw(acc, sh);
     if (threadIdx.x == 0) partials[(size_t)c * 4 + 0] = dw_to_double(acc);
   }
@@ -348,25 +356,42 @@ __global__ void __launch_bounds__(BT)
     const S* q = vec<S>(P, 4);
     const S* idg = (sizeof(S) == 8) ? (const S*)P.invdiag64 : (const S*)P.invdiag32;
     dw a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
-    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
-      const S we = w[e];
+    auto body = [&](long long e, S we, float im, S dg, S rv, S qv) {
       const dw w2 = prod2<S>(we, we);
-      const float im = P.invmult[e];
       a0 = dw_add(a0, {w2.h * im, w2.l * im});
       if (mode & 1) {
-        const S ze = we * idg[e];
+        const S ze = we * dg;
         z[e] = ze;
         S re;
         if (mode & 2) {
           re = we * (S)im;
           r[e] = re;
         } else {
-          re = r[e];
+          re = rv;
         }
         a1 = dw_add(a1, prod2<S>(re, ze));
-        if (mode & 4) a2 = dw_add(a2, prod2<S>(q[e], ze));
+        if (mode & 4) a2 = dw_add(a2, prod2<S>(qv, ze));
       }
+    };
+    long long e = C.lo + threadIdx.x;
+    for (; e + (RED_U - 1) * BT < C.hi; e += RED_U * BT) {  // loads first, same order
+      S wv[RED_U], dv[RED_U], rv[RED_U], qv[RED_U];
+      float im[RED_U];
+#pragma unroll
+      for (int u = 0; u < RED_U; ++u) {
+        const long long f = e + u * BT;
+        wv[u] = w[f];
+        im[u] = P.invmult[f];
+        dv[u] = (mode & 1) ? idg[f] : S(0);
+        rv[u] = ((mode & 1) && !(mode & 2)) ? r[f] : S(0);
+        qv[u] = ((mode & 1) && (mode & 4)) ? q[f] : S(0);
+      }
+#pragma unroll
+      for (int u = 0; u < RED_U; ++u) body(e + u * BT, wv[u], im[u], dv[u], rv[u], qv[u]);
     }
+    for (; e < C.hi; e += BT)
+      body(e, w[e], P.invmult[e], (mode & 1) ? idg[e] : S(0),
+           ((mode & 1) && !(mode & 2)) ? r[e] : S(0), ((mode & 1) && (mode & 4)) ? q[e] : S(0));
     a0 = block_reduce_dw(a0, sh);
     if (threadIdx.x == 0) partials[(size_t)c * 4 + 0] = dw_to_double(a0);
     if (mode & 1) {
