@@ -254,22 +254,33 @@ __global__ void __launch_bounds__(BT)
     const S* p = vec<S>(P, 3);
     const S* q = vec<S>(P, 4);
     S* w = vec<S>(P, 5);
-    if constexpr (sizeof(S) == 4) {  // FP32 state: FP32 arithmetic (the FP64 pipe is slow)
-      const float af = (float)a;
-      for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
-        u[e] = fmaf(af, p[e], u[e]);
-        const float re = fmaf(-af, q[e], r[e]);
-        r[e] = re;
-        w[e] = re;
+    // FP32 state: FP32 arithmetic (the FP64 pipe is slow).  RED_U elements' loads are issued
+    // before their stores (the vectors are distinct arrays)
+    auto step = [&](long long e, S ue, S pe, S qe, S rq) {
+      S re;
+      if constexpr (sizeof(S) == 4) {
+        const float af = (float)a;
+        u[e] = fmaf(af, pe, ue);
+        re = fmaf(-af, qe, rq);
+      } else {
+        u[e] = fma(a, pe, ue);
+        re = fma(-a, qe, rq);
       }
-    } else {
-      for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) {
-        u[e] = fma(a, p[e], u[e]);
-        const double re = fma(-a, q[e], r[e]);
-        r[e] = re;
-        w[e] = re;
+      r[e] = re;
+      w[e] = re;
+    };
+    long long e = C.lo + threadIdx.x;
+    for (; e + (RED_U - 1) * BT < C.hi; e += RED_U * BT) {
+      S uv[RED_U], pv[RED_U], qv[RED_U], rv[RED_U];
+#pragma unroll
+      for (int k = 0; k < RED_U; ++k) {
+        const long long f = e + k * BT;
+        uv[k] = u[f], pv[k] = p[f], qv[k] = q[f], rv[k] = r[f];
       }
+#pragma unroll
+      for (int k = 0; k < RED_U; ++k) step(e + k * BT, uv[k], pv[k], qv[k], rv[k]);
     }
+    for (; e < C.hi; e += BT) step(e, u[e], p[e], q[e], r[e]);
   }
 }
 
@@ -417,7 +428,15 @@ __global__ void __launch_bounds__(BT)
     const S b = (S)P.sc[slot].beta;
     S* p = vec<S>(P, 3);
     const S* z = vec<S>(P, 2);
-    for (long long e = C.lo + threadIdx.x; e < C.hi; e += BT) p[e] = z[e] + b * p[e];
+    long long e = C.lo + threadIdx.x;
+    for (; e + (RED_U - 1) * BT < C.hi; e += RED_U * BT) {  // loads before stores
+      S zv[RED_U], pv[RED_U];
+#pragma unroll
+      for (int k = 0; k < RED_U; ++k) zv[k] = z[e + k * BT], pv[k] = p[e + k * BT];
+#pragma unroll
+      for (int k = 0; k < RED_U; ++k) p[e + k * BT] = zv[k] + b * pv[k];
+    }
+    for (; e < C.hi; e += BT) p[e] = z[e] + b * p[e];
   }
 }
 
