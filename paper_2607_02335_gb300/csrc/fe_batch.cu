@@ -315,12 +315,33 @@ __device__ __forceinline__ void dss_row(S* __restrict__ v, int axis, int row, in
     rstep = (long long)mx * my;
     locL0 = P * N2, locR0 = 0, sa = 1, sb = N;
   }
-  for (int it = lane; it < items; it += 32) {
+  // RED_U pairs' loads in flight before their stores (pairs of a pass are disjoint)
+  auto addr = [&](int it, S*& pl, S*& pr) {
     const int g = it / N2, f = it - g * N2, fb = f / N, fa = f - fb * N;
     const long long L = first + (long long)g * lstep;
     const int off = fa * sa + fb * sb;
-    S* pl = v + L * N3 + locL0 + off;
-    S* pr = v + (L + rstep) * N3 + locR0 + off;
+    pl = v + L * N3 + locL0 + off;
+    pr = v + (L + rstep) * N3 + locR0 + off;
+  };
+  int it = lane;
+  for (; it + (RED_U - 1) * 32 < items; it += RED_U * 32) {
+    S *pl[RED_U], *pr[RED_U], l[RED_U], r[RED_U];
+#pragma unroll
+    for (int k = 0; k < RED_U; ++k) {
+      addr(it + k * 32, pl[k], pr[k]);
+      l[k] = *pl[k];
+      r[k] = *pr[k];
+    }
+#pragma unroll
+    for (int k = 0; k < RED_U; ++k) {
+      const S sum = l[k] + r[k];
+      *pl[k] = sum;
+      *pr[k] = sum;
+    }
+  }
+  for (; it < items; it += 32) {
+    S *pl, *pr;
+    addr(it, pl, pr);
     const S sum = *pl + *pr;
     *pl = sum;
     *pr = sum;
