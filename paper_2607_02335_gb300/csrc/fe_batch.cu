@@ -224,16 +224,26 @@ __global__ void __launch_bounds__(BT)
     if (*(volatile const int*)&P.sc[slot].done) continue;
     const S* q = vec<S>(P, 4);
     const S* p = vec<S>(P, 3);
+    // float: double-word sums of exact products; double: binary64 FMAs (one FP64-pipe operation
+    // per product costs less than converting both factors to double-word)
     dw acc = {0.0f, 0.0f};
+    double acc64 = 0.0;
+    auto add = [&](S a, S b) {
+      if constexpr (sizeof(S) == 8)
+        acc64 = fma(a, b, acc64);
+      else
+        acc = dw_add(acc, prod2<S>(a, b));
+    };
     long long e = C.lo + threadIdx.x;
     for (; e + (RED_U - 1) * BT < C.hi; e += RED_U * BT) {  // loads first, same order
       S qv[RED_U], pv[RED_U];
 #pragma unroll
       for (int u = 0; u < RED_U; ++u) qv[u] = q[e + u * BT], pv[u] = p[e + u * BT];
 #pragma unroll
-      for (int u = 0; u < RED_U; ++u) acc = dw_add(acc, prod2<S>(qv[u], pv[u]));
+      for (int u = 0; u < RED_U; ++u) add(qv[u], pv[u]);
     }
-    for (; e < C.hi; e += BT) acc = dw_add(acc, prod2<S>(q[e], p[e]));
+    for (; e < C.hi; e += BT) add(q[e], p[e]);
+    if constexpr (sizeof(S) == 8) acc = dw_from_double(acc64);
     acc = block_reduce_dw(acc, sh);
     if (threadIdx.x == 0) partials[(size_t)c * 4 + 0] = dw_to_double(acc);
   }

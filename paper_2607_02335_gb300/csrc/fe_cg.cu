@@ -156,6 +156,32 @@ __device__ __forceinline__ dw prod_dw<float>(float a, float b) {
   return {p, __fmaf_rn(a, b, -p)};
 }
 
+// A thread's running sum of products in a pairing: float vectors in double-word (exact products);
+// double vectors in binary64 FMAs on the FP64 pipe, one per product, which costs less than
+// converting both factors to double-word (the conversions were the kernels' issue bound)
+template <class S>
+struct Acc;
+template <>
+struct Acc<float> {
+  dw v = {0.0f, 0.0f};
+  __device__ __forceinline__ void add_prod(float a, float b) { v = dw_add(v, prod_dw<float>(a, b)); }
+  __device__ __forceinline__ dw value() const { return v; }
+};
+template <>
+struct Acc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ dw value() const { return dw_from_double(v); }
+};
+// double-word for both: the preconditioner kernel already spends its FP64-pipe share on z = w /
+// diag (measured: binary64 FMAs for <r,z> there made it slower, 165 -> 202 us at Q3 64^3)
+template <class S>
+struct AccDw {
+  dw v = {0.0f, 0.0f};
+  __device__ __forceinline__ void add_prod(S a, S b) { v = dw_add(v, prod_dw<S>(a, b)); }
+  __device__ __forceinline__ dw value() const { return v; }
+};
+
 // partial of <q, p>  (slot 0)
 template <class S>
 __global__ void __launch_bounds__(RED_THREADS)
@@ -163,7 +189,7 @@ __global__ void __launch_bounds__(RED_THREADS)
          const CgScal* __restrict__ sc, long long n) {
   if (*(volatile const int*)&sc->done) return;
   __shared__ dw sh[32];
-  dw acc = {0.0f, 0.0f};
+  Acc<S> acc;
   constexpr long long STRIDE = (long long)RED_BLOCKS * RED_THREADS;
   long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
   // RED_U elements' loads in flight before their products join the accumulator, in the same order
@@ -175,11 +201,11 @@ __global__ void __launch_bounds__(RED_THREADS)
       pv[u] = p[e + u * STRIDE];
     }
 #pragma unroll
-    for (int u = 0; u < RED_U; ++u) acc = dw_add(acc, prod_dw<S>(qv[u], pv[u]));
+    for (int u = 0; u < RED_U; ++u) acc.add_prod(qv[u], pv[u]);
   }
-  for (; e < n; e += STRIDE) acc = dw_add(acc, prod_dw<S>(q[e], p[e]));
-  acc = block_reduce_dw(acc, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = dw_to_double(acc);
+  for (; e < n; e += STRIDE) acc.add_prod(q[e], p[e]);
+  const dw accv = block_reduce_dw(acc.value(), sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = dw_to_double(accv);
 }
 
 // z = w * invdiag (when z != null); partials: slot 0 sum w^2 invmult, slot 1 <r,z>, slot 2 <q,z>
@@ -194,7 +220,8 @@ __global__ void __launch_bounds__(RED_THREADS)
               int check_done, int redistribute) {
   if (check_done && *(volatile const int*)&sc->done) return;
   __shared__ dw sh[32];
-  dw a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
+  dw a0 = {0.0f, 0.0f};
+  AccDw<S> a1, a2;
   auto body = [&](long long e, S we, float im, S idg, S rv, S qv) {
     const dw w2 = prod_dw<S>(we, we);
     a0 = dw_add(a0, {w2.h * im, w2.l * im});  // im: a power of two or zero, exact scaling
@@ -208,8 +235,8 @@ __global__ void __launch_bounds__(RED_THREADS)
       } else {
         re = rv;
       }
-      a1 = dw_add(a1, prod_dw<S>(re, ze));
-      if (q) a2 = dw_add(a2, prod_dw<S>(qv, ze));
+      a1.add_prod(re, ze);
+      if (q) a2.add_prod(qv, ze);
     }
   };
   constexpr long long STRIDE = (long long)RED_BLOCKS * RED_THREADS;
@@ -236,11 +263,11 @@ __global__ void __launch_bounds__(RED_THREADS)
   a0 = block_reduce_dw(a0, sh);
   if (threadIdx.x == 0) partials[0 * RED_BLOCKS + blockIdx.x] = dw_to_double(a0);
   if (z) {
-    a1 = block_reduce_dw(a1, sh);
-    if (threadIdx.x == 0) partials[1 * RED_BLOCKS + blockIdx.x] = dw_to_double(a1);
+    const dw v1 = block_reduce_dw(a1.value(), sh);
+    if (threadIdx.x == 0) partials[1 * RED_BLOCKS + blockIdx.x] = dw_to_double(v1);
     if (q) {
-      a2 = block_reduce_dw(a2, sh);
-      if (threadIdx.x == 0) partials[2 * RED_BLOCKS + blockIdx.x] = dw_to_double(a2);
+      const dw v2 = block_reduce_dw(a2.value(), sh);
+      if (threadIdx.x == 0) partials[2 * RED_BLOCKS + blockIdx.x] = dw_to_double(v2);
     }
   }
 }
