@@ -18,6 +18,11 @@ namespace {
 // coordinates and 64-bit offsets are formed once per CTA, the threads of the row use 32-bit
 // arithmetic with compile-time divisors.
 
+// Four elements per thread have their loads issued before their stores (HOST_U), and a select
+// CTA takes SEL_ROWS node rows: one row each (a few hundred nodes) left the CTAs too short.
+constexpr int HOST_U = 4;
+constexpr int SEL_ROWS = 8;
+
 // x_cell[e] = x_unique[global node of e], for the cells of row r = cz my + cy
 template <int N>
 __global__ void __launch_bounds__(256) k_expand(const double* __restrict__ xu,
@@ -30,33 +35,56 @@ __global__ void __launch_bounds__(256) k_expand(const double* __restrict__ xu,
   const double* src = xu + (cz * P * Ny + (long long)cy * P) * Nx;  // node (0, cy p, cz p)
   double* dst = xc + r * mx * N3;
   const int len = mx * N3;
-  for (int e = threadIdx.x; e < len; e += blockDim.x) {
+  auto from = [&](int e) {
     const int cx = e / N3, loc = e - cx * N3;
     const int k = loc / N2, j = (loc / N) % N, i = loc % N;
-    dst[e] = __ldg(src + (k * Ny + j) * Nx + cx * P + i);
+    return (k * Ny + j) * Nx + cx * P + i;
+  };
+  int e = threadIdx.x;
+  for (; e + (HOST_U - 1) * (int)blockDim.x < len; e += HOST_U * blockDim.x) {
+    double v[HOST_U];
+#pragma unroll
+    for (int u = 0; u < HOST_U; ++u) v[u] = __ldg(src + from(e + u * blockDim.x));
+#pragma unroll
+    for (int u = 0; u < HOST_U; ++u) dst[e + u * blockDim.x] = v[u];
   }
+  for (; e < len; e += blockDim.x) dst[e] = __ldg(src + from(e));
 }
 
 // y_unique[g] for the node layers gz0 <= gz < gz0 + nrows, row r = (gz - gz0) Ny + gy: along z the
 // copy in the lower cell (k = p) on a cell interface, so that a layer's nodes are final as soon as
 // the cell layers below them are; along x and y the copy in the upper cell (all copies are equal
-// once the DSS passes of the cell layer are done)
+// once the DSS passes of the cell layer are done).  CTA b takes rows [b SEL_ROWS, (b+1) SEL_ROWS).
 template <int N>
 __global__ void __launch_bounds__(256) k_select(const double* __restrict__ yc,
-                                                double* __restrict__ yu, int mx, int my, int gz0) {
+                                                double* __restrict__ yu, int mx, int my, int gz0,
+                                                long long nrows) {
   constexpr int P = N - 1, N3 = N * N * N;
   const int Nx = mx * P + 1, Ny = my * P + 1;
-  const long long r = blockIdx.x;
-  const int gy = (int)(r % Ny), gz = gz0 + (int)(r / Ny);
-  const int cy = gy / P < my ? gy / P : my - 1;
-  const int cz = (gz > 0 && gz % P == 0) ? gz / P - 1 : gz / P;
-  const int j = gy - cy * P, k = gz - cz * P;
-  const double* src = yc + ((long long)cz * my + cy) * mx * N3 + (k * N + j) * N;
-  double* dst = yu + ((long long)gz * Ny + gy) * Nx;
-  for (int gx = threadIdx.x; gx < Nx; gx += blockDim.x) {
+  const long long r0 = (long long)blockIdx.x * SEL_ROWS;
+  const int rows = nrows - r0 < SEL_ROWS ? (int)(nrows - r0) : SEL_ROWS;
+  const int len = rows * Nx;
+  auto from = [&](int e) {
+    const int rl = e / Nx, gx = e - rl * Nx;
+    const long long r = r0 + rl;
+    const int gy = (int)(r % Ny), gz = gz0 + (int)(r / Ny);
+    const int cy = gy / P < my ? gy / P : my - 1;
+    const int cz = (gz > 0 && gz % P == 0) ? gz / P - 1 : gz / P;
+    const int j = gy - cy * P, k = gz - cz * P;
     const int cx = gx / P < mx ? gx / P : mx - 1;
-    dst[gx] = __ldg(src + (long long)cx * N3 + (gx - cx * P));
+    return (((long long)cz * my + cy) * mx + cx) * N3 + (k * N + j) * N + (gx - cx * P);
+  };
+  // rows r0.. of layer gz0 + r / Ny are contiguous in y_unique from (gz0 Ny + r0) Nx on
+  double* dst = yu + ((long long)gz0 * Ny + r0) * Nx;
+  int e = threadIdx.x;
+  for (; e + (HOST_U - 1) * (int)blockDim.x < len; e += HOST_U * blockDim.x) {
+    double v[HOST_U];
+#pragma unroll
+    for (int u = 0; u < HOST_U; ++u) v[u] = __ldg(yc + from(e + u * blockDim.x));
+#pragma unroll
+    for (int u = 0; u < HOST_U; ++u) dst[e + u * blockDim.x] = v[u];
   }
+  for (; e < len; e += blockDim.x) dst[e] = __ldg(yc + from(e));
 }
 
 // expand the cell layers [z0, z1) (from node layers z0 p .. z1 p), or select the node layers
@@ -71,8 +99,9 @@ fe_status launch_expand_select(const fe_mesh* m, bool expand, const double* src,
     k_expand<N><<<(unsigned)((long long)my * (z1 - z0)), 256, 0, st>>>(
         src + (long long)z0 * p * row, dst + (long long)z0 * mx * my * m->n3, mx, my);
   } else {
-    k_select<N><<<(unsigned)((long long)(my * p + 1) * (z1 - z0)), 256, 0, st>>>(src, dst, mx, my,
-                                                                                 z0);
+    const long long nrows = (long long)(my * p + 1) * (z1 - z0);
+    k_select<N><<<(unsigned)((nrows + SEL_ROWS - 1) / SEL_ROWS), 256, 0, st>>>(src, dst, mx, my, z0,
+                                                                             nrows);
   }
   return fe_cuda_check(cudaGetLastError(), expand ? "expand launch" : "select launch");
 }
