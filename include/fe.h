@@ -221,8 +221,10 @@ fe_status fe_l2_error(const fe_mesh* mesh, int kind, const double* u, double* er
  * inner operator in 16-bit operands and FP32 accumulation (stored geometry only; inner vectors
  * stay FP32).  The FP32 iteration receives the residual assembled in FP64 and split evenly over
  * the copies of each node.  The FP64 residual of the returned x decides convergence.  b (dual)
- * and x (primal, in/out) are device arrays of cellwise_len doubles.  Synchronous: returns after
- * the solve. */
+ * and x (primal, in/out) are device arrays of cellwise_len doubles.  Every solve (this one, the
+ * batched and served ones, fe_slab_cg_solve) runs on the system scaled by an exact power of two
+ * that brings max|b| into [1, 2), and scales x back, so any finite scale of b behaves like unit
+ * size; a non-finite entry of b returns FE_ERR_INVALID.  Synchronous: returns after the solve. */
 typedef struct {
   double rtol;       /* relative residual target */
   int maxit;         /* iteration cap (inner iterations in total for mixed) */

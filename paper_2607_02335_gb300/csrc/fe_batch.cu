@@ -1027,17 +1027,20 @@ extern "C" fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes
   B.active.assign(nprob, 1);
   FE_CUDA(cudaMallocHost(&B.hsc, 2 * nprob * sizeof(CgScal)), "batch scalars");
   B.cap_hsc = 2 * nprob;
+  std::vector<double> sb(nprob, 1.0);
   for (int i = 0; i < nprob; ++i) {
     CgWork* w = nullptr;
     FE_TRY(fe_cg_get_work(meshes[i], mixed, &w));
     FE_TRY(fe_ensure_geometry(meshes[i], FE_F64, false));
     if (mixed) FE_TRY(fe_ensure_geometry(meshes[i], FE_F32, false));
     FE_TRY(fe_cg_ensure_diag(meshes[i], w, FE_LAPLACE));
+    // each problem scaled by its own exact power of two (fe_cg_rhs_scale), undone on x at the end
+    const long long ncw = meshes[i]->ncw;
+    FE_TRY(fe_cg_rhs_scale(w, b[i], ncw, &sb[i]));
+    FE_TRY(fe_cg_scale(b[i], w->bs, sb[i], ncw, w->st));
+    FE_TRY(fe_cg_scale(x[i], w->x, sb[i], ncw, w->st));
     FE_CUDA(cudaStreamSynchronize(w->st), "workspace set-up");
-    FE_CUDA(cudaMemcpyAsync(w->x, x[i], meshes[i]->ncw * sizeof(double), cudaMemcpyDeviceToDevice,
-                            B.st),
-            "batch copy x");
-    FE_TRY(fe_batch_fill(&B, i, meshes[i], w, b[i], opts));
+    FE_TRY(fe_batch_fill(&B, i, meshes[i], w, w->bs, opts));
   }
   B.any_flexible = (!mixed && opts->flexible) ? 1 : 0;
   FE_TRY(fe_batch_build(&B));
@@ -1045,9 +1048,7 @@ extern "C" fe_status fe_cg_solve_batched(int nprob, const fe_mesh* const* meshes
   FE_TRY(fe_batch_read(&B));
   fe_status worst = FE_OK;
   for (int i = 0; i < nprob; ++i) {
-    FE_CUDA(cudaMemcpyAsync(x[i], B.hp[i].x64, meshes[i]->ncw * sizeof(double),
-                            cudaMemcpyDeviceToDevice, B.st),
-            "batch copy x back");
+    FE_TRY(fe_cg_scale(B.hp[i].x64, x[i], 1.0 / sb[i], meshes[i]->ncw, B.st));
     const CgScal& o = B.hsc[2 * i];
     const CgScal& in = B.hsc[2 * i + 1];
     res[i].status = (fe_status)o.status;

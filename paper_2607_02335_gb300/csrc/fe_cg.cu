@@ -70,6 +70,23 @@ __global__ void k_residual(const double* __restrict__ b, const double* __restric
     r[e] = b[e] - q[e];
 }
 
+// largest |v| as the bit pattern of a non-negative double (whose order is the values' order)
+__global__ void k_absmax_bits(const double* __restrict__ v, long long n,
+                              unsigned long long* __restrict__ out) {
+  unsigned long long m = 0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)__double_as_longlong(v[e]) & 0x7FFFFFFFFFFFFFFFull);
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_scale_vec(const double* src, double* dst, double s, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = s * src[e];
+}
+
 // Inner right-hand side r32 = s * (S r) / mult, d32 = 0.  The dual residual r is unassembled: the
 // copies of a node hold partial integrals that cancel when summed, so near convergence single
 // copies are orders of magnitude larger than G^T r.  Rounding them to FP32 would destroy the
@@ -370,7 +387,7 @@ static void free_work(CgWork* w, cudaStream_t st) {
     if (w->g64[f]) cudaGraphExecDestroy(w->g64[f]);
     if (w->g32[f]) cudaGraphExecDestroy(w->g32[f]);
   }
-  void* bufs[] = {w->x, w->r, w->z, w->p, w->q, w->w, w->invdiag64, w->partials, w->hist,
+  void* bufs[] = {w->x, w->r, w->z, w->p, w->q, w->w, w->bs, w->invdiag64, w->partials, w->hist,
                   w->r32, w->z32, w->p32, w->q32, w->w32, w->d32, w->invdiag32, w->invmult, w->sc};
   for (void* b : bufs) fe_dfree(b, st);
   cudaFreeHost(w->hsc);
@@ -399,7 +416,7 @@ fe_status fe_cg_get_work(const fe_mesh* cm, bool mixed, CgWork** out) {
     const long long n = m->ncw;
     w->n = n;
     FE_CUDA(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking), "cg stream");
-    double** d[] = {&w->x, &w->r, &w->z, &w->p, &w->q, &w->w, &w->invdiag64};
+    double** d[] = {&w->x, &w->r, &w->z, &w->p, &w->q, &w->w, &w->bs, &w->invdiag64};
     for (double** v : d) FE_TRY(fe_dalloc((void**)v, n * sizeof(double), w->st, "cg vector"));
     FE_TRY(fe_dalloc((void**)&w->invdiag32, n * sizeof(float), w->st, "cg vector"));
     FE_TRY(fe_dalloc((void**)&w->invmult, n * sizeof(float), w->st, "cg vector"));
@@ -726,6 +743,38 @@ fe_status solve_reliable(const fe_mesh* m, CgWork* w, int op, const double* b, d
 
 }  // namespace
 
+fe_status fe_launch_absmax(const double* v, long long n, unsigned long long* out, cudaStream_t st) {
+  FE_CUDA(cudaMemsetAsync(out, 0, sizeof(*out), st), "absmax");
+  k_absmax_bits<<<grid_for(n), 256, 0, st>>>(v, n, out);
+  return fe_cuda_check(cudaGetLastError(), "absmax launch");
+}
+
+bool fe_scale_of_max(double mx, double* s) {
+  if (!std::isfinite(mx)) return false;
+  *s = mx > 0.0 ? std::ldexp(1.0, -std::ilogb(mx)) : 1.0;
+  return true;
+}
+
+fe_status fe_cg_rhs_scale(CgWork* w, const double* b, long long n, double* s) {
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(w->partials);
+  FE_TRY(fe_launch_absmax(b, n, d, w->st));
+  unsigned long long bits = 0;
+  FE_CUDA(cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, w->st), "rhs scale");
+  FE_CUDA(cudaStreamSynchronize(w->st), "rhs scale");
+  double mx;
+  std::memcpy(&mx, &bits, sizeof(mx));
+  if (!fe_scale_of_max(mx, s)) {
+    fe_set_error("cg: the right-hand side holds a non-finite value");
+    return FE_ERR_INVALID;
+  }
+  return FE_OK;
+}
+
+fe_status fe_cg_scale(const double* src, double* dst, double s, long long n, cudaStream_t st) {
+  k_scale_vec<<<grid_for(n), 256, 0, st>>>(src, dst, s, n);
+  return fe_cuda_check(cudaGetLastError(), "cg scale launch");
+}
+
 extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
                                  const fe_cg_opts* opts, fe_cg_result* res, void* stream) {
   if (!m || !b || !x || !opts || !res) {
@@ -797,8 +846,12 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
     w->g64_hist = hist;
   }
 
-  // u := x, ||G^T b||
-  FE_CUDA(cudaMemcpyAsync(w->x, x, n * sizeof(double), cudaMemcpyDeviceToDevice, w->st), "cg copy");
+  // the system scaled by an exact power of two (fe_cg_rhs_scale): b := sb b, u := sb x, ||G^T b||
+  double sb = 1.0;
+  FE_TRY(fe_cg_rhs_scale(w, b, n, &sb));
+  FE_TRY(fe_cg_scale(b, w->bs, sb, n, w->st));
+  FE_TRY(fe_cg_scale(x, w->x, sb, n, w->st));
+  b = w->bs;
   FE_TRY(set_scal(w, 0, opts->maxit, 0, opts->rtol));
   FE_TRY(residual_norm<double>(m, w, b, w->w, &w->sc[0], FIN_INIT_B));
   CgScal h;
@@ -844,7 +897,7 @@ extern "C" fe_status fe_cg_solve(const fe_mesh* m, const double* b, double* x,
   } else {
     FE_TRY(solve_reliable(m, w, op, b, bnorm2, opts, res, &status));
   }
-  FE_CUDA(cudaMemcpyAsync(x, w->x, n * sizeof(double), cudaMemcpyDeviceToDevice, w->st), "cg copy");
+  FE_TRY(fe_cg_scale(w->x, x, 1.0 / sb, n, w->st));  // 1/sb: a power of two, exact
   FE_CUDA(cudaStreamSynchronize(w->st), "cg synchronize");
   res->status = status;
   if (status == FE_ERR_NOT_CONVERGED) fe_set_error("fe_cg_solve: not converged");

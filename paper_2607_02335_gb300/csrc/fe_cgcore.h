@@ -85,6 +85,7 @@ __device__ __forceinline__ void fin_scalars(CgScal* sc, double rn2, double rz, d
 struct CgWork {
   long long n = 0;
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *w = nullptr;
+  double* bs = nullptr;  // the right-hand side scaled by the solve's power of two
   float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *w32 = nullptr,
         *d32 = nullptr;
   double* invdiag64 = nullptr;
@@ -105,4 +106,15 @@ struct CgWork {
 };
 
 fe_status fe_cg_get_work(const fe_mesh* m, bool mixed, CgWork** out);  // fe_cg.cu
+// The power of two 2^-e with e the binary exponent of max|b| (1 for b = 0): solves run on
+// 2^-e b and 2^-e x, exact scalings that keep the pairings' double-word sums (FP32's exponent
+// range) away from overflow and underflow whatever the scale of b.  FE_ERR_INVALID when b holds a
+// non-finite value.  Synchronizes w->st.
+fe_status fe_cg_rhs_scale(CgWork* w, const double* b, long long n, double* s);
+// *out = bit pattern of max|v| (a non-negative double), on st
+fe_status fe_launch_absmax(const double* v, long long n, unsigned long long* out, cudaStream_t st);
+// the power of two 2^-e with e the binary exponent of mx (1 for mx = 0); false if mx is not finite
+bool fe_scale_of_max(double mx, double* s);
+// dst = s src on st (src may equal dst)
+fe_status fe_cg_scale(const double* src, double* dst, double s, long long n, cudaStream_t st);
 fe_status fe_cg_ensure_diag(const fe_mesh* m, CgWork* w, int op);       // fe_cg.cu

@@ -42,6 +42,7 @@ struct Request {
   fe_mesh* mesh = nullptr;
   CgWork* w = nullptr;
   double* b_dev = nullptr;
+  double bscale = 1.0;  // the exact power of two the request's system is scaled by
   fe_cg_result result;
   std::vector<double> x_host;
 };
@@ -124,6 +125,9 @@ fe_status setup_request(fe_server* S, Request* r) {
                             r->w->st),
             "server rhs upload");
   }
+  // the request's system scaled by an exact power of two (fe_cg_rhs_scale); x0 = 0
+  FE_TRY(fe_cg_rhs_scale(r->w, r->b_dev, n, &r->bscale));
+  FE_TRY(fe_cg_scale(r->b_dev, r->b_dev, r->bscale, n, r->w->st));
   FE_CUDA(cudaMemsetAsync(r->w->x, 0, n * sizeof(double), r->w->st), "server x0");
   FE_CUDA(cudaStreamSynchronize(r->w->st), "server set-up");
   if (r->mesh->d.geom_mode == FE_GEOM_STORED) fe_mesh_drop_geo64(r->mesh, S->st);
@@ -150,6 +154,7 @@ void finish_request(fe_server* S, Request* r, fe_status st, const CgScal* sc) {
   }
   if (sc && r->w) {
     r->x_host.resize(r->mesh->ncw);
+    fe_cg_scale(r->w->x, r->w->x, 1.0 / r->bscale, r->mesh->ncw, S->st);  // exact: a power of two
     cudaMemcpyAsync(r->x_host.data(), r->w->x, r->mesh->ncw * sizeof(double), cudaMemcpyDeviceToHost,
                     S->st);
     cudaStreamSynchronize(S->st);

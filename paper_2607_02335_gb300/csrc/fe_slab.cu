@@ -20,6 +20,7 @@
 // slab sums the gathered values in rank order and takes the same decisions.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "fe_cgcore.h"
 #include "fe_vec.cuh"
@@ -292,13 +293,13 @@ __global__ void k_update(double* __restrict__ x, double* __restrict__ r, double*
 
 struct SlabWork {
   double *r = nullptr, *w = nullptr, *z = nullptr, *s = nullptr, *p = nullptr, *q = nullptr,
-         *invdiag = nullptr, *partials = nullptr, *hist = nullptr;
+         *invdiag = nullptr, *partials = nullptr, *hist = nullptr, *bs = nullptr;
   float* invmult = nullptr;
   CgScal* sc = nullptr;
   CgScal* hsc = nullptr;
   cudaStream_t st = nullptr;
   ~SlabWork() {
-    void* bufs[] = {r, w, z, s, p, q, invdiag, partials, hist, invmult, sc};
+    void* bufs[] = {r, w, z, s, p, q, invdiag, partials, hist, bs, invmult, sc};
     for (void* b : bufs) fe_dfree(b, st);
     if (st) cudaStreamSynchronize(st);
     if (hsc) cudaFreeHost(hsc);
@@ -433,7 +434,7 @@ extern "C" fe_status fe_slab_cg_solve(const fe_mesh* m, const double* b, double*
   SlabWork W;
   W.st = (cudaStream_t)stream;
   cudaStream_t st = W.st;
-  double** vecs[] = {&W.r, &W.w, &W.z, &W.s, &W.p, &W.q, &W.invdiag};
+  double** vecs[] = {&W.r, &W.w, &W.z, &W.s, &W.p, &W.q, &W.invdiag, &W.bs};
   for (double** v : vecs) FE_TRY(fe_dalloc((void**)v, n * sizeof(double), st, "slab cg vector"));
   FE_TRY(fe_dalloc((void**)&W.invmult, n * sizeof(float), st, "slab cg vector"));
   FE_TRY(fe_dalloc((void**)&W.partials, 3 * RED_BLOCKS * sizeof(double), st, "slab cg partials"));
@@ -453,6 +454,32 @@ extern "C" fe_status fe_slab_cg_solve(const fe_mesh* m, const double* b, double*
   std::memset(&h, 0, sizeof(h));
   h.maxit = opts->maxit;
   FE_CUDA(cudaMemcpyAsync(W.sc, &h, sizeof(CgScal), cudaMemcpyHostToDevice, st), "scal init");
+
+  // The system scaled by an exact power of two from the largest |b| over all slabs (as
+  // fe_cg_solve: the pairings' double-word sums have FP32's exponent range): b := sb b, x := sb x
+  double sb = 1.0;
+  {
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(W.partials);
+    FE_TRY(fe_launch_absmax(b, n, d, st));
+    // the bits of a non-negative double are the double: one slot of the scalar allgather
+    FE_CUDA(cudaMemcpyAsync(comm->red_send, d, sizeof(double), cudaMemcpyDeviceToDevice, st),
+            "scale copy");
+    FE_TRY(allgather(comm, 1, st));
+    std::vector<double> all(comm->size > 0 ? comm->size : 1);
+    FE_CUDA(cudaMemcpyAsync(all.data(), comm->red_all, all.size() * sizeof(double),
+                            cudaMemcpyDeviceToHost, st),
+            "scale readback");
+    FE_CUDA(cudaStreamSynchronize(st), "scale readback");
+    double mx = 0.0;
+    for (double v : all) mx = v > mx || v != v ? v : mx;
+    if (!fe_scale_of_max(mx, &sb)) {
+      fe_set_error("fe_slab_cg_solve: the right-hand side holds a non-finite value");
+      return FE_ERR_INVALID;
+    }
+    FE_TRY(fe_cg_scale(b, W.bs, sb, n, st));
+    FE_TRY(fe_cg_scale(x, x, sb, n, st));
+    b = W.bs;
+  }
 
   // ||G^T b||^2 over the whole mesh
   FE_CUDA(cudaMemcpyAsync(W.w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy");
@@ -493,6 +520,8 @@ extern "C" fe_status fe_slab_cg_solve(const fe_mesh* m, const double* b, double*
       return FE_ERR_CUDA;
     }
   }
+  FE_TRY(fe_cg_scale(x, x, 1.0 / sb, n, st));  // 1/sb: a power of two, exact
+  FE_CUDA(cudaStreamSynchronize(st), "synchronize");
   res->iters = h.iter;
   res->outer_iters = 1;
   res->rel_res = h.relres;

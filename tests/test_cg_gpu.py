@@ -197,3 +197,52 @@ def test_reliable_update_solve_at_48cubed(fe):
     assert float((x32 - x64).abs().max()) <= 1e-8 * float(x64.abs().max())
     e64, e32 = gm.l2_error(x64), gm.l2_error(x32)
     assert abs(e64 - e32) <= 1e-6 * e64
+
+
+@pytest.mark.parametrize("scale", [1e-300, 1e-30, 1e30, 1e300])
+@pytest.mark.parametrize("scheme", ["fp64", "mixed", "fcg"])
+def test_badly_scaled_rhs(fe, scheme, scale):
+    """A right-hand side far from unit size solves like the unscaled one (solution scaled, same
+    iteration count up to a few): the solver scales the system by an exact power of two, so the
+    double-word pairings (FP32's exponent range) neither overflow nor flush."""
+    m, p = (6, 5, 4), 3
+    gm = fe.Mesh(m, p, deform_amp=0.1, dirichlet=True)
+    b = gm.rhs(fe.FE_RHS_SINE)
+    mixed = 0 if scheme == "fp64" else fe.FE_F32
+    out = {}
+    for sc in (1.0, scale):
+        x = torch.zeros_like(b)
+        r = gm.cg_solve(b * sc, x, rtol=1e-10, maxit=2000, mixed=mixed,
+                        flexible=(scheme == "fcg"), inner_rtol=0.1)
+        assert r.status == fe.FE_OK and r.iters > 0 and r.rel_res <= 1e-10, (sc, r.iters)
+        out[sc] = (r.iters, x.cpu().numpy() / sc)
+    assert abs(out[scale][0] - out[1.0][0]) <= max(3, out[1.0][0] // 20)
+    assert rel_max_err(out[scale][1], out[1.0][1]) <= 1e-8
+
+
+def test_batched_badly_scaled_rhs(fe):
+    """Each problem of a batch is scaled by its own power of two."""
+    meshes = [fe.Mesh(5, 2, deform_amp=0.05, dirichlet=True), fe.Mesh(4, 3, dirichlet=True)]
+    scales = [1e-200, 1e200]
+    for mixed in (0, fe.FE_F32):
+        opts = fe.fe_cg_opts(1e-10, 2000, mixed, 0, 0.1, None)
+        bs = [m.rhs(fe.FE_RHS_SINE) for m in meshes]
+        xs = [torch.zeros_like(b) for b in bs]
+        ref = fe.fe_cg_solve_batched([m.handle for m in meshes], bs, xs, opts)
+        xr = [x.cpu().numpy() for x in xs]
+        bs2 = [b * s for b, s in zip(bs, scales)]
+        xs2 = [torch.zeros_like(b) for b in bs2]
+        res = fe.fe_cg_solve_batched([m.handle for m in meshes], bs2, xs2, opts)
+        for r0, r1, x0, x1, s in zip(ref, res, xr, xs2, scales):
+            assert r1.status == fe.FE_OK and r1.iters > 0, (mixed, s)
+            assert abs(r1.iters - r0.iters) <= 3
+            assert rel_max_err(x1.cpu().numpy() / s, x0) <= 1e-8
+
+
+def test_nonfinite_rhs_is_rejected(fe):
+    gm = fe.Mesh(3, 2, dirichlet=True)
+    b = gm.rhs(fe.FE_RHS_SINE)
+    b[5] = float("inf")
+    with pytest.raises(fe.FeError) as e:
+        gm.cg_solve(b, torch.zeros_like(b), rtol=1e-10)
+    assert e.value.status == fe.FE_ERR_INVALID

@@ -225,13 +225,14 @@ def test_slab_pcg_follows_the_assembled_pcg(fe, sl, nslabs):
     xg, gidx = _unique_from_cellwise(om, xc)
     assert np.array_equal(xc, xg[gidx])
     assert rel_max_err(xg, ref["x"]) <= 1e-9
-    # one plane exchange and one allgather per iteration (plus the set-up ones)
+    # one plane exchange and one allgather per iteration (plus the set-up ones: the diagonal's
+    # exchange, and the allgather of the largest |b| that scales the system)
     for r, (nx, ng) in enumerate(grp.calls):
         if nslabs == 1:
             assert (nx, ng) == (0, 0)
         else:
-            assert nx == ng + 1  # the diagonal's exchange has no allgather
-            assert 0 <= ng - 2 - res[r].iters <= 3  # flag read every 4 iterations
+            assert nx == ng
+            assert 0 <= ng - 3 - res[r].iters <= 3  # flag read every 4 iterations
 
 
 def test_slab_pcg_manufactured_solution(fe, sl):
@@ -253,6 +254,25 @@ def test_slab_pcg_manufactured_solution(fe, sl):
     assert rel_max_err(xc.cpu().numpy(), xw.cpu().numpy()) <= 1e-8
     e2 = sum(s.l2_error(x) ** 2 for s, x in zip(slabs, xs)) ** 0.5
     assert e2 == pytest.approx(whole.l2_error(xw), rel=1e-6)
+
+
+@pytest.mark.parametrize("scale", [1e-300, 1e30])
+def test_slab_pcg_badly_scaled_rhs(fe, sl, scale):
+    """Right-hand sides far from unit size solve like the unscaled one: the system is scaled by an
+    exact power of two taken from the largest |b| over all slabs."""
+    m, p, nslabs = (4, 4, 6), 2, 2
+    ranges = sl.slab_ranges(m[2], nslabs)
+    slabs = [sl.Slab(m, p, z0, z1, deform_amp=0.1, dirichlet=True) for z0, z1 in ranges]
+    g = sl.ThreadSlabGroup(nslabs)
+    comms = [g.comm(r, slabs[r].plane_len, "cuda:0") for r in range(nslabs)]
+    sols = {}
+    for sc in (1.0, scale):
+        xs = [torch.zeros(s.cellwise_len, dtype=torch.float64, device="cuda") for s in slabs]
+        res = run_slabs(nslabs, lambda r: slabs[r].cg_solve(slabs[r].rhs() * sc, xs[r],
+                                                            comm=comms[r], rtol=1e-10, maxit=500))
+        assert all(r_.status == fe.FE_OK and r_.iters > 0 for r_ in res), (sc, res[0].iters)
+        sols[sc] = torch.cat(xs).cpu().numpy() / sc
+    assert rel_max_err(sols[scale], sols[1.0]) <= 1e-8
 
 
 def test_slab_errors(fe, sl):
