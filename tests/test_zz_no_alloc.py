@@ -3,6 +3,7 @@ device memory (their memory is all in their own pool, or an allocation's possibl
 synchronization is not acceptable on their path).  It must agree with fe_pairing, the entry point
 whose partial sums live in library-allocated scratch, on consecutive calls that share the static
 scratch array.  This file is collected last so that a failure here comes after every other test."""
+import gc
 import math
 
 import numpy as np
@@ -69,13 +70,21 @@ def test_noalloc_pairing_against_host_fp64_sum_without_allocating(scale):
     b = torch.from_numpy(bn).cuda()
     _pair(fe, gm, fe.FE_F64, a, b, fe.fe_pairing_noalloc)  # first call on the device: set-up
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # meshes of earlier tests that the garbage collector frees inside the window would hand
+    # device memory back (free memory up): collect them first and keep the collector off
+    gc.collect()
     torch.cuda.synchronize()
-    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
-    for _ in range(2):
-        fe.fe_pairing_noalloc(gm.handle, fe.FE_F64, a, b, out)
-        torch.cuda.synchronize()
-        assert abs(out.item() - ref) <= 1e-14 * mag, scale
-    assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_reserved() == reserved0
+    gc.disable()
+    try:
+        free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+        for _ in range(2):
+            fe.fe_pairing_noalloc(gm.handle, fe.FE_F64, a, b, out)
+            torch.cuda.synchronize()
+            assert abs(out.item() - ref) <= 1e-14 * mag, scale
+        free1, reserved1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    finally:
+        gc.enable()
+    assert free1 >= free0 and reserved1 == reserved0  # nothing allocated on the device
     got = _pair(fe, gm, fe.FE_F64, a, b, fe.fe_pairing)
     assert abs(got - ref) <= 1e-14 * mag, scale
     gm.close()
