@@ -969,11 +969,19 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 }
 
 // Resident CTAs per SM the one-layer kernels are compiled for: the double-word kernels are held
-// to the register budget of 3 (Laplace, unrolled degrees: 80 registers), 4 (Laplace, rolled: 64)
-// or 6 (mass: 40) CTAs per SM; the rest are left to the compiler.
+// to the register budget of 3 (Laplace, unrolled degrees: 80 registers; n = 3: 4), 4 (Laplace,
+// rolled: 64) or 6 (mass: 40) CTAs per SM; the rest are left to the compiler.
+// n = 3 double-word Laplace: 4 CTAs per SM (64 registers, no spills); its kernel waits on shared
+// memory rather than on issue, and the extra CTA took Q2 48^3 from 0.0887 to 0.0846 ms (assembled
+// 0.1184 to 0.1133 ms)
+#ifndef FE_DW_LAPLACE_MINB_N3
+#define FE_DW_LAPLACE_MINB_N3 4
+#endif
 template <int N, class V, int OP>
 __host__ __device__ constexpr int apply_minb() {
-  return std::is_same<V, dw>::value ? (OP == FE_LAPLACE ? (N < FE_ROLL_MINN ? 3 : 4) : 6) : 1;
+  return std::is_same<V, dw>::value
+             ? (OP == FE_LAPLACE ? (N == 3 ? FE_DW_LAPLACE_MINB_N3 : (N < FE_ROLL_MINN ? 3 : 4)) : 6)
+             : 1;
 }
 #ifdef FE_MINB
 #define FE_APPLY_BOUNDS __launch_bounds__(Cfg<N>::THREADS, FE_MINB)
