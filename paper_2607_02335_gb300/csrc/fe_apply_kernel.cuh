@@ -970,8 +970,8 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 
 // Resident CTAs per SM the one-layer kernels are compiled for: the double-word kernels are held
 // to the register budget of 3 (Laplace, unrolled degrees: 80 registers; n = 3: 4), 4 (Laplace,
-// rolled: 64; n = 8: 5) or 6 (mass: 40; up to n = 4: 8) CTAs per SM; the rest are left to the
-// compiler.
+// rolled: 64; n = 7: 3, n = 8: 5) or 6 (mass: 40; up to n = 4: 8, n = 6: 5) CTAs per SM; the rest
+// are left to the compiler.
 // n = 3 double-word Laplace: 4 CTAs per SM (64 registers, no spills); its kernel waits on shared
 // memory rather than on issue, and the extra CTA took Q2 48^3 from 0.0887 to 0.0846 ms (assembled
 // 0.1184 to 0.1133 ms)
@@ -981,6 +981,14 @@ __device__ __forceinline__ void apply_cells(const CellArgs<N, V>& a, const Tab1D
 // n = 8 double-word Laplace: 5 CTAs per SM (51 registers, no spills): Q7 32^3 0.621 -> 0.601 ms
 #ifndef FE_DW_LAPLACE_MINB_N8
 #define FE_DW_LAPLACE_MINB_N8 5
+#endif
+// n = 7 Laplace at 3 CTAs per SM and n = 6 mass at 5: the budgets of 4 and 6 spilled (100 and 16
+// bytes); Q6 32^3 Laplace 0.443 -> 0.437 ms, Q5 40^3 mass 0.171 -> 0.168 ms
+#ifndef FE_DW_LAPLACE_MINB_N7
+#define FE_DW_LAPLACE_MINB_N7 3
+#endif
+#ifndef FE_DW_MASS_MINB_N6
+#define FE_DW_MASS_MINB_N6 5
 #endif
 // double-word mass up to n = 4: 8 CTAs per SM (32 registers): Q3 96^3 0.580 -> 0.566 ms, Q2 48^3
 // assembled 0.0641 -> 0.0611 ms; from n = 5 on 32 registers spill, and 6 CTAs stay
@@ -992,8 +1000,10 @@ __host__ __device__ constexpr int apply_minb() {
   return std::is_same<V, dw>::value
              ? (OP == FE_LAPLACE
                     ? (N == 3 ? FE_DW_LAPLACE_MINB_N3
-                              : (N < FE_ROLL_MINN ? 3 : (N == 8 ? FE_DW_LAPLACE_MINB_N8 : 4)))
-                    : (N <= 4 ? FE_DW_MASS_MINB_LOW : 6))
+                              : (N < FE_ROLL_MINN ? 3
+                                                  : (N == 8 ? FE_DW_LAPLACE_MINB_N8
+                                                            : (N == 7 ? FE_DW_LAPLACE_MINB_N7 : 4))))
+                    : (N <= 4 ? FE_DW_MASS_MINB_LOW : (N == 6 ? FE_DW_MASS_MINB_N6 : 6)))
              : 1;
 }
 #ifdef FE_MINB
