@@ -145,10 +145,18 @@ __device__ __forceinline__ void apply_item(const BProb& P, int prec, int src, lo
     apply_cells<N, V, FE_LAPLACE, GEOM_STORED_K>(a, tab_of<N, V>(), cell0, sm, stride);
 }
 
+// register budget of the persistent apply: 3 CTAs per SM for the unrolled double-word degrees, 4
+// for the rolled ones (its CTA is wider than the tile and walks many tiles; the one-layer apply's
+// per-degree budgets were measured on the one-layer kernel)
+template <int N, class V>
+__host__ __device__ constexpr int batch_minb() {
+  return std::is_same<V, dw>::value ? (N < FE_ROLL_MINN ? 3 : 4) : 1;
+}
+
 // persistent apply over the tiles [lo, hi) of one degree (tiles are grouped by degree), each kernel
 // compiled for its own degree: registers and shared memory of that degree, not of the largest
 template <int N, class V>
-__global__ void __launch_bounds__(BT, (apply_minb<N, V, FE_LAPLACE>()))
+__global__ void __launch_bounds__(BT, (batch_minb<N, V>()))
     kb_apply_n(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, long long lo,
                long long hi, int slot, int prec, int src, unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char sm[];

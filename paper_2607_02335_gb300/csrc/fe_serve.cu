@@ -82,7 +82,6 @@ struct fe_server {
   cudaStream_t st = nullptr;
   FeBatch b64, b32;
   std::vector<Request*> run64, run32, pending32;
-  bool inner_phase = false;
 };
 
 namespace {
@@ -215,24 +214,81 @@ fe_status step_fp64(fe_server* S, std::vector<Request*>& news) {
   return retire(S, S->b64, S->run64);
 }
 
-fe_status step_mixed(fe_server* S) {
-  if (!S->inner_phase) {  // outer boundary: joins, then a new inner phase
-    FE_TRY(join(S, S->b32, S->run32, S->pending32, true));
-    if (S->run32.empty()) return FE_OK;
-    FE_TRY(fe_batch_read(&S->b32));
-    FE_TRY(retire(S, S->b32, S->run32));  // converged at the initial guess
-    if (S->run32.empty()) return FE_OK;
-    FE_TRY(fe_batch_inner_start(&S->b32));
-    S->inner_phase = true;
-    return FE_OK;
+// Reliable updates (or, for new requests, the initial residual check) of the given requests alone,
+// in a temporary batch; the converged ones go to `leaving`, the others start their next FP32 run
+// and go to `cont`.  The requests keep their device state, so the running batch needs no rebuild
+// for the ones that continue.
+fe_status update_runs(fe_server* S, std::vector<Request*>& reqs, bool fresh,
+                      std::vector<Request*>* cont, std::vector<std::pair<Request*, CgScal[2]>>* leaving) {
+  std::vector<Request*> go;
+  {
+    FeBatch J;
+    J.st = S->st;
+    J.own_stream = false;
+    FE_TRY(rebuild(S, J, reqs));
+    if (fresh)
+      FE_TRY(fe_batch_start(&J, true));
+    else
+      FE_TRY(fe_batch_inner_finish(&J));
+    FE_TRY(fe_batch_read(&J));
+    for (size_t i = 0; i < reqs.size(); ++i) {
+      const CgScal* sc = &J.hsc[2 * i];
+      if (sc[0].done) {
+        leaving->emplace_back();
+        leaving->back().first = reqs[i];
+        leaving->back().second[0] = sc[0];
+        leaving->back().second[1] = sc[1];
+      } else {
+        go.push_back(reqs[i]);
+      }
+    }
   }
-  for (int k = 0; k < 4; ++k) FE_TRY(fe_batch_iteration<float>(&S->b32, 1, 1));
-  FE_TRY(fe_batch_read(&S->b32));
-  if (!fe_batch_all_done(&S->b32, 1)) return FE_OK;
-  FE_TRY(fe_batch_inner_finish(&S->b32));
-  FE_TRY(fe_batch_read(&S->b32));
-  S->inner_phase = false;
-  return retire(S, S->b32, S->run32);
+  if (!go.empty()) {
+    FeBatch K;
+    K.st = S->st;
+    K.own_stream = false;
+    FE_TRY(rebuild(S, K, go));
+    FE_TRY(fe_batch_inner_start(&K));
+  }
+  cont->insert(cont->end(), go.begin(), go.end());
+  return FE_OK;
+}
+
+// Mixed requests run their FP32 runs independently: a round advances every running request by
+// four FP32 iterations (a request whose run has ended is skipped by the kernels); then the
+// requests whose run ended take their reliable update alone and leave converged or start their
+// next run, so no request waits for another's run.  New requests join between rounds.
+fe_status step_mixed(fe_server* S) {
+  std::vector<std::pair<Request*, CgScal[2]>> leaving;
+  bool changed = false;
+  if (!S->pending32.empty()) {
+    std::vector<Request*> news;
+    news.swap(S->pending32);
+    FE_TRY(update_runs(S, news, true, &S->run32, &leaving));
+    changed = true;
+  }
+  if (!S->run32.empty()) {
+    if (changed) FE_TRY(rebuild(S, S->b32, S->run32));
+    changed = false;
+    for (int k = 0; k < 4; ++k) FE_TRY(fe_batch_iteration<float>(&S->b32, 1, 1));
+    FE_TRY(fe_batch_read(&S->b32));
+    std::vector<Request*> ended, keep;
+    for (size_t i = 0; i < S->run32.size(); ++i)
+      (S->b32.hsc[2 * i + 1].done ? ended : keep).push_back(S->run32[i]);
+    if (!ended.empty()) {
+      const size_t before = leaving.size();
+      std::vector<Request*> cont;
+      FE_TRY(update_runs(S, ended, false, &cont, &leaving));
+      if (leaving.size() > before) {  // the running batch must stop referencing them first
+        keep.insert(keep.end(), cont.begin(), cont.end());
+        S->run32.swap(keep);
+        changed = true;
+      }
+    }
+  }
+  if (changed) FE_TRY(rebuild(S, S->b32, S->run32));
+  for (auto& l : leaving) finish_request(S, l.first, FE_OK, l.second);
+  return FE_OK;
 }
 
 void worker_main(fe_server* S) {
