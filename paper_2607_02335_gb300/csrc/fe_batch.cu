@@ -980,18 +980,58 @@ fe_status fe_batch_solve(FeBatch* B, const fe_cg_opts* opts) {
     }
     return FE_OK;
   }
-  // mixed: FP32 PCG runs between FP64 reliable updates
+  // mixed: FP32 PCG runs between FP64 reliable updates, each problem on its own: after every
+  // round of iterations the problems whose run has ended take their reliable update in a batch of
+  // their own and leave converged or start their next run (the running batch's kernels skip a
+  // problem whose run has ended), so a round costs the iterations it runs, not the longest run
+  FE_TRY(fe_batch_read(B));
+  FE_TRY(drop_converged(B));
+  if (fe_batch_all_done(B, 0)) return FE_OK;
+  FE_TRY(fe_batch_inner_start(B));
+  auto subset = [&](const std::vector<int>& idx, FeBatch& J) -> fe_status {
+    J.st = B->st;
+    J.own_stream = false;
+    J.hp.resize(idx.size());
+    for (size_t k = 0; k < idx.size(); ++k) J.hp[k] = B->hp[idx[k]];
+    J.active.assign(idx.size(), 1);
+    FE_CUDA(cudaMallocHost(&J.hsc, 2 * idx.size() * sizeof(CgScal)), "batch scalars");
+    J.cap_hsc = 2 * idx.size();
+    return fe_batch_build(&J);
+  };
   for (;;) {
+    for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<float>(B, 1, 1));
     FE_TRY(fe_batch_read(B));
-    if (fe_batch_all_done(B, 0)) break;
-    FE_TRY(drop_converged(B));
-    FE_TRY(fe_batch_inner_start(B));
-    FE_TRY(fe_batch_read(B));
-    while (!fe_batch_all_done(B, 1)) {
-      for (int k = 0; k < batch; ++k) FE_TRY(fe_batch_iteration<float>(B, 1, 1));
-      FE_TRY(fe_batch_read(B));
+    std::vector<int> ended;
+    for (size_t i = 0; i < B->hp.size(); ++i)
+      if (B->active[i] && B->hsc[2 * i + 1].done) ended.push_back((int)i);
+    if (ended.empty()) continue;
+    std::vector<int> cont;
+    bool left = false;
+    {
+      FeBatch J;
+      FE_TRY(subset(ended, J));
+      FE_TRY(fe_batch_inner_finish(&J));
+      FE_TRY(fe_batch_read(&J));
+      for (size_t k = 0; k < ended.size(); ++k) {
+        if (J.hsc[2 * k].done) {
+          B->active[ended[k]] = 0;
+          left = true;
+        } else {
+          cont.push_back(ended[k]);
+        }
+      }
     }
-    FE_TRY(fe_batch_inner_finish(B));
+    if (!cont.empty()) {
+      FeBatch K;
+      FE_TRY(subset(cont, K));
+      FE_TRY(fe_batch_inner_start(&K));
+    }
+    if (left) {
+      bool any = false;
+      for (size_t i = 0; i < B->hp.size(); ++i) any |= B->active[i] != 0;
+      if (!any) break;
+      FE_TRY(fe_batch_build(B));
+    }
   }
   return FE_OK;
 }
