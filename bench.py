@@ -253,21 +253,47 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def committed_traffic():
-    """dram read + write bytes per launch of the roofline kernel from the committed ncu summary,
-    or None when the kernel sources changed after the capture."""
+def committed_profile():
+    """The committed ncu figures of the roofline kernel (profiles/traffic.txt), or {} when the
+    kernel sources changed after the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
-        return None
+        return {}
     d = {}
     with open(path) as f:
         for line in f:
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 d[k.strip()] = v.strip()
-    if d.get("source_sha") != kernel_source_sha():
-        return None
+    return d if d.get("source_sha") == kernel_source_sha() else {}
+
+
+def committed_traffic():
+    """dram read + write bytes per launch of the roofline kernel from the committed ncu summary,
+    or None when the kernel sources changed after the capture."""
+    d = committed_profile()
     return int(d["bytes_per_launch"]) if "bytes_per_launch" in d else None
+
+
+def issue_roofline(kernel_ms, cellwise_dofs):
+    """The roofline kernel against the SMs' instruction issue: warp instructions per cell-wise DoF
+    from the committed ncu capture, times the DoFs of the timed launch, over the CUDA-event time,
+    against 152 SMs x 4 schedulers x one warp instruction per clock at the maximum SM clock."""
+    d = committed_profile()
+    if "warp_instructions_per_cellwise_dof" not in d:
+        return None
+    per_dof = float(d["warp_instructions_per_cellwise_dof"])
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    achieved = per_dof * cellwise_dofs / (kernel_ms * 1e-3) / 1e12
+    peak = 152 * 4 * mhz * 1e6 / 1e12
+    return {"unit": "T warp-instructions/s", "achieved": round(achieved, 4), "peak": round(peak, 4),
+            "frac": round(achieved / peak, 4), "warp_instructions_per_cellwise_dof": per_dof,
+            "note": "the kernel is bound by instruction issue (double-word FP64 arithmetic on the "
+                    "FP32 pipe); frac is its share of the issue peak"}
 
 
 def max_over_ranks(x, world, device):
@@ -396,7 +422,8 @@ def run_ours(args, rank, world):
                 "frac": round(achieved / peak, 4), "traffic": committed_traffic(),
                 "kernel": f"k_apply<{dom['degree'] + 1},dw,{dom['op']},stored>",
                 "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                "alg_bytes_per_launch": dom["volumetric_alg_bytes"]}
+                "alg_bytes_per_launch": dom["volumetric_alg_bytes"],
+                "issue": issue_roofline(dom["volumetric_ms"], dom["cellwise_dofs"])}
 
     # end to end through the C ABI with host buffers: every step copies each mesh's input in and
     # both operators' outputs out, as unique-node vectors (fe_apply_host: the cell-wise expansion
