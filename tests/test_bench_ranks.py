@@ -87,3 +87,18 @@ def test_unknown_extra_blocks_are_rejected():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--extras", "serving,bogus"],
                        capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert r.returncode != 0 and "bogus" in r.stderr
+
+
+def test_committed_profile_belongs_to_the_committed_kernels():
+    """profiles/traffic.txt was captured from the kernel sources in the tree (the bench reports
+    its traffic and instruction figures only then), and the issue roofline built from it is a
+    fraction of the issue peak for the kernel time the bench measures."""
+    b = _bench()
+    d = b.committed_profile()
+    assert d, "profiles/traffic.txt is stale: recapture it for the current kernel sources"
+    assert b.committed_traffic() == int(d["bytes_per_launch"])
+    per_dof = float(d["warp_instructions_per_cellwise_dof"])
+    assert per_dof * 32 == pytest.approx(float(d["warp_instructions"]) * 32 / 7077888)
+    r = b.issue_roofline(1.385, 56623104)  # Q3 96^3 Laplace volumetric, its measured time
+    assert r is not None and 0.5 < r["frac"] < 1.05
+    assert r["achieved"] == pytest.approx(per_dof * 56623104 / 1.385e-3 / 1e12, rel=1e-3)
