@@ -98,7 +98,7 @@ def test_committed_profile_belongs_to_the_committed_kernels():
     assert d, "profiles/traffic.txt is stale: recapture it for the current kernel sources"
     assert b.committed_traffic() == int(d["bytes_per_launch"])
     per_dof = float(d["warp_instructions_per_cellwise_dof"])
-    assert per_dof * 32 == pytest.approx(float(d["warp_instructions"]) * 32 / 7077888)
+    assert per_dof == pytest.approx(float(d["warp_instructions"]) / 7077888, rel=1e-4)
     r = b.issue_roofline(1.385, 56623104)  # Q3 96^3 Laplace volumetric, its measured time
     assert r is not None and 0.5 < r["frac"] < 1.05
     assert r["achieved"] == pytest.approx(per_dof * 56623104 / 1.385e-3 / 1e12, rel=1e-3)
