@@ -64,6 +64,9 @@ def parse():
                          "reduced_precision_apply, block_structured_dss, packed_storage, "
                          "hanging_node_dss, slab_decomposition, solve_mixed_vs_fp64, batched, "
                          "serving")
+    ap.add_argument("--profile-batched", type=int, default=0,
+                    help="N: only run the batched mixed solve of the first N problems of the "
+                         "batched workload, untimed (for profiler captures)")
     ap.add_argument("--profile-case", default=None,
                     help="p,m,op[,vol[,f64|f32|bf16|fp16]]: only run K+W applies of one case "
                          "(for profiler captures)")
@@ -1004,10 +1007,36 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": args.profile_case, "launches": args.warmup + args.steps}))
 
 
+def run_profile_batched(args):
+    """The first N problems of the batched workload solved once by the batched engine (mixed,
+    rtol 1e-10), untimed."""
+    import torch
+
+    from paper_2607_02335_gb300 import fe
+    from paper_2607_02335_gb300 import synth as S
+
+    probs = S.batched_problems(256, seed=0)[: args.profile_batched]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    meshes = [fe.Mesh(pr["m"], pr["p"], deform_amp=pr["amp"], dirichlet=True) for pr in probs]
+    bs = [torch.rand(g.cellwise_len, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
+          for g in meshes]
+    xs = [torch.zeros_like(b) for b in bs]
+    opts = fe.fe_cg_opts(1e-10, 20000, fe.FE_F32, 0, 0.1, None)
+    res = fe.fe_cg_solve_batched([g.handle for g in meshes], bs, xs, opts)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batched": len(meshes),
+                      "converged": sum(r.status == fe.FE_OK for r in res),
+                      "iters_max": max(r.iters for r in res)}))
+
+
 def main():
     args = parse()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.profile_batched > 0:
+        run_profile_batched(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
