@@ -154,24 +154,30 @@ __host__ __device__ constexpr int batch_minb() {
 }
 
 // persistent apply over the tiles [lo, hi) of one degree (tiles are grouped by degree), each kernel
-// compiled for its own degree: registers and shared memory of that degree, not of the largest
+// compiled for its own degree: registers and shared memory of that degree, not of the largest.
+// The next work item is claimed before the current tile's apply (its atomic round trip overlaps
+// the apply) and published through a double-buffered shared slot.
 template <int N, class V>
 __global__ void __launch_bounds__(BT, (batch_minb<N, V>()))
     kb_apply_n(const BProb* __restrict__ probs, const Tile* __restrict__ tiles, long long lo,
                long long hi, int slot, int prec, int src, unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ long long item;
-  for (;;) {
-    if (threadIdx.x == 0) item = lo + (long long)atomicAdd(counter, 1ULL);
-    __syncthreads();
-    const long long it = item;
-    __syncthreads();
-    if (it >= hi) break;
+  __shared__ long long item[2];  // written one tile ahead by thread 0
+  if (threadIdx.x == 0) item[0] = lo + (long long)atomicAdd(counter, 1ULL);
+  __syncthreads();
+  int buf = 0;
+  long long it = item[0];
+  while (it < hi) {  // uniform: every thread reads the same item
+    unsigned long long nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(counter, 1ULL);  // consumed after this tile
     const Tile T = tiles[it];
     const BProb& P = probs[T.prob];
-    if (*(volatile const int*)&P.sc[slot].done) continue;  // uniform over the CTA
-    apply_item<N, V>(P, prec, src, T.cell0, sm);
-    __syncthreads();  // the next tile reuses the shared-memory tile
+    if (!*(volatile const int*)&P.sc[slot].done)  // uniform over the CTA
+      apply_item<N, V>(P, prec, src, T.cell0, sm);
+    if (threadIdx.x == 0) item[buf ^ 1] = lo + (long long)nxt;
+    __syncthreads();  // the shared-memory tile is free and the next item visible
+    buf ^= 1;
+    it = item[buf];
   }
 }
 
@@ -257,11 +263,12 @@ __global__ void __launch_bounds__(BT)
   }
 }
 
-// u += alpha p ; r -= alpha q ; w = r
+// u += alpha p ; r -= alpha q ; w = r.  keep_r = 0 leaves r unwritten: with redistribution the
+// preconditioner overwrites r with (S r)/mult before anything reads it.
 template <class S>
 __global__ void __launch_bounds__(BT)
     kb_update_ur(const BProb* __restrict__ probs, const Chunk* __restrict__ chunks, int nchunks,
-                 int slot) {
+                 int slot, int keep_r) {
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const Chunk C = chunks[c];
     const BProb& P = probs[C.prob];
@@ -284,7 +291,7 @@ __global__ void __launch_bounds__(BT)
         u[e] = fma(a, pe, ue);
         re = fma(-a, qe, rq);
       }
-      r[e] = re;
+      if (keep_r) r[e] = re;
       w[e] = re;
     };
     long long e = C.lo + threadIdx.x;
@@ -797,7 +804,7 @@ fe_status fe_batch_iteration(FeBatch* B, int slot, int redistribute) {
   FE_TRY(launch_apply_batched<S>(B, slot));
   kb_qp<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot, B->d_partials);
   kb_fin_alpha<<<np, BT, 0, B->st>>>(B->d_probs, slot, B->d_partials);
-  kb_update_ur<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot);
+  kb_update_ur<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot, !redistribute);
   FE_TRY(launch_dss_batched<S>(B, slot));
   kb_precond<S><<<g, BT, 0, B->st>>>(B->d_probs, ch, B->nvch, slot,
                                      1 | (redistribute ? 2 : 0) | (flexible ? 4 : 0), B->d_partials);

@@ -110,18 +110,20 @@ __global__ void k_correct(double* __restrict__ x, const float* __restrict__ d, d
     x[e] += inv_s * (double)d[e];
 }
 
-// u += alpha p ; r -= alpha q, and the new r also into w (the DSS then works on w in place)
+// u += alpha p ; r -= alpha q, and the new r also into w (the DSS then works on w in place).
+// keep_r = 0 leaves r unwritten: with redistribution the preconditioner overwrites r with
+// (S r)/mult before anything reads it, so the store would be dead traffic.
 template <class S, class U>
 __global__ void k_update_ur(U* __restrict__ u, S* __restrict__ r, S* __restrict__ w,
                             const S* __restrict__ p, const S* __restrict__ q,
-                            const CgScal* __restrict__ sc, long long n) {
+                            const CgScal* __restrict__ sc, long long n, int keep_r) {
   if (*(volatile const int*)&sc->done) return;
   const double a = sc->alpha;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     u[e] = (U)((double)u[e] + a * (double)p[e]);
     const S re = (S)((double)r[e] - a * (double)q[e]);
-    r[e] = re;
+    if (keep_r) r[e] = re;
     w[e] = re;
   }
 }
@@ -130,14 +132,14 @@ template <>
 __global__ void k_update_ur<float, float>(float* __restrict__ u, float* __restrict__ r,
                                           float* __restrict__ w, const float* __restrict__ p,
                                           const float* __restrict__ q,
-                                          const CgScal* __restrict__ sc, long long n) {
+                                          const CgScal* __restrict__ sc, long long n, int keep_r) {
   if (*(volatile const int*)&sc->done) return;
   const float a = (float)sc->alpha;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     u[e] = fmaf(a, p[e], u[e]);
     const float re = fmaf(-a, q[e], r[e]);
-    r[e] = re;
+    if (keep_r) r[e] = re;
     w[e] = re;
   }
 }
@@ -461,13 +463,15 @@ fe_status enqueue_iteration(const fe_mesh* m, CgWork* w, int op, bool flexible, 
     FE_TRY(fe_launch_apply_f64dw(L));
   else
     FE_TRY(launch_inner_apply(L, w));
+  // FP32 iterations redistribute: r = (S r)/mult is formed by the preconditioner
+  const int redistribute = sizeof(S) == 4 ? 1 : 0;
   k_qp<S><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(q, p, w->partials, sc, n);
   k_fin_alpha<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, hist);
-  k_update_ur<S, U><<<grid_for(n), 256, 0, w->st>>>(u, r, wv, p, q, sc, n);
+  k_update_ur<S, U><<<grid_for(n), 256, 0, w->st>>>(u, r, wv, p, q, sc, n, !redistribute);
   FE_TRY(fe_launch_dss(m, sizeof(S) == 8 ? FE_F64 : FE_F32, wv, w->st));
   k_precond<S><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(wv, r, flexible ? q : nullptr, invdiag,
                                                       w->invmult, z, w->partials, sc, n, 1,
-                                                      sizeof(S) == 4 ? 1 : 0);
+                                                      redistribute);
   k_fin_beta<<<1, RED_THREADS, 0, w->st>>>(w->partials, sc, -1.0, FIN_ITER, flexible ? 1 : 0, hist);
   k_update_p<S><<<grid_for(n), 256, 0, w->st>>>(p, z, sc, n);
   return fe_cuda_check(cudaGetLastError(), "cg iteration launch");
@@ -620,7 +624,7 @@ fe_status solve_fcg_outer(const fe_mesh* m, CgWork* w, int op, const double* b, 
     k_qp<double><<<RED_BLOCKS, RED_THREADS, 0, w->st>>>(w->q, w->p, w->partials, &w->sc[0], n);
     k_fin_alpha<<<1, RED_THREADS, 0, w->st>>>(w->partials, &w->sc[0], nullptr);
     k_update_ur<double, double><<<grid_for(n), 256, 0, w->st>>>(w->x, w->r, w->w, w->p, w->q,
-                                                                 &w->sc[0], n);
+                                                                 &w->sc[0], n, 1);
     FE_TRY(residual_norm<double>(m, w, w->r, w->w, &w->sc[0], FIN_NORM));
     FE_TRY(read_scal(w, 0, &h));
     ++outer;
