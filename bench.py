@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="N: only run the batched mixed solve of the first N problems of the "
                          "batched workload, untimed (for profiler captures)")
+    ap.add_argument("--profile-solve", default=None, choices=["fp64", "mixed"],
+                    help="only run one solve of the Q3 64^3 Poisson problem of the "
+                         "solve_mixed_vs_fp64 block (FP64 PCG, or FP32 PCG with FP64 reliable "
+                         "updates), untimed (for profiler captures)")
     ap.add_argument("--profile-case", default=None,
                     help="p,m,op[,vol[,f64|f32|bf16|fp16]]: only run K+W applies of one case "
                          "(for profiler captures)")
@@ -1030,8 +1034,29 @@ def run_profile_batched(args):
                       "iters_max": max(r.iters for r in res)}))
 
 
+def run_profile_solve(args):
+    """One solve of the solve_mixed_vs_fp64 workload (Q3 64^3 deformed, sine load, rtol 1e-10):
+    FP64 PCG or FP32 PCG with FP64 reliable updates, untimed."""
+    import torch
+
+    from paper_2607_02335_gb300 import fe
+
+    gm = fe.Mesh(64, 3, deform_amp=AMP, dirichlet=True)
+    b = gm.rhs(fe.FE_RHS_SINE)
+    x = torch.zeros_like(b)
+    mixed = fe.FE_F32 if args.profile_solve == "mixed" else 0
+    res = gm.cg_solve(b, x, rtol=1e-10, maxit=20000, mixed=mixed, flexible=False, inner_rtol=0.1)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": args.profile_solve, "status": fe.STATUS_NAMES[res.status],
+                      "iters": res.iters, "outer_iters": res.outer_iters}))
+    gm.close()
+
+
 def main():
     args = parse()
+    if args.profile_solve:
+        run_profile_solve(args)
+        return
     if args.profile_case:
         run_profile_case(args)
         return
