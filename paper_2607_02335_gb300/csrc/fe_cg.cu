@@ -110,6 +110,13 @@ __global__ void k_correct(double* __restrict__ x, const float* __restrict__ d, d
     x[e] += inv_s * (double)d[e];
 }
 
+// Elements per thread whose loads a two-input streaming kernel (<q,p>, the p update) issues
+// together: eight FP32 elements keep as many bytes in flight per thread as four FP64 ones.
+template <class S>
+__host__ __device__ constexpr int stream_u() {
+  return sizeof(S) == 4 ? 2 * RED_U : RED_U;
+}
+
 // u += alpha p ; r -= alpha q, and the new r also into w (the DSS then works on w in place).
 // keep_r = 0 leaves r unwritten: with redistribution the preconditioner overwrites r with
 // (S r)/mult before anything reads it, so the store would be dead traffic.  Launched on a
@@ -180,20 +187,21 @@ __global__ void k_keep_direction(float* __restrict__ p, const float* __restrict_
     p[e] = fmaf(c, p[e], z[e]);
 }
 
-// p = z + beta p (RED_U elements' loads in flight per thread, as k_update_ur)
+// p = z + beta p (stream_u elements' loads in flight per thread, on a resident grid)
 template <class S>
 __global__ void k_update_p(S* __restrict__ p, const S* __restrict__ z, const CgScal* __restrict__ sc,
                            long long n) {
   if (*(volatile const int*)&sc->done) return;
   const S b = (S)sc->beta;
+  constexpr int PU = stream_u<S>();
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; e + (RED_U - 1) * stride < n; e += RED_U * stride) {
-    S zv[RED_U], pv[RED_U];
+  for (; e + (PU - 1) * stride < n; e += PU * stride) {
+    S zv[PU], pv[PU];
 #pragma unroll
-    for (int k = 0; k < RED_U; ++k) zv[k] = z[e + k * stride], pv[k] = p[e + k * stride];
+    for (int k = 0; k < PU; ++k) zv[k] = z[e + k * stride], pv[k] = p[e + k * stride];
 #pragma unroll
-    for (int k = 0; k < RED_U; ++k) p[e + k * stride] = zv[k] + b * pv[k];
+    for (int k = 0; k < PU; ++k) p[e + k * stride] = zv[k] + b * pv[k];
   }
   for (; e < n; e += stride) p[e] = z[e] + b * p[e];
 }
@@ -245,17 +253,18 @@ __global__ void __launch_bounds__(RED_THREADS)
   __shared__ dw sh[32];
   Acc<S> acc;
   constexpr long long STRIDE = (long long)RED_BLOCKS * RED_THREADS;
+  constexpr int QU = stream_u<S>();
   long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
-  // RED_U elements' loads in flight before their products join the accumulator, in the same order
-  for (; e + (RED_U - 1) * STRIDE < n; e += RED_U * STRIDE) {
-    S qv[RED_U], pv[RED_U];
+  // QU elements' loads in flight before their products join the accumulator, in the same order
+  for (; e + (QU - 1) * STRIDE < n; e += QU * STRIDE) {
+    S qv[QU], pv[QU];
 #pragma unroll
-    for (int u = 0; u < RED_U; ++u) {
+    for (int u = 0; u < QU; ++u) {
       qv[u] = q[e + u * STRIDE];
       pv[u] = p[e + u * STRIDE];
     }
 #pragma unroll
-    for (int u = 0; u < RED_U; ++u) acc.add_prod(qv[u], pv[u]);
+    for (int u = 0; u < QU; ++u) acc.add_prod(qv[u], pv[u]);
   }
   for (; e < n; e += STRIDE) acc.add_prod(q[e], p[e]);
   const dw accv = block_reduce_dw(acc.value(), sh);
