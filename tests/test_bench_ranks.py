@@ -102,3 +102,34 @@ def test_committed_profile_belongs_to_the_committed_kernels():
     r = b.issue_roofline(1.385, 56623104)  # Q3 96^3 Laplace volumetric, its measured time
     assert r is not None and 0.5 < r["frac"] < 1.05
     assert r["achieved"] == pytest.approx(per_dof * 56623104 / 1.385e-3 / 1e12, rel=1e-3)
+
+
+def test_profile_commands_run_with_the_committed_bench(monkeypatch):
+    """Every profiler summary under profiles/ names the command that made it: an ncu run with
+    --clock-control none over `python bench.py ...` arguments that the committed bench.py still
+    accepts (a stale summary would cite a command that no longer runs)."""
+    import glob
+    import re
+    import shlex
+    import sys
+    b = _bench()
+    paths = sorted(glob.glob(os.path.join(ROOT, "profiles", "*")))
+    assert paths
+    checked = 0
+    for path in paths:
+        text = open(path).read().replace("\\\n", " ")
+        cmds = [ln for ln in text.splitlines() if re.search(r"\bncu\s+-", ln) and "bench.py" in ln]
+        assert cmds, f"{os.path.basename(path)} gives no ncu command over bench.py"
+        for cmd in cmds:
+            assert "--clock-control none" in cmd, (path, cmd)
+            words = shlex.split(cmd[cmd.index("bench.py"):])
+            monkeypatch.setattr(sys, "argv", words)
+            args = b.parse()
+            if args.profile_case:
+                parts = args.profile_case.split(",")
+                assert int(parts[0]) in range(1, 8) and int(parts[1]) > 0
+                assert parts[2] in ("laplace", "mass")
+                assert len(parts) < 4 or parts[3] == "vol"
+                assert len(parts) < 5 or parts[4] in ("f64", "f32", "bf16", "fp16")
+            checked += 1
+    assert checked >= len(paths)
